@@ -1,0 +1,31 @@
+"""Compile the CPU oracle (plain C99, gcc) into oracle/_build/libpgm_oracle.so.
+
+Test infrastructure: the oracle is only loaded by tests, the smoke check and the
+benchmark's CPU-baseline leg.  Building it is not using it.
+"""
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT_DIR, "libpgm_oracle.so")
+SRC = os.path.join(HERE, "pgm_oracle.c")
+
+
+def build(force: bool = False) -> str:
+    """Build the oracle library if it is missing or older than its source."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    srcs = [SRC, os.path.join(HERE, "pgm_oracle.h")]
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(s) for s in srcs)):
+        return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-Wall", "-Wextra",
+           "-Wno-unused-parameter", SRC, "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True))
