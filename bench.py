@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Throughput of the Pyramidal Gradient Matching hot path on GB300.
+
+One step = the whole path (gradient pyramids of both images, pyramidal
+matching in both directions, consistency and outlier filtering, region
+removal and match export) over a batch of Sintel-shaped 1024x436 RGB pairs
+with the paper's full version PGM-C (6-channel gradients, Table 2 colour
+schedule, r = 7 / 5 patches, 4 / 6 iterations, W = 2, N = 2) on a 5-level
+pyramid and a stride-3 seed lattice.  Inputs are resident in HBM when the
+timed region starts; L2 is flushed (a 256 MB write) before every timed step.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(the plain C reference implementation of the method) on the host cores
+instead.  Multi-GPU (torchrun): every rank matches its own pairs (replicas,
+weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pairs/s and G candidate-evals/s at 1024×436 (bit-exact); served p50/p99 ms"
+W_IMG, H_IMG = 1024, 436
+PARAMS = dict(levels=5, seed_stride=3, patch_fwd=15, patch_bwd=11, color=1, descriptor=0,
+              iters_coarse=4, iters_fine=6, refine_rounds=2, rs_W=2)
+VARIANTS = {"PGM-CD": dict(color=1, descriptor=1), "PGM-G": dict(color=0, descriptor=0),
+            "PGM-GD": dict(color=0, descriptor=1)}
+WORKLOAD = ("sintel-like 1024x436 RGB pairs (3-6 layered textured polygons, <=150 px motion), "
+            "PGM-C: 6-ch Sobel-5 gradients, Table-2 colour schedule, L=5, seed stride 3, "
+            "patch 15/11, iters 4/6, W=2, N=2")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=16, help="pairs per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--cpu-pairs", type=int, default=0, help="oracle sample size (0: one per core)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ CPU oracle
+def _oracle_one(args):
+    seed, prm = args
+    import oracle as O
+    from paper_1704_03217_gb300 import synth
+    f1, f2, _ = synth.sintel_like_pair(seed, W_IMG, H_IMG)
+    t0 = time.perf_counter()
+    O.run_pair(prm, f1, f2, O.SCHED_CHECKERBOARD, seed)
+    return time.perf_counter() - t0
+
+
+def oracle_rate(n_pairs, cores, seed0=1000):
+    """Pairs/s of the oracle, one pair per process, `cores` processes."""
+    from oracle import build as obuild
+    obuild.build()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        times = pool.map(_oracle_one, [(seed0 + k, PARAMS) for k in range(n_pairs)])
+        wall = time.perf_counter() - t0
+    # pair generation runs inside the workers too: charge only the oracle time
+    per_proc = max(sum(times[k::cores]) for k in range(cores))
+    return n_pairs / per_proc, per_proc, wall
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    n = a.cpu_pairs or cores
+    for _ in range(a.warmup):
+        oracle_rate(n, cores)
+    rates, secs = [], []
+    for _ in range(a.steps):
+        r, t, _ = oracle_rate(n, cores)
+        rates.append(r); secs.append(t)
+    total = sum(secs)
+    value = n * a.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs_per_step": n},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d sintel-like pairs per step, one per process" % n},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.p, self.path = gpu, None, None
+
+    def start(self):
+        try:
+            self.path = "/tmp/pgm_clocks_%d.csv" % os.getpid()
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            v = [x.strip() for x in ln.split(",")]
+            if len(v) < 9:
+                continue
+            try:
+                sm.append(float(v[1])); mx.append(float(v[2]))
+            except ValueError:
+                continue
+            for nm, flag in zip(names, v[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- GPU arm
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        # the oracle leg runs first, before this process touches the GPU
+        cores = os.cpu_count() or 1
+        n = a.cpu_pairs or cores
+        r, t, _ = oracle_rate(n, cores)
+        cpu = {"value": r, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": "%d sintel-like 1024x436 PGM-C pairs, one per process, %.1f s of "
+                         "oracle time per process" % (n, t)}
+
+    from paper_1704_03217_gb300 import build as pbuild
+    pbuild.build()
+    from paper_1704_03217_gb300 import api, synth, _lib
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    B = a.batch
+    prm = api.Params(**PARAMS)
+    pairs = [synth.sintel_like_pair(10 * rank * B + k, W_IMG, H_IMG) for k in range(B)]
+    imgs1 = [torch.from_numpy(p[0]).to(dev) for p in pairs]
+    imgs2 = [torch.from_numpy(p[1]).to(dev) for p in pairs]
+    m = api.PairMatcher(prm, W_IMG, H_IMG, batch=B, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sids = [rank * B + k for k in range(B)]
+
+    def step():
+        m.enqueue(imgs1, imgs2, sids)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # -------- device-timed region
+    L = _lib.load()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = L.pgm_launch_count()
+    for k in range(a.steps):
+        flush.fill_(k & 0xff)                      # L2 flush, outside the events
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = L.pgm_launch_count() - launches0
+    clk = clocks.stop()
+    ms = sum(s.elapsed_time(e) for s, e in ev)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * B * a.steps / (ms_max * 1e-3)
+    nominal = api.nominal_evals(prm, W_IMG, H_IMG, W_IMG, H_IMG)
+    counts = [int(c) for c in m.count[:, 0].tolist()]
+
+    # -------- end-to-end through the public API with host buffers
+    pin1 = [p[0] for p in pairs]
+    host1 = [torch.from_numpy(x).pin_memory() for x in pin1]
+    host2 = [torch.from_numpy(p[1]).pin_memory() for p in pairs]
+    out_rows = torch.empty(m.rows.shape, dtype=torch.int32).pin_memory()
+    out_cnt = torch.empty(m.count.shape, dtype=torch.int32).pin_memory()
+    e2e_steps = max(3, a.steps // 2)
+    e2e_t = 0.0
+    for k in range(e2e_steps + 1):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(B):
+            imgs1[i].copy_(host1[i], non_blocking=True)
+            imgs2[i].copy_(host2[i], non_blocking=True)
+        step()
+        out_cnt.copy_(m.count, non_blocking=True)
+        out_rows.copy_(m.rows, non_blocking=True)
+        torch.cuda.synchronize()
+        if k > 0:                                    # first one is a warm-up
+            e2e_t += time.perf_counter() - t0
+    h2d = sum(x.numel() for x in host1) + sum(x.numel() for x in host2)
+    d2h = out_rows.numel() * 4 + out_cnt.numel() * 4
+    e2e = world * B * e2e_steps / e2e_t
+
+    # -------- per-kernel times (profiling pass, not the timed one)
+    import ctypes as C
+    L.pgm_profile_enable(1)
+    prof_steps = 2
+    for _ in range(prof_steps):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    kms = (C.c_double * 7)()
+    kn = (C.c_int64 * 7)()
+    L.pgm_profile_read(kms, kn)
+    L.pgm_profile_enable(0)
+    kernel_ms = {name: kms[i] / prof_steps for i, name in enumerate(_lib.K_CLASSES)}
+    kernel_launches = {name: kn[i] // prof_steps for i, name in enumerate(_lib.K_CLASSES)}
+    ev_counts = [w.evals() for w in m.ws]
+    nch = 6
+    el_pm = sum(e["pm"][0] * PARAMS["patch_fwd"] ** 2 * nch + e["pm"][1] * PARAMS["patch_bwd"] ** 2 * nch
+                for e in ev_counts)                     # per step
+    pm_launch_ms = kernel_ms["pm"] / max(1, kernel_launches["pm"])
+    el_per_launch = el_pm / max(1, kernel_launches["pm"])
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak_tops = sms * 128 * sm_mhz * 1e6 / 1e12        # INT32 lanes x clock
+    achieved_tops = 3 * el_per_launch / (pm_launch_ms * 1e-3) / 1e12
+    l1_gbs = 2 * el_per_launch / (pm_launch_ms * 1e-3) / 1e9
+    l1_peak = sms * 128 * sm_mhz * 1e6 / 1e9
+
+    variants = {}
+    if not a.no_variants:
+        for name, kw in VARIANTS.items():
+            pv = prm.replace(**kw)
+            mv = api.PairMatcher(pv, W_IMG, H_IMG, batch=B, device=dev)
+            for _ in range(2):
+                mv.enqueue(imgs1, imgs2, sids)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tot = 0.0
+            for k in range(max(3, a.steps // 4)):
+                flush.fill_(k)
+                e0.record(stream)
+                mv.enqueue(imgs1, imgs2, sids)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            variants[name] = {"pairs_per_s": B * max(3, a.steps // 4) / (tot * 1e-3),
+                              "gcand_evals_per_s": api.nominal_evals(pv, W_IMG, H_IMG, W_IMG, H_IMG)
+                              * B * max(3, a.steps // 4) / (tot * 1e-3) / 1e9}
+            del mv
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs_per_step": B, "image": "1024x436x3 uint8",
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "gcand_evals_per_s": nominal * value / 1e9,
+            "nominal_evals_per_pair": nominal,
+            "matches_per_pair": sum(counts) / len(counts),
+            "e2e": {"value": e2e, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "kernel": "k_pm (propagation + random search)",
+                         "achieved": achieved_tops, "peak": peak_tops, "unit": "Top/s (int32)",
+                         "frac": achieved_tops / peak_tops, "traffic": None,
+                         "peak_source": "derived: %d SMs x 128 INT32 lanes x %.0f MHz" % (sms, sm_mhz),
+                         "ops_per_element": 3,
+                         "l1_GBps": l1_gbs, "l1_peak_GBps": l1_peak, "l1_frac": l1_gbs / l1_peak,
+                         "pm_ms_per_launch": pm_launch_ms, "pm_launches_per_step": kernel_launches["pm"]},
+            "kernel_ms_per_step": kernel_ms, "kernel_launches_per_step": kernel_launches,
+            "evals_per_step": {"pm": sum(sum(e["pm"]) for e in ev_counts),
+                               "cost": sum(sum(e["cost"]) for e in ev_counts),
+                               "init": sum(sum(e["init"]) for e in ev_counts)},
+            "variants": variants,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,242 @@
+/*
+ * pgm.h -- C ABI of the GB300 (sm_103a) hot path of Pyramidal Gradient
+ * Matching (Li, "Pyramidal Gradient Matching for Optical Flow Estimation",
+ * arXiv 1704.03217).
+ *
+ * Problem statement (Sec. III): given two images I1, I2, build their
+ * gradient pyramids (Sec. III-A Eq. 1-2, Sec. III-D, Table 2), compute a
+ * forward field F: I1 -> I2 and a backward field I2 -> I1 on a regular seed
+ * lattice by coarse-to-fine limited PatchMatch (Sec. III-B Eq. 3-5, Sec. III-D
+ * Eq. 6-8, Fig. 5), filter outliers by forward-backward consistency and small
+ * region removal (Sec. III-E), and export the surviving matches
+ * (Sec. III-G).
+ *
+ * Conventions (all entry points):
+ *  - The caller owns every buffer; the library allocates no memory.  "d_"
+ *    pointers are device pointers of the current CUDA device; others are
+ *    host pointers.
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream).  The returned status covers argument checks
+ *    and launch errors only; device-side failures are recorded in the
+ *    workspace's error word and reported by pgm_sync_status().
+ *  - Nothing throws across the ABI.  Calls on different workspaces may run
+ *    concurrently from different host threads.
+ *  - Results are a deterministic function of (params, images, stream_id):
+ *    all arithmetic is integer and the random search draws from a
+ *    counter-based generator (Philox4x32-10) keyed by params.philox_key.
+ */
+#ifndef PGM_H
+#define PGM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PGM_OK = 0,
+    PGM_ERR_ARG = 1,           /* NULL pointer, bad enum value, bad parameter */
+    PGM_ERR_SIZE = 2,          /* image too small for the pyramid / lattice   */
+    PGM_ERR_WORKSPACE = 3,     /* buffer smaller than the *_bytes query       */
+    PGM_ERR_CUDA = 4,          /* a CUDA launch or API call failed            */
+    PGM_ERR_TIMEOUT = 5,       /* a bounded device wait ran out               */
+    PGM_ERR_DEVICE_BOUNDS = 6, /* a device-side index check failed            */
+    PGM_ERR_UNSUPPORTED = 7    /* valid but outside this build's limits       */
+} pgm_status;
+
+enum { PGM_GRAY = 0, PGM_RGB = 1 };                 /* params.color           */
+enum { PGM_FULL = 0, PGM_DIR = 1 };                 /* params.descriptor      */
+enum { PGM_CS_PAPER = 0, PGM_CS_PLAIN = 1 };        /* params.cs_sched        */
+enum { PGM_L2SQ = 0, PGM_L1 = 1 };                  /* params.norm            */
+enum { PGM_RS_SYMMETRIC = 0, PGM_RS_PAPER_FLOOR = 1 }; /* params.rs_mode      */
+enum { PGM_ABL_NO_REFINE = 1, PGM_ABL_PROPAGATE_ALL = 2, PGM_ABL_NO_OUTLIER_PROP = 4 };
+
+/* Method parameters.  Defaults (pgm_default_params) are the paper's
+ * (Sec. IV: W=2, S=5, L=3, s=1/2, N=2, m=L-1, 4 iterations per level and 6 at
+ * full resolution; Sec. III-E: r=7 forward, r=5 backward, regions < 9
+ * removed, motion difference < 12 px), on a seed lattice of stride 3. */
+typedef struct {
+    int32_t levels;        /* L, 1..12 pyramid levels, downsample 1/2      */
+    int32_t seed_stride;   /* sigma >= 1: lattice stride in level pixels,
+                              seeds at c + sigma*i with c = sigma/2         */
+    int32_t patch_fwd;     /* patch side P (1..16) of the forward field    */
+    int32_t patch_bwd;     /* patch side P (1..16) of the backward field   */
+    int32_t sobel;         /* S in {3, 5} (Eq. 1)                          */
+    int32_t color;         /* PGM_GRAY (PGM-G/GD) or PGM_RGB (PGM-C/CD)    */
+    int32_t descriptor;    /* PGM_FULL gradient or PGM_DIR (G ./ |G|)      */
+    int32_t cs_sched;      /* PGM_CS_PAPER: Table 2 colour spaces per level
+                              and direction; PGM_CS_PLAIN: RGB throughout  */
+    int32_t norm;          /* PGM_L2SQ (Eq. 3) or PGM_L1                   */
+    int32_t iters_coarse;  /* propagation+search iterations at levels > 0  */
+    int32_t iters_fine;    /* ... at level 0                               */
+    int32_t refine_rounds; /* N, rounds of refinement between m and m-1    */
+    int32_t rs_W;          /* W >= 1, limited random-search radius (Eq. 5) */
+    int32_t rs_mode;       /* PGM_RS_SYMMETRIC or PGM_RS_PAPER_FLOOR       */
+    int32_t tau2;          /* consistency threshold |u_f + u_b|^2 <= tau2  */
+    int32_t min_region;    /* regions with fewer seeds are removed         */
+    int32_t region_dmax2;  /* 4-neighbours join a region iff |du|^2 < this */
+    int32_t max_visits;    /* 0: whole schedule; k > 0: stop after k visits */
+    int32_t ablation;      /* PGM_ABL_* bits (Table 1 rows)                */
+    int32_t reserved;      /* must be 0                                    */
+    uint64_t philox_key;   /* key of the random-search stream              */
+} pgm_params;
+
+/* Fill *p with the defaults above.  Never fails for a non-NULL p. */
+void pgm_default_params(pgm_params* p);
+
+/* Static description of a status code. */
+const char* pgm_status_string(pgm_status s);
+
+/* ------------------------------------------------------------------ */
+/* Gradient pyramid (Sec. III-A Eq. 1-2, Sec. III-D, Sec. III-E Table 2) */
+/* ------------------------------------------------------------------ */
+
+/* Bytes of the pyramid buffer of one w x h image (0 on invalid input).
+ * The layout depends only on (params, w, h). */
+size_t pgm_pyramid_bytes(const pgm_params* p, int w, int h);
+
+/* Build the gradient pyramid of one image.
+ *   d_img: w x h pixels, c = 1 (gray) or 3 (interleaved RGB) uint8 channels,
+ *          rows `pitch` bytes apart (pitch >= w*c).
+ *   d_pyr: device buffer of at least pgm_pyramid_bytes(p, w, h) bytes,
+ *          256-byte aligned; overwritten.
+ * Levels: I^{l+1} = 5-tap binomial of I^l decimated by 2 (W_{l+1} =
+ * ceil(W_l/2)); PGM_GRAY converts RGB to gray first; PGM_RGB converts each
+ * level to the colour space of Table 2 for the forward and the backward
+ * direction; then Sobel gradients (int16) and, for PGM_DIR, their signs.
+ * Errors: PGM_ERR_ARG (NULL, c not 1/3, PGM_RGB with c = 1, bad params),
+ * PGM_ERR_WORKSPACE (pyr_bytes too small), PGM_ERR_CUDA. */
+pgm_status pgm_build_pyramid(const pgm_params* p, const uint8_t* d_img, int w, int h, int c,
+                             size_t pitch, void* d_pyr, size_t pyr_bytes, void* stream);
+
+/* Where one level's descriptor lives inside a pyramid buffer (for tests and
+ * tools): int16 values, pixel-interleaved, `nch` = 2C channels per pixel in
+ * the order Gx of each colour channel, then Gy of each; rows `row_elems`
+ * int16 apart.  scheme 0 serves the forward field, 1 the backward field
+ * (equal to 0 unless PGM_RGB with PGM_CS_PAPER). */
+pgm_status pgm_pyramid_desc_layout(const pgm_params* p, int w, int h, int scheme, int level,
+                                   size_t* offset_bytes, int* lw, int* lh, int* nch,
+                                   int* row_elems);
+/* Where one level's colour-converted uint8 image lives: C planes of lh rows,
+ * rows `row_bytes` apart, planes `plane_bytes` apart. */
+pgm_status pgm_pyramid_image_layout(const pgm_params* p, int w, int h, int scheme, int level,
+                                    size_t* offset_bytes, int* lw, int* lh, int* channels,
+                                    int* row_bytes, size_t* plane_bytes);
+
+/* ------------------------------------------------------------------ */
+/* Pyramidal matching (Sec. III-B Eq. 3-5, Sec. III-D Eq. 6-8, Fig. 5)  */
+/* ------------------------------------------------------------------ */
+
+/* Bytes of the match workspace for a w1 x h1 -> w2 x h2 pair (0 on
+ * invalid input). */
+size_t pgm_match_workspace_bytes(const pgm_params* p, int w1, int h1, int w2, int h2);
+
+/* Run the whole coarse-to-fine schedule on one pair.
+ *   d_pyr1, d_pyr2: pyramids of I1 (w1 x h1) and I2 (w2 x h2) built with
+ *                   the same params.
+ *   stream_id:      low 32 bits enter the random-search counter, so that
+ *                   different pairs draw independent numbers.
+ *   d_ws:           >= pgm_match_workspace_bytes, 256-byte aligned; it
+ *                   receives the fields of every level and both directions
+ *                   and must be kept for pgm_filter / pgm_field_layout.
+ * Schedule (m = L-1): exhaustive nearest-neighbour init at m, then
+ * [m-1, m] x N with field and outlier record, then m-1 with the field only,
+ * then m-2 .. 0.  Each visit: cost of the current field, `iters` iterations
+ * of propagation + limited random search (checkerboard order), consistency
+ * check, outlier-record update, then the transfer to the next level.
+ * Errors: PGM_ERR_ARG, PGM_ERR_SIZE (a level has no seed), PGM_ERR_WORKSPACE,
+ * PGM_ERR_UNSUPPORTED (patch > 16, coarsest level over 2^24 pixels),
+ * PGM_ERR_CUDA. */
+pgm_status pgm_match(const pgm_params* p, const void* d_pyr1, const void* d_pyr2,
+                     int w1, int h1, int w2, int h2, uint64_t stream_id,
+                     void* d_ws, size_t ws_bytes, void* stream);
+
+/* Run pgm_match on n independent pairs in shared launches (pairs may have
+ * different sizes; each has its own pyramids and workspace).  Arrays are
+ * host arrays of length n: d_pyr1[i], d_pyr2[i], dims[4*i..4*i+3] = (w1, h1,
+ * w2, h2), d_ws[i] (each >= pgm_match_workspace_bytes of that pair),
+ * stream_ids[i].  The result of every pair equals pgm_match on that pair
+ * alone.  Same errors as pgm_match, checked for every pair before any
+ * launch. */
+pgm_status pgm_match_batch(const pgm_params* p, int n, const void* const* d_pyr1,
+                           const void* const* d_pyr2, const int32_t* dims,
+                           const uint64_t* stream_ids, void* const* d_ws,
+                           const size_t* ws_bytes, void* stream);
+
+/* Where the state of one level and direction (0 forward, 1 backward) lives
+ * in a match workspace: nx x ny seeds in raster order; u: int32 per seed,
+ * low 16 bits ux, high 16 bits uy (two's complement); cost: uint64 per seed
+ * (meaningful where valid); flags: uint8 per seed, bit 0 initialised, bit 1
+ * outlier (O^l), bit 2 outlier record initialised. */
+pgm_status pgm_field_layout(const pgm_params* p, int w1, int h1, int w2, int h2, int level,
+                            int dir, int* nx, int* ny, size_t* off_u, size_t* off_cost,
+                            size_t* off_flags);
+
+/* ------------------------------------------------------------------ */
+/* Final filter (Sec. III-E small-region removal, Sec. III-G export)    */
+/* ------------------------------------------------------------------ */
+
+/* On the level-0 forward field of a workspace filled by pgm_match: inlier
+ * seeds (outlier record "no") that are lattice 4-neighbours join a region
+ * iff |u_s - u_t|^2 < region_dmax2; regions with fewer than min_region seeds
+ * are removed.  The survivors are written in lattice raster order as rows
+ * (x1, y1, x2, y2) int32 of level-0 pixel coordinates to d_matches
+ * [max_matches][4]; *d_count (device int32) receives the number of
+ * survivors, which may exceed max_matches (then only max_matches rows are
+ * written).  d_keep (optional, may be NULL): one uint8 per level-0 forward
+ * seed, 1 = kept.
+ * Errors: PGM_ERR_ARG, PGM_ERR_WORKSPACE, PGM_ERR_CUDA. */
+pgm_status pgm_filter(const pgm_params* p, int w1, int h1, int w2, int h2, void* d_ws,
+                      size_t ws_bytes, int32_t* d_matches, int64_t max_matches,
+                      int32_t* d_count, uint8_t* d_keep, void* stream);
+
+/* Wait for `stream` and return the device-side status recorded in the
+ * workspace (PGM_OK, PGM_ERR_TIMEOUT or PGM_ERR_DEVICE_BOUNDS), clearing
+ * it.  Synchronising call. */
+pgm_status pgm_sync_status(const pgm_params* p, int w1, int h1, int w2, int h2, void* d_ws,
+                           size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Observability (no counterpart in the paper)                          */
+/* ------------------------------------------------------------------ */
+
+/* Workspace header: bytes [0, 4) hold the device status word; bytes
+ * [8, 56) six uint64 counters of patch distances (Eq. 3) actually evaluated:
+ * propagation/search forward, backward; cost refresh forward, backward;
+ * exhaustive initialisation forward, backward.  pgm_match and
+ * pgm_match_batch zero them at their start. */
+#define PGM_WS_EVALS_OFFSET 8
+#define PGM_WS_EVALS_COUNT 6
+
+/* Kernel classes for pgm_profile_read. */
+enum { PGM_K_PYRAMID = 0, PGM_K_INIT = 1, PGM_K_COST = 2, PGM_K_PM = 3, PGM_K_CONSIST = 4,
+       PGM_K_TRANSFER = 5, PGM_K_FILTER = 6, PGM_K_COUNT = 7 };
+
+/* Number of kernels this library has launched in this process (all
+ * threads, all devices).  Never fails. */
+int64_t pgm_launch_count(void);
+
+/* Start (on = 1) or stop (on = 0) per-kernel-class timing of the calling
+ * host thread: while on, each kernel launch is bracketed by a CUDA event
+ * pair recorded on its stream.  Starting clears the accumulated times.
+ * Meant for profiling runs, not for timed runs (the events cost a little).
+ * Errors: PGM_ERR_CUDA if an event cannot be created. */
+pgm_status pgm_profile_enable(int on);
+
+/* Wait for the recorded events and return, per kernel class, the summed
+ * device milliseconds ms[PGM_K_COUNT] and launch counts
+ * launches[PGM_K_COUNT] since the last pgm_profile_enable(1) (either
+ * pointer may be NULL).  Errors: PGM_ERR_CUDA. */
+pgm_status pgm_profile_read(double* ms, int64_t* launches);
+
+/* Nominal candidate evaluations of one pair under params (2 propagation + K
+ * random-search candidates per seed and iteration, one cost per seed and
+ * visit, both directions; the exhaustive init is not counted). */
+int64_t pgm_nominal_evals(const pgm_params* p, int w1, int h1, int w2, int h2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PGM_H */

@@ -1,0 +1,88 @@
+"""ctypes declarations of libpgm's C ABI (include/pgm.h).
+
+Loading fails loudly: there is no fallback implementation of any step.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpgm.so")
+
+PARAM_FIELDS = [
+    ("levels", 3), ("seed_stride", 3), ("patch_fwd", 15), ("patch_bwd", 11), ("sobel", 5),
+    ("color", 1), ("descriptor", 0), ("cs_sched", 0), ("norm", 0), ("iters_coarse", 4),
+    ("iters_fine", 6), ("refine_rounds", 2), ("rs_W", 2), ("rs_mode", 0), ("tau2", 1),
+    ("min_region", 9), ("region_dmax2", 144), ("max_visits", 0), ("ablation", 0),
+    ("reserved", 0),
+]
+
+
+class CParams(C.Structure):
+    _fields_ = [(n, C.c_int32) for n, _ in PARAM_FIELDS] + [("philox_key", C.c_uint64)]
+
+
+STATUS = {0: "PGM_OK", 1: "PGM_ERR_ARG", 2: "PGM_ERR_SIZE", 3: "PGM_ERR_WORKSPACE",
+          4: "PGM_ERR_CUDA", 5: "PGM_ERR_TIMEOUT", 6: "PGM_ERR_DEVICE_BOUNDS",
+          7: "PGM_ERR_UNSUPPORTED"}
+
+# every symbol include/pgm.h declares
+EXPORTS = [
+    "pgm_default_params", "pgm_status_string", "pgm_pyramid_bytes", "pgm_build_pyramid",
+    "pgm_pyramid_desc_layout", "pgm_pyramid_image_layout", "pgm_match_workspace_bytes",
+    "pgm_match", "pgm_match_batch", "pgm_field_layout", "pgm_filter", "pgm_sync_status",
+    "pgm_nominal_evals", "pgm_launch_count", "pgm_profile_enable", "pgm_profile_read",
+]
+K_CLASSES = ["pyramid", "init", "cost", "pm", "consist", "transfer", "filter"]
+WS_EVALS_OFFSET, WS_EVALS_COUNT = 8, 6   # pm fwd/bwd, cost fwd/bwd, init fwd/bwd
+
+
+class PGMError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (where, STATUS.get(code, "?"), code))
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpgm.so (built by paper_1704_03217_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libpgm.so not built (%s); run paper_1704_03217_gb300.build" % path)
+    L = C.CDLL(path)
+    P = C.POINTER(CParams)
+    vp, sz, i32, i64, u64 = C.c_void_p, C.c_size_t, C.c_int, C.c_int64, C.c_uint64
+    pi, psz = C.POINTER(C.c_int), C.POINTER(C.c_size_t)
+    L.pgm_default_params.argtypes = [P]; L.pgm_default_params.restype = None
+    L.pgm_status_string.argtypes = [i32]; L.pgm_status_string.restype = C.c_char_p
+    L.pgm_pyramid_bytes.argtypes = [P, i32, i32]; L.pgm_pyramid_bytes.restype = sz
+    L.pgm_build_pyramid.argtypes = [P, vp, i32, i32, i32, sz, vp, sz, vp]
+    L.pgm_pyramid_desc_layout.argtypes = [P, i32, i32, i32, i32, psz, pi, pi, pi, pi]
+    L.pgm_pyramid_image_layout.argtypes = [P, i32, i32, i32, i32, psz, pi, pi, pi, pi, psz]
+    L.pgm_match_workspace_bytes.argtypes = [P, i32, i32, i32, i32]
+    L.pgm_match_workspace_bytes.restype = sz
+    L.pgm_match.argtypes = [P, vp, vp, i32, i32, i32, i32, u64, vp, sz, vp]
+    L.pgm_match_batch.argtypes = [P, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int32),
+                                  C.POINTER(u64), C.POINTER(vp), psz, vp]
+    L.pgm_field_layout.argtypes = [P, i32, i32, i32, i32, i32, i32, pi, pi, psz, psz, psz]
+    L.pgm_filter.argtypes = [P, i32, i32, i32, i32, vp, sz, vp, i64, vp, vp, vp]
+    L.pgm_sync_status.argtypes = [P, i32, i32, i32, i32, vp, sz, vp]
+    L.pgm_nominal_evals.argtypes = [P, i32, i32, i32, i32]; L.pgm_nominal_evals.restype = i64
+    L.pgm_launch_count.argtypes = []; L.pgm_launch_count.restype = i64
+    L.pgm_profile_enable.argtypes = [i32]; L.pgm_profile_enable.restype = C.c_int
+    L.pgm_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.pgm_profile_read.restype = C.c_int
+    for name in ("pgm_build_pyramid", "pgm_pyramid_desc_layout", "pgm_pyramid_image_layout",
+                 "pgm_match", "pgm_match_batch", "pgm_field_layout", "pgm_filter",
+                 "pgm_sync_status"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def check(code, where):
+    if code != 0:
+        raise PGMError(code, where)

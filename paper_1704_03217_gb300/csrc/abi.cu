@@ -1,0 +1,517 @@
+// abi.cu -- the extern "C" entry points of libpgm: argument checks, buffer
+// layouts (plans), the visit schedule of Fig. 5 and the launch sequence.
+#include <string.h>
+
+#include <atomic>
+#include <vector>
+
+#include "pgm_device.cuh"
+
+namespace pgm {
+
+// ------------------------------------------------------ launch accounting
+static std::atomic<long long> g_launches{0};
+
+namespace {
+struct ProfEvent { int cls; int n; cudaEvent_t a, b; };
+struct ProfState {
+    bool on = false;
+    std::vector<ProfEvent> open;          // recorded, not yet read
+    std::vector<cudaEvent_t> pool;
+    double ms[PGM_K_COUNT] = {0};
+    long long launches[PGM_K_COUNT] = {0};
+};
+thread_local ProfState g_prof;
+
+cudaEvent_t take_event() {
+    if (!g_prof.pool.empty()) {
+        cudaEvent_t e = g_prof.pool.back();
+        g_prof.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+}  // namespace
+
+KScope::KScope(int c, cudaStream_t s, int nl) : cls(c), st(s), n(nl), slot(-1) {
+    if (!g_prof.on) return;
+    cudaEvent_t a = take_event(), b = take_event();
+    if (!a || !b) return;
+    cudaEventRecord(a, st);
+    g_prof.open.push_back({cls, n, a, b});
+    slot = (int)g_prof.open.size() - 1;
+}
+
+KScope::~KScope() {
+    g_launches.fetch_add(n, std::memory_order_relaxed);
+    if (slot >= 0 && slot < (int)g_prof.open.size()) cudaEventRecord(g_prof.open[slot].b, st);
+}
+
+pgm_status check_params(const pgm_params* p) {
+    if (!p) return PGM_ERR_ARG;
+    if (p->levels < 1 || p->levels > MAXL) return PGM_ERR_ARG;
+    if (p->seed_stride < 1 || p->seed_stride > 64) return PGM_ERR_ARG;
+    if (p->patch_fwd < 1 || p->patch_bwd < 1) return PGM_ERR_ARG;
+    if (p->patch_fwd > MAXP || p->patch_bwd > MAXP) return PGM_ERR_UNSUPPORTED;
+    if (p->sobel != 3 && p->sobel != 5) return PGM_ERR_ARG;
+    if (p->color != PGM_GRAY && p->color != PGM_RGB) return PGM_ERR_ARG;
+    if (p->descriptor != PGM_FULL && p->descriptor != PGM_DIR) return PGM_ERR_ARG;
+    if (p->cs_sched != PGM_CS_PAPER && p->cs_sched != PGM_CS_PLAIN) return PGM_ERR_ARG;
+    if (p->norm != PGM_L2SQ && p->norm != PGM_L1) return PGM_ERR_ARG;
+    if (p->iters_coarse < 0 || p->iters_fine < 0 || p->iters_coarse > 32767 ||
+        p->iters_fine > 32767) return PGM_ERR_ARG;
+    if (p->refine_rounds < 0 || p->refine_rounds > 64) return PGM_ERR_ARG;
+    if (p->rs_W < 1 || p->rs_W > (1 << 14)) return PGM_ERR_ARG;
+    if (p->rs_mode != PGM_RS_SYMMETRIC && p->rs_mode != PGM_RS_PAPER_FLOOR) return PGM_ERR_ARG;
+    if (p->tau2 < 0 || p->min_region < 0 || p->region_dmax2 < 0 || p->max_visits < 0)
+        return PGM_ERR_ARG;
+    if (p->ablation < 0 || p->ablation > 7 || p->reserved != 0) return PGM_ERR_ARG;
+    return PGM_OK;
+}
+
+// Table 2 read with period 3 for deeper pyramids; scheme 0 forward, 1 backward
+static int space_of(const pgm_params* p, int scheme, int level) {
+    if (p->color == PGM_GRAY) return SP_GRAY;
+    if (p->cs_sched == PGM_CS_PLAIN) return SP_RGB;
+    static const int fwd[3] = {SP_RGB, SP_LAB, SP_YCRCB};
+    static const int bwd[3] = {SP_LAB, SP_YCRCB, SP_RGB};
+    return scheme == 0 ? fwd[level % 3] : bwd[level % 3];
+}
+
+bool make_pyr_plan(const pgm_params* p, int w, int h, PyrPlan* pp) {
+    if (check_params(p) != PGM_OK || w < 1 || h < 1 || w > 32767 || h > 32767) return false;
+    memset(pp, 0, sizeof(*pp));
+    pp->L = p->levels;
+    pp->C = p->color == PGM_RGB ? 3 : 1;
+    pp->nch = 2 * pp->C;
+    pp->nsch = (p->color == PGM_RGB && p->cs_sched == PGM_CS_PAPER) ? 2 : 1;
+    size_t off = 0;
+    for (int l = 0; l < pp->L; ++l) {
+        pp->W[l] = l == 0 ? w : (pp->W[l - 1] + 1) / 2;
+        pp->H[l] = l == 0 ? h : (pp->H[l - 1] + 1) / 2;
+        pp->img_row[l] = (int)align_up(pp->W[l], 16);
+        pp->img_plane[l] = (size_t)pp->img_row[l] * pp->H[l];
+        pp->img_off[l] = off;
+        off = align_up(off + pp->img_plane[l] * pp->C, 256);
+        pp->desc_row[l] = (int)align_up((size_t)pp->W[l] * pp->nch, 8);
+    }
+    for (int s = 0; s < pp->nsch; ++s)
+        for (int l = 0; l < pp->L; ++l) {
+            int sp = space_of(p, s, l);
+            pp->space[s][l] = sp;
+            if (sp == SP_LAB || sp == SP_YCRCB) {
+                pp->cimg_off[s][l] = off;
+                off = align_up(off + pp->img_plane[l] * pp->C, 256);
+            } else {
+                pp->cimg_off[s][l] = pp->img_off[l];
+            }
+            pp->desc_off[s][l] = off;
+            off = align_up(off + (size_t)pp->desc_row[l] * pp->H[l] * 2, 256);
+        }
+    for (int s = pp->nsch; s < 2; ++s)
+        for (int l = 0; l < pp->L; ++l) {
+            pp->space[s][l] = pp->space[0][l];
+            pp->cimg_off[s][l] = pp->cimg_off[0][l];
+            pp->desc_off[s][l] = pp->desc_off[0][l];
+        }
+    pp->bytes = off + 256;     // tail slack: vector loads never leave the buffer
+    return true;
+}
+
+bool make_ws_plan(const pgm_params* p, int w1, int h1, int w2, int h2, WsPlan* wp) {
+    PyrPlan a, b;
+    if (!make_pyr_plan(p, w1, h1, &a) || !make_pyr_plan(p, w2, h2, &b)) return false;
+    memset(wp, 0, sizeof(*wp));
+    wp->L = p->levels;
+    size_t off = 256;          // [0, 256): status word
+    wp->off_err = 0;
+    for (int l = 0; l < wp->L; ++l)
+        for (int d = 0; d < 2; ++d) {
+            const PyrPlan& r = d == 0 ? a : b;
+            int nx = lattice_n(r.W[l], p->seed_stride), ny = lattice_n(r.H[l], p->seed_stride);
+            wp->nx[l][d] = nx; wp->ny[l][d] = ny;
+            size_t n = (size_t)nx * ny;
+            wp->off_u[l][d] = off;     off = align_up(off + 4 * n, 256);
+            wp->off_cost[l][d] = off;  off = align_up(off + 8 * n, 256);
+            wp->off_flags[l][d] = off; off = align_up(off + n, 256);
+        }
+    size_t n0 = (size_t)wp->nx[0][0] * wp->ny[0][0];
+    wp->nblk0 = (int)((n0 + 255) / 256);
+    wp->off_label = off; off = align_up(off + 4 * n0, 256);
+    wp->off_size = off;  off = align_up(off + 4 * n0, 256);
+    wp->off_bsum = off;  off = align_up(off + 4 * (size_t)wp->nblk0 + 4, 256);
+    wp->bytes = off;
+    return true;
+}
+
+// Fig. 5 for general L (m = L-1): m (init); [m-1, m] x N with field and
+// outlier record; m-1 with the field only; then m-2 .. 0 with both.
+void make_schedule(const pgm_params* p, Schedule* s) {
+    const int m = p->levels - 1;
+    const int N = (p->ablation & PGM_ABL_NO_REFINE) ? 0 : p->refine_rounds;
+    int n = 0;
+    s->level[n] = m; s->with_o[n] = 0; ++n;
+    if (m > 0) {
+        for (int r = 0; r < N; ++r) {
+            s->level[n] = m - 1; s->with_o[n] = 1; ++n;
+            s->level[n] = m; s->with_o[n] = 1; ++n;
+        }
+        s->level[n] = m - 1; s->with_o[n] = 0; ++n;
+        for (int l = m - 2; l >= 0; --l) { s->level[n] = l; s->with_o[n] = 1; ++n; }
+    }
+    if (p->ablation & PGM_ABL_NO_OUTLIER_PROP)
+        for (int v = 0; v < n; ++v) s->with_o[v] = 0;
+    if (p->max_visits > 0 && p->max_visits < n) n = p->max_visits;
+    s->n = n;
+}
+
+namespace {
+
+struct PairCtx {
+    PyrPlan a, b;
+    WsPlan w;
+    const uint8_t* pyr1; const uint8_t* pyr2;
+    uint8_t* ws;
+    uint32_t stream_id;
+};
+
+void fill_dir(const pgm_params* p, const PairCtx& c, int l, int d, DirLvl* D) {
+    const PyrPlan& R = d == 0 ? c.a : c.b;     // reference image's pyramid
+    const PyrPlan& T = d == 0 ? c.b : c.a;
+    const uint8_t* rp = d == 0 ? c.pyr1 : c.pyr2;
+    const uint8_t* tp = d == 0 ? c.pyr2 : c.pyr1;
+    int s = d < R.nsch ? d : R.nsch - 1;
+    D->ref = reinterpret_cast<const int16_t*>(rp + R.desc_off[s][l]);
+    D->tgt = reinterpret_cast<const int16_t*>(tp + T.desc_off[s][l]);
+    D->ref_pitch = R.desc_row[l]; D->tgt_pitch = T.desc_row[l];
+    D->rw = R.W[l]; D->rh = R.H[l]; D->tw = T.W[l]; D->th = T.H[l];
+    D->nx = c.w.nx[l][d]; D->ny = c.w.ny[l][d];
+    D->onx = c.w.nx[l][1 - d]; D->ony = c.w.ny[l][1 - d];
+    D->P = d == 0 ? p->patch_fwd : p->patch_bwd;
+    D->pad = 0;
+    D->u = reinterpret_cast<int32_t*>(c.ws + c.w.off_u[l][d]);
+    D->cost = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_cost[l][d]);
+    D->flags = c.ws + c.w.off_flags[l][d];
+    D->ou = reinterpret_cast<const int32_t*>(c.ws + c.w.off_u[l][1 - d]);
+    D->oflags = c.ws + c.w.off_flags[l][1 - d];
+}
+
+pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) {
+    Schedule sch;
+    make_schedule(p, &sch);
+    const int nch = ctx[0].a.nch;
+    const int maxP = p->patch_fwd > p->patch_bwd ? p->patch_fwd : p->patch_bwd;
+    MatchConst mc;
+    memset(&mc, 0, sizeof(mc));
+    mc.sigma = p->seed_stride; mc.c = p->seed_stride / 2;
+    mc.norm = p->norm; mc.rs_W = p->rs_W; mc.rs_mode = p->rs_mode; mc.K = rs_count(p->rs_W);
+    mc.key0 = (uint32_t)(p->philox_key & 0xffffffffu); mc.key1 = (uint32_t)(p->philox_key >> 32);
+    mc.tau2 = p->tau2;
+    static thread_local LvlBatch B;       // ~8 KB: kept off the stack
+    static thread_local XferBatch X;
+    for (int k = 0; k < n; ++k)           // reset the evaluation counters
+        if (cudaMemsetAsync(ctx[k].ws + PGM_WS_EVALS_OFFSET, 0, 8 * PGM_WS_EVALS_COUNT, st) != cudaSuccess)
+            return PGM_ERR_CUDA;
+    for (int v = 0; v < sch.n; ++v) {
+        const int l = sch.level[v];
+        memset(&B, 0, sizeof(B));
+        B.n = n; B.level = l; B.visit = v;
+        int max_seeds = 0, max_half = 0;
+        for (int k = 0; k < n; ++k) {
+            for (int d = 0; d < 2; ++d) {
+                fill_dir(p, ctx[k], l, d, &B.d[k][d]);
+                int ns = B.d[k][d].nx * B.d[k][d].ny;
+                int nh = ((B.d[k][d].nx + 1) / 2) * B.d[k][d].ny;
+                if (ns > max_seeds) max_seeds = ns;
+                if (nh > max_half) max_half = nh;
+            }
+            B.stream_id[k] = ctx[k].stream_id;
+            B.evals[k] = reinterpret_cast<unsigned long long*>(ctx[k].ws + PGM_WS_EVALS_OFFSET);
+        }
+        pgm_status r;
+        if (v == 0) {
+            r = launch_init(B, mc, nch, maxP, max_seeds, st);
+        } else {
+            const int src = sch.level[v - 1];
+            memset(&X, 0, sizeof(X));
+            X.n = n; X.up = l == src + 1; X.with_o = sch.with_o[v];
+            X.prop_all = (p->ablation & PGM_ABL_PROPAGATE_ALL) ? 1 : 0;
+            for (int k = 0; k < n; ++k)
+                for (int d = 0; d < 2; ++d) {
+                    const WsPlan& w = ctx[k].w;
+                    XferDir& T = X.d[k][d];
+                    T.su = reinterpret_cast<const int32_t*>(ctx[k].ws + w.off_u[src][d]);
+                    T.sflags = ctx[k].ws + w.off_flags[src][d];
+                    T.snx = w.nx[src][d]; T.sny = w.ny[src][d];
+                    T.du = reinterpret_cast<int32_t*>(ctx[k].ws + w.off_u[l][d]);
+                    T.dcost = reinterpret_cast<unsigned long long*>(ctx[k].ws + w.off_cost[l][d]);
+                    T.dflags = ctx[k].ws + w.off_flags[l][d];
+                    T.dnx = w.nx[l][d]; T.dny = w.ny[l][d];
+                }
+            r = launch_transfer(X, max_seeds, st);
+        }
+        if (r != PGM_OK) return r;
+        r = launch_cost_fill(B, mc, nch, maxP, max_seeds, st);
+        if (r != PGM_OK) return r;
+        const int T = l == 0 ? p->iters_fine : p->iters_coarse;
+        for (int t = 0; t < T; ++t)
+            for (int col = 0; col < 2; ++col) {
+                mc.t = t; mc.colour = col;
+                r = launch_pm_phase(B, mc, nch, maxP, max_half, st);
+                if (r != PGM_OK) return r;
+            }
+        mc.t = 0; mc.colour = 0;
+        r = launch_consist(B, mc, max_seeds, st);
+        if (r != PGM_OK) return r;
+    }
+    return PGM_OK;
+}
+
+pgm_status prepare_pair(const pgm_params* p, const void* pyr1, const void* pyr2, int w1, int h1,
+                        int w2, int h2, uint64_t sid, void* ws, size_t ws_bytes, PairCtx* c) {
+    if (!pyr1 || !pyr2 || !ws) return PGM_ERR_ARG;
+    if (w1 < 1 || h1 < 1 || w2 < 1 || h2 < 1 || w1 > 32767 || h1 > 32767 || w2 > 32767 ||
+        h2 > 32767) return PGM_ERR_SIZE;
+    if (!make_pyr_plan(p, w1, h1, &c->a) || !make_pyr_plan(p, w2, h2, &c->b) ||
+        !make_ws_plan(p, w1, h1, w2, h2, &c->w)) return PGM_ERR_ARG;
+    if (ws_bytes < c->w.bytes) return PGM_ERR_WORKSPACE;
+    if (((uintptr_t)pyr1 | (uintptr_t)pyr2 | (uintptr_t)ws) & 255u) return PGM_ERR_ARG;
+    for (int l = 0; l < p->levels; ++l)
+        for (int d = 0; d < 2; ++d)
+            if (c->w.nx[l][d] < 1 || c->w.ny[l][d] < 1) return PGM_ERR_SIZE;
+    const int m = p->levels - 1;
+    // exhaustive init: target raster index and cost are packed into 24 + 40 bits
+    if ((long long)c->a.W[m] * c->a.H[m] >= (1LL << 24) ||
+        (long long)c->b.W[m] * c->b.H[m] >= (1LL << 24)) return PGM_ERR_UNSUPPORTED;
+    c->pyr1 = static_cast<const uint8_t*>(pyr1);
+    c->pyr2 = static_cast<const uint8_t*>(pyr2);
+    c->ws = static_cast<uint8_t*>(ws);
+    c->stream_id = (uint32_t)sid;
+    return PGM_OK;
+}
+
+}  // namespace
+}  // namespace pgm
+
+using namespace pgm;
+
+extern "C" {
+
+void pgm_default_params(pgm_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->levels = 3; p->seed_stride = 3; p->patch_fwd = 15; p->patch_bwd = 11; p->sobel = 5;
+    p->color = PGM_RGB; p->descriptor = PGM_FULL; p->cs_sched = PGM_CS_PAPER; p->norm = PGM_L2SQ;
+    p->iters_coarse = 4; p->iters_fine = 6; p->refine_rounds = 2; p->rs_W = 2;
+    p->rs_mode = PGM_RS_SYMMETRIC; p->tau2 = 1; p->min_region = 9; p->region_dmax2 = 144;
+    p->max_visits = 0; p->ablation = 0; p->reserved = 0;
+    p->philox_key = 0x5EED5EED1234ABCDull;
+}
+
+const char* pgm_status_string(pgm_status s) {
+    switch (s) {
+    case PGM_OK: return "ok";
+    case PGM_ERR_ARG: return "invalid argument";
+    case PGM_ERR_SIZE: return "image too small for the pyramid or seed lattice";
+    case PGM_ERR_WORKSPACE: return "buffer smaller than required";
+    case PGM_ERR_CUDA: return "CUDA error";
+    case PGM_ERR_TIMEOUT: return "device wait timed out";
+    case PGM_ERR_DEVICE_BOUNDS: return "device-side bounds check failed";
+    case PGM_ERR_UNSUPPORTED: return "outside this build's limits";
+    }
+    return "unknown status";
+}
+
+size_t pgm_pyramid_bytes(const pgm_params* p, int w, int h) {
+    PyrPlan pp;
+    return make_pyr_plan(p, w, h, &pp) ? pp.bytes : 0;
+}
+
+pgm_status pgm_build_pyramid(const pgm_params* p, const uint8_t* d_img, int w, int h, int c,
+                             size_t pitch, void* d_pyr, size_t pyr_bytes, void* stream) {
+    pgm_status r = check_params(p);
+    if (r != PGM_OK) return r;
+    if (!d_img || !d_pyr || (c != 1 && c != 3) || (p->color == PGM_RGB && c != 3))
+        return PGM_ERR_ARG;
+    if (w < 1 || h < 1 || w > 32767 || h > 32767) return PGM_ERR_SIZE;
+    if (pitch < (size_t)w * c || ((uintptr_t)d_pyr & 255u)) return PGM_ERR_ARG;
+    PyrPlan pp;
+    if (!make_pyr_plan(p, w, h, &pp)) return PGM_ERR_ARG;
+    if (pyr_bytes < pp.bytes) return PGM_ERR_WORKSPACE;
+    return launch_pyramid(p, pp, d_img, c, pitch, static_cast<uint8_t*>(d_pyr),
+                          static_cast<cudaStream_t>(stream));
+}
+
+pgm_status pgm_pyramid_desc_layout(const pgm_params* p, int w, int h, int scheme, int level,
+                                   size_t* offset_bytes, int* lw, int* lh, int* nch,
+                                   int* row_elems) {
+    PyrPlan pp;
+    if (!make_pyr_plan(p, w, h, &pp) || scheme < 0 || scheme > 1 || level < 0 ||
+        level >= pp.L || !offset_bytes || !lw || !lh || !nch || !row_elems) return PGM_ERR_ARG;
+    *offset_bytes = pp.desc_off[scheme][level];
+    *lw = pp.W[level]; *lh = pp.H[level]; *nch = pp.nch; *row_elems = pp.desc_row[level];
+    return PGM_OK;
+}
+
+pgm_status pgm_pyramid_image_layout(const pgm_params* p, int w, int h, int scheme, int level,
+                                    size_t* offset_bytes, int* lw, int* lh, int* channels,
+                                    int* row_bytes, size_t* plane_bytes) {
+    PyrPlan pp;
+    if (!make_pyr_plan(p, w, h, &pp) || scheme < 0 || scheme > 1 || level < 0 ||
+        level >= pp.L || !offset_bytes || !lw || !lh || !channels || !row_bytes || !plane_bytes)
+        return PGM_ERR_ARG;
+    *offset_bytes = pp.cimg_off[scheme][level];
+    *lw = pp.W[level]; *lh = pp.H[level]; *channels = pp.C;
+    *row_bytes = pp.img_row[level]; *plane_bytes = pp.img_plane[level];
+    return PGM_OK;
+}
+
+size_t pgm_match_workspace_bytes(const pgm_params* p, int w1, int h1, int w2, int h2) {
+    WsPlan wp;
+    return make_ws_plan(p, w1, h1, w2, h2, &wp) ? wp.bytes : 0;
+}
+
+pgm_status pgm_match(const pgm_params* p, const void* d_pyr1, const void* d_pyr2, int w1, int h1,
+                     int w2, int h2, uint64_t stream_id, void* d_ws, size_t ws_bytes,
+                     void* stream) {
+    pgm_status r = check_params(p);
+    if (r != PGM_OK) return r;
+    static thread_local PairCtx c;
+    r = prepare_pair(p, d_pyr1, d_pyr2, w1, h1, w2, h2, stream_id, d_ws, ws_bytes, &c);
+    if (r != PGM_OK) return r;
+    return run_batch(p, &c, 1, static_cast<cudaStream_t>(stream));
+}
+
+pgm_status pgm_match_batch(const pgm_params* p, int n, const void* const* d_pyr1,
+                           const void* const* d_pyr2, const int32_t* dims,
+                           const uint64_t* stream_ids, void* const* d_ws,
+                           const size_t* ws_bytes, void* stream) {
+    pgm_status r = check_params(p);
+    if (r != PGM_OK) return r;
+    if (n < 0 || (n > 0 && (!d_pyr1 || !d_pyr2 || !dims || !stream_ids || !d_ws || !ws_bytes)))
+        return PGM_ERR_ARG;
+    static thread_local PairCtx ctx[MAXB];
+    for (int base = 0; base < n; base += MAXB) {      // validate everything first
+        int m = n - base < MAXB ? n - base : MAXB;
+        for (int k = 0; k < m; ++k) {
+            int i = base + k;
+            r = prepare_pair(p, d_pyr1[i], d_pyr2[i], dims[4 * i], dims[4 * i + 1],
+                             dims[4 * i + 2], dims[4 * i + 3], stream_ids[i], d_ws[i],
+                             ws_bytes[i], &ctx[k]);
+            if (r != PGM_OK) return r;
+        }
+    }
+    for (int base = 0; base < n; base += MAXB) {
+        int m = n - base < MAXB ? n - base : MAXB;
+        for (int k = 0; k < m; ++k) {
+            int i = base + k;
+            prepare_pair(p, d_pyr1[i], d_pyr2[i], dims[4 * i], dims[4 * i + 1], dims[4 * i + 2],
+                         dims[4 * i + 3], stream_ids[i], d_ws[i], ws_bytes[i], &ctx[k]);
+        }
+        r = run_batch(p, ctx, m, static_cast<cudaStream_t>(stream));
+        if (r != PGM_OK) return r;
+    }
+    return PGM_OK;
+}
+
+pgm_status pgm_field_layout(const pgm_params* p, int w1, int h1, int w2, int h2, int level,
+                            int dir, int* nx, int* ny, size_t* off_u, size_t* off_cost,
+                            size_t* off_flags) {
+    WsPlan wp;
+    if (!make_ws_plan(p, w1, h1, w2, h2, &wp) || level < 0 || level >= wp.L || dir < 0 ||
+        dir > 1 || !nx || !ny || !off_u || !off_cost || !off_flags) return PGM_ERR_ARG;
+    *nx = wp.nx[level][dir]; *ny = wp.ny[level][dir];
+    *off_u = wp.off_u[level][dir]; *off_cost = wp.off_cost[level][dir];
+    *off_flags = wp.off_flags[level][dir];
+    return PGM_OK;
+}
+
+pgm_status pgm_filter(const pgm_params* p, int w1, int h1, int w2, int h2, void* d_ws,
+                      size_t ws_bytes, int32_t* d_matches, int64_t max_matches,
+                      int32_t* d_count, uint8_t* d_keep, void* stream) {
+    pgm_status r = check_params(p);
+    if (r != PGM_OK) return r;
+    if (!d_ws || !d_count || max_matches < 0 || (max_matches > 0 && !d_matches))
+        return PGM_ERR_ARG;
+    if (((uintptr_t)d_matches) & 15u) return PGM_ERR_ARG;
+    WsPlan wp;
+    if (!make_ws_plan(p, w1, h1, w2, h2, &wp)) return PGM_ERR_ARG;
+    if (ws_bytes < wp.bytes) return PGM_ERR_WORKSPACE;
+    return launch_filter(p, wp, static_cast<uint8_t*>(d_ws), d_matches, max_matches, d_count,
+                         d_keep, static_cast<cudaStream_t>(stream));
+}
+
+pgm_status pgm_sync_status(const pgm_params* p, int w1, int h1, int w2, int h2, void* d_ws,
+                           size_t ws_bytes, void* stream) {
+    pgm_status r = check_params(p);
+    if (r != PGM_OK) return r;
+    WsPlan wp;
+    if (!d_ws || !make_ws_plan(p, w1, h1, w2, h2, &wp)) return PGM_ERR_ARG;
+    if (ws_bytes < wp.bytes) return PGM_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t word = 0;
+    if (cudaMemcpyAsync(&word, static_cast<uint8_t*>(d_ws) + wp.off_err, 4,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess) return PGM_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PGM_ERR_CUDA;
+    if (word != 0) {
+        if (cudaMemsetAsync(static_cast<uint8_t*>(d_ws) + wp.off_err, 0, 4, st) != cudaSuccess)
+            return PGM_ERR_CUDA;
+        return (pgm_status)word;
+    }
+    return PGM_OK;
+}
+
+int64_t pgm_launch_count(void) { return (int64_t)g_launches.load(); }
+
+pgm_status pgm_profile_enable(int on) {
+    if (on) {
+        for (auto& e : g_prof.open) { g_prof.pool.push_back(e.a); g_prof.pool.push_back(e.b); }
+        g_prof.open.clear();
+        for (int k = 0; k < PGM_K_COUNT; ++k) { g_prof.ms[k] = 0; g_prof.launches[k] = 0; }
+        cudaEvent_t probe = take_event();
+        if (!probe) return PGM_ERR_CUDA;
+        g_prof.pool.push_back(probe);
+    }
+    g_prof.on = on != 0;
+    return PGM_OK;
+}
+
+pgm_status pgm_profile_read(double* ms, int64_t* launches) {
+    for (auto& e : g_prof.open) {
+        if (cudaEventSynchronize(e.b) != cudaSuccess) return PGM_ERR_CUDA;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, e.a, e.b) != cudaSuccess) return PGM_ERR_CUDA;
+        g_prof.ms[e.cls] += t;
+        g_prof.launches[e.cls] += e.n;
+        g_prof.pool.push_back(e.a);
+        g_prof.pool.push_back(e.b);
+    }
+    g_prof.open.clear();
+    for (int k = 0; k < PGM_K_COUNT; ++k) {
+        if (ms) ms[k] = g_prof.ms[k];
+        if (launches) launches[k] = g_prof.launches[k];
+    }
+    return PGM_OK;
+}
+
+int64_t pgm_nominal_evals(const pgm_params* p, int w1, int h1, int w2, int h2) {
+    WsPlan wp;
+    if (!make_ws_plan(p, w1, h1, w2, h2, &wp)) return -1;
+    Schedule sch;
+    make_schedule(p, &sch);
+    const int64_t per_it = 2 + rs_count(p->rs_W);
+    int64_t total = 0;
+    for (int v = 0; v < sch.n; ++v) {
+        const int l = sch.level[v];
+        const int64_t T = l == 0 ? p->iters_fine : p->iters_coarse;
+        for (int d = 0; d < 2; ++d) {
+            const int64_t ns = (int64_t)wp.nx[l][d] * wp.ny[l][d];
+            total += ns * (1 + T * per_it);
+        }
+    }
+    return total;
+}
+
+}  // extern "C"

@@ -1,0 +1,463 @@
+// match.cu -- the matching kernels of one pyramid level (Sec. III-B, III-D).
+//
+//   k_init      exhaustive nearest-neighbour initialisation at the coarsest
+//               level (the exact field the KD-tree init of Sec. III-D
+//               approximates); one CTA per seed, threads over targets.
+//   k_cost      D_r (Eq. 3) of every initialised seed's current match.
+//   k_pm        one checkerboard colour phase of propagation (Eq. 4) and
+//               limited random search (Eq. 5); one warp per seed.
+//   k_consist   forward-backward consistency + outlier-record update (Eq. 6).
+//   k_transfer  field (Eq. 7) and outlier-record (Eq. 8) propagation.
+//
+// All arithmetic is integer: descriptors are int16, a patch distance is an
+// exact uint64 sum, so the result does not depend on the reduction order.
+#include "pgm_device.cuh"
+
+namespace pgm {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned long long INF = ~0ull;
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+__device__ __forceinline__ int lo16(uint32_t v) { return (int)(int16_t)(v & 0xffffu); }
+__device__ __forceinline__ int hi16(uint32_t v) { return ((int)v) >> 16; }
+__device__ __forceinline__ int32_t pack_u(int ux, int uy) {
+    return (int32_t)(((uint32_t)ux & 0xffffu) | ((uint32_t)uy << 16));
+}
+
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products,
+// key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// offset of the k-th limited random-search candidate (Eq. 5)
+__device__ __forceinline__ int rs_off(uint32_t r, int k, int W, int mode) {
+    if (mode == PGM_RS_SYMMETRIC) {
+        int rho = max(1, W >> k);
+        return (int)(((unsigned long long)r * (unsigned long long)(2 * rho + 1)) >> 32) - rho;
+    }
+    long long num = ((long long)r * 2 - 4294967295LL) * (long long)W;
+    return (int)(num >> (32 + k));      // arithmetic shift = floor division by 2^(32+k)
+}
+
+// ------------------------------------------------------------------
+// Warp-cooperative patch distance.  Lane l holds patch pixels l, l+32, ...
+// (row-major in the P x P patch) of the reference, NCH channels each.
+template <int NCH, int PPL>
+struct Ref {
+    int a[PPL][NCH];
+    int ox[PPL], oy[PPL];
+};
+
+template <int NCH, int PPL>
+__device__ __forceinline__ void load_ref(Ref<NCH, PPL>& R, const DirLvl& D, int px, int py,
+                                         int lane) {
+    const int P = D.P, h = P / 2;
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+        int k = lane + 32 * m;
+        int kk = k < P * P ? k : 0;
+        R.ox[m] = kk % P - h;
+        R.oy[m] = kk / P - h;
+        int x = clampi(px + R.ox[m], 0, D.rw - 1), y = clampi(py + R.oy[m], 0, D.rh - 1);
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(D.ref + (size_t)y * D.ref_pitch +
+                                                              (size_t)x * NCH);
+#pragma unroll
+        for (int c = 0; c < NCH / 2; ++c) {
+            uint32_t v = (k < P * P) ? __ldg(w + c) : 0u;
+            R.a[m][2 * c] = lo16(v);
+            R.a[m][2 * c + 1] = hi16(v);
+        }
+    }
+}
+
+template <int NCH, int PPL, int NORM>
+__device__ __forceinline__ unsigned long long warp_cost(const Ref<NCH, PPL>& R, const DirLvl& D,
+                                                        int qx, int qy, int lane) {
+    const int P2 = D.P * D.P;
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+        if (lane + 32 * m < P2) {
+            int x = clampi(qx + R.ox[m], 0, D.tw - 1), y = clampi(qy + R.oy[m], 0, D.th - 1);
+            const uint32_t* w = reinterpret_cast<const uint32_t*>(
+                D.tgt + (size_t)y * D.tgt_pitch + (size_t)x * NCH);
+            uint32_t s = 0;
+#pragma unroll
+            for (int c = 0; c < NCH / 2; ++c) {
+                uint32_t v = __ldg(w + c);
+                int d0 = lo16(v) - R.a[m][2 * c], d1 = hi16(v) - R.a[m][2 * c + 1];
+                if (NORM == PGM_L2SQ) s += (uint32_t)(d0 * d0) + (uint32_t)(d1 * d1);
+                else s += (uint32_t)(abs(d0) + abs(d1));
+            }
+            acc += s;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    return acc;
+}
+
+__device__ __forceinline__ bool inside(const DirLvl& D, int qx, int qy) {
+    return qx >= 0 && qy >= 0 && qx < D.tw && qy < D.th;
+}
+
+// ---------------------------------------------------------------- init
+template <int NCH, int NORM>
+__global__ void __launch_bounds__(256) k_init(const __grid_constant__ LvlBatch B, const MatchConst mc) {
+    const int pair = blockIdx.z, dir = blockIdx.y;
+    const DirLvl& D = B.d[pair][dir];
+    const int s = blockIdx.x;
+    if (s >= D.nx * D.ny) return;
+    __shared__ int ref[MAXP * MAXP][NCH];
+    __shared__ unsigned long long red[8];
+    const int i = s % D.nx, j = s / D.nx;
+    const int px = mc.c + mc.sigma * i, py = mc.c + mc.sigma * j;
+    const int P = D.P, h = P / 2, P2 = P * P;
+    for (int k = threadIdx.x; k < P2; k += blockDim.x) {
+        int x = clampi(px + k % P - h, 0, D.rw - 1), y = clampi(py + k / P - h, 0, D.rh - 1);
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(D.ref + (size_t)y * D.ref_pitch +
+                                                              (size_t)x * NCH);
+#pragma unroll
+        for (int c = 0; c < NCH / 2; ++c) {
+            uint32_t v = __ldg(w + c);
+            ref[k][2 * c] = lo16(v);
+            ref[k][2 * c + 1] = hi16(v);
+        }
+    }
+    __syncthreads();
+    unsigned long long best = INF;
+    const int nq = D.tw * D.th;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        const int qx = q % D.tw, qy = q / D.tw;
+        unsigned long long cost = 0;
+        for (int oy = 0; oy < P; ++oy) {
+            const int y = clampi(qy + oy - h, 0, D.th - 1);
+            const int16_t* row = D.tgt + (size_t)y * D.tgt_pitch;
+            for (int ox = 0; ox < P; ++ox) {
+                const int x = clampi(qx + ox - h, 0, D.tw - 1);
+                const uint32_t* w = reinterpret_cast<const uint32_t*>(row + (size_t)x * NCH);
+                const int* r = ref[oy * P + ox];
+                uint32_t sacc = 0;
+#pragma unroll
+                for (int c = 0; c < NCH / 2; ++c) {
+                    uint32_t v = __ldg(w + c);
+                    int d0 = lo16(v) - r[2 * c], d1 = hi16(v) - r[2 * c + 1];
+                    if (NORM == PGM_L2SQ) sacc += (uint32_t)(d0 * d0) + (uint32_t)(d1 * d1);
+                    else sacc += (uint32_t)(abs(d0) + abs(d1));
+                }
+                cost += sacc;
+            }
+        }
+        // ties: lower cost, then smaller target raster index (y, then x)
+        unsigned long long key = (cost << 24) | (unsigned long long)q;
+        best = key < best ? key : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(FULL, best, o);
+        best = v < best ? v : best;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(B.evals[pair] + 4 + dir, (unsigned long long)nq);
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = red[w] < best ? red[w] : best;
+        const int q = (int)(best & 0xffffffull);
+        D.u[s] = pack_u(q % D.tw - px, q / D.tw - py);
+        D.cost[s] = best >> 24;
+        D.flags[s] = F_VALID;
+    }
+}
+
+// ---------------------------------------------------------- cost fill
+template <int NCH, int PPL, int NORM>
+__global__ void __launch_bounds__(256) k_cost(const __grid_constant__ LvlBatch B, const MatchConst mc) {
+    const int pair = blockIdx.z, dir = blockIdx.y;
+    const DirLvl& D = B.d[pair][dir];
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (s >= D.nx * D.ny) return;
+    const uint8_t f = D.flags[s];
+    if (!(f & F_VALID)) return;
+    const int i = s % D.nx, j = s / D.nx;
+    const int px = mc.c + mc.sigma * i, py = mc.c + mc.sigma * j;
+    const int32_t u = D.u[s];
+    const int qx = px + lo16(u), qy = py + hi16(u);
+    if (!inside(D, qx, qy)) {            // match centre left the target image
+        if (lane == 0) D.flags[s] = f & ~F_VALID;
+        return;
+    }
+    Ref<NCH, PPL> R;
+    load_ref(R, D, px, py, lane);
+    unsigned long long c = warp_cost<NCH, PPL, NORM>(R, D, qx, qy, lane);
+    if (lane == 0) { D.cost[s] = c; atomicAdd(B.evals[pair] + 2 + dir, 1ull); }
+}
+
+// ------------------------------------------------------ PatchMatch phase
+// Seeds of colour (i + j) & 1 == mc.colour update from the current field;
+// all their lattice neighbours have the other colour and stay fixed.
+template <int NCH, int PPL, int NORM>
+__global__ void __launch_bounds__(256) k_pm(const __grid_constant__ LvlBatch B, const MatchConst mc) {
+    const int pair = blockIdx.z, dir = blockIdx.y;
+    const DirLvl& D = B.d[pair][dir];
+    const int lane = threadIdx.x & 31;
+    const int wid = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int hw = (D.nx + 1) >> 1;
+    if (wid >= hw * D.ny) return;
+    const int j = wid / hw;
+    const int i = 2 * (wid - j * hw) + ((j + mc.colour) & 1);
+    if (i >= D.nx) return;
+    const int s = j * D.nx + i;
+    const int px = mc.c + mc.sigma * i, py = mc.c + mc.sigma * j;
+
+    const uint8_t f0 = D.flags[s];
+    bool have = f0 & F_VALID;
+    int32_t bu = D.u[s];
+    unsigned long long bc = have ? D.cost[s] : INF;
+    const int32_t u_in = bu;
+    const bool have_in = have;
+
+    // propagation direction of iteration t: (+,+), (-,-), (-,+), (+,-)
+    const int t4 = mc.t & 3;
+    const int sx = (t4 == 0 || t4 == 3) ? 1 : -1;
+    const int sy = (t4 == 0 || t4 == 2) ? 1 : -1;
+
+    Ref<NCH, PPL> R;
+    bool loaded = false;
+    unsigned n_eval = 0;
+    // Eq. 4: candidates u(p - dx), u(p - dy) (displacement form)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int ni = k == 0 ? i - sx : i, nj = k == 0 ? j : j - sy;
+        if (ni < 0 || nj < 0 || ni >= D.nx || nj >= D.ny) continue;
+        const int ns = nj * D.nx + ni;
+        if (!(D.flags[ns] & F_VALID)) continue;
+        const int32_t cu = D.u[ns];
+        if (have && cu == bu) continue;                 // same match, same cost
+        const int qx = px + lo16(cu), qy = py + hi16(cu);
+        if (!inside(D, qx, qy)) continue;
+        if (!loaded) { load_ref(R, D, px, py, lane); loaded = true; }
+        const unsigned long long c = warp_cost<NCH, PPL, NORM>(R, D, qx, qy, lane);
+        ++n_eval;
+        if (c < bc) { bc = c; bu = cu; have = true; }
+    }
+    if (!have) {
+        if (lane == 0 && n_eval) atomicAdd(B.evals[pair] + dir, (unsigned long long)n_eval);
+        return;
+    }
+    // Eq. 5: K candidates around the post-propagation match
+    const int ux0 = lo16(bu), uy0 = hi16(bu);
+    uint4 r = make_uint4(0, 0, 0, 0);
+    for (int k = 0; k < mc.K; ++k) {
+        if ((k & 1) == 0) {
+            uint4 ctr = make_uint4((uint32_t)s,
+                                   ((uint32_t)B.visit << 16) | ((uint32_t)dir << 15) | (uint32_t)mc.t,
+                                   ((uint32_t)B.level << 16) | (uint32_t)(k >> 1),
+                                   B.stream_id[pair]);
+            r = philox(ctr, mc.key0, mc.key1);
+        }
+        const uint32_t rx = (k & 1) ? r.z : r.x, ry = (k & 1) ? r.w : r.y;
+        const int dx = rs_off(rx, k, mc.rs_W, mc.rs_mode), dy = rs_off(ry, k, mc.rs_W, mc.rs_mode);
+        if (dx == 0 && dy == 0) continue;
+        const int cx = ux0 + dx, cy = uy0 + dy;
+        const int qx = px + cx, qy = py + cy;
+        if (!inside(D, qx, qy)) continue;
+        if (!loaded) { load_ref(R, D, px, py, lane); loaded = true; }
+        const unsigned long long c = warp_cost<NCH, PPL, NORM>(R, D, qx, qy, lane);
+        ++n_eval;
+        if (c < bc) { bc = c; bu = pack_u(cx, cy); }
+    }
+    if (lane == 0 && n_eval) atomicAdd(B.evals[pair] + dir, (unsigned long long)n_eval);
+    if (lane == 0 && (bu != u_in || !have_in)) {
+        D.u[s] = bu;
+        D.cost[s] = bc;
+        D.flags[s] = f0 | F_VALID;
+    }
+}
+
+// ------------------------------------------------------- consistency
+// C = yes unless both ends are initialised and |u_f(p) + u_b(q^)|^2 <= tau2,
+// q^ the seed of the other lattice nearest to q = p + u_f.  Then Eq. 6 read
+// as "outlier when either is yes": O <- O or C if O was propagated, else C.
+// Only the other direction's VALID bit and u are read; this kernel writes
+// only OUTL bits, so the two directions can be updated in one launch.
+__global__ void k_consist(const __grid_constant__ LvlBatch B, const MatchConst mc) {
+    const int pair = blockIdx.z, dir = blockIdx.y;
+    const DirLvl& D = B.d[pair][dir];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= D.nx * D.ny) return;
+    const uint8_t f = D.flags[s];
+    int out = 1;
+    if ((f & F_VALID) && D.onx > 0 && D.ony > 0) {
+        const int i = s % D.nx, j = s / D.nx;
+        const int32_t u = D.u[s];
+        const int ux = lo16(u), uy = hi16(u);
+        const int qx = mc.c + mc.sigma * i + ux, qy = mc.c + mc.sigma * j + uy;
+        int a = qx - mc.c + mc.sigma / 2, b = qy - mc.c + mc.sigma / 2;
+        a = (a >= 0 ? a : a - mc.sigma + 1) / mc.sigma;     // floor division
+        b = (b >= 0 ? b : b - mc.sigma + 1) / mc.sigma;
+        const int g = clampi(b, 0, D.ony - 1) * D.onx + clampi(a, 0, D.onx - 1);
+        if (D.oflags[g] & F_VALID) {
+            const int32_t ou = D.ou[g];
+            const int ex = ux + lo16(ou), ey = uy + hi16(ou);
+            out = (long long)ex * ex + (long long)ey * ey > (long long)mc.tau2;
+        }
+    }
+    const int o_new = (f & F_OINIT) ? (((f & F_OUTL) != 0) | out) : out;
+    D.flags[s] = (uint8_t)((f & ~F_OUTL) | (o_new ? F_OUTL : 0));
+}
+
+// ------------------------------------------------------------ transfer
+__global__ void k_transfer(const __grid_constant__ XferBatch X) {
+    const int pair = blockIdx.z, dir = blockIdx.y;
+    const XferDir& T = X.d[pair][dir];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T.dnx * T.dny) return;
+    const int x = t % T.dnx, y = t / T.dnx;
+    long long sx = 0, sy = 0;
+    int n = 0, n_inl = 0;
+    if (X.up) {                       // children {2x,2x+1} x {2y,2y+1} of the finer lattice
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                const int cx = 2 * x + a, cy = 2 * y + b;
+                if (cx >= T.snx || cy >= T.sny) continue;
+                const int cs = cy * T.snx + cx;
+                const uint8_t f = T.sflags[cs];
+                const bool inl = !(f & F_OUTL);
+                n_inl += inl;
+                if (inl || (X.prop_all && (f & F_VALID))) {
+                    const int32_t u = T.su[cs];
+                    sx += lo16(u); sy += hi16(u); ++n;
+                }
+            }
+    } else if (T.snx > 0 && T.sny > 0) {   // the parent on the coarser lattice
+        const int cs = min(y / 2, T.sny - 1) * T.snx + min(x / 2, T.snx - 1);
+        const uint8_t f = T.sflags[cs];
+        const bool inl = !(f & F_OUTL);
+        n_inl = inl;
+        if (inl || (X.prop_all && (f & F_VALID))) {
+            const int32_t u = T.su[cs];
+            sx = 2LL * lo16(u); sy = 2LL * hi16(u); n = 1;
+        }
+    }
+    int ux = 0, uy = 0;
+    if (n > 0) {
+        if (X.up) {                   // mean of the children, halved, half away from zero
+            const long long d = 2LL * n;
+            const long long ax = sx < 0 ? -sx : sx, ay = sy < 0 ? -sy : sy;
+            const long long rx = (ax + n) / d, ry = (ay + n) / d;
+            ux = (int)(sx < 0 ? -rx : rx);
+            uy = (int)(sy < 0 ? -ry : ry);
+        } else {
+            ux = (int)sx; uy = (int)sy;
+        }
+    }
+    T.du[t] = pack_u(ux, uy);
+    T.dcost[t] = INF;
+    uint8_t f = n > 0 ? F_VALID : 0;
+    if (X.with_o) f |= F_OINIT | (n_inl == 0 ? F_OUTL : 0);
+    T.dflags[t] = f;
+}
+
+// ------------------------------------------------------------ dispatch
+inline int ppl_of(int maxP) {
+    int p2 = maxP * maxP;
+    return p2 <= 32 ? 1 : p2 <= 64 ? 2 : p2 <= 128 ? 4 : 8;
+}
+
+#define PGM_DISPATCH_NCH_PPL_NORM(KERNEL, GRID, ...)                                    \
+    do {                                                                                \
+        int ppl = ppl_of(maxP);                                                         \
+        if (nch == 2) {                                                                 \
+            if (mc.norm == 0) {                                                         \
+                if (ppl == 1) KERNEL<2, 1, 0><<<GRID, 256, 0, st>>>(__VA_ARGS__);       \
+                else if (ppl == 2) KERNEL<2, 2, 0><<<GRID, 256, 0, st>>>(__VA_ARGS__);  \
+                else if (ppl == 4) KERNEL<2, 4, 0><<<GRID, 256, 0, st>>>(__VA_ARGS__);  \
+                else KERNEL<2, 8, 0><<<GRID, 256, 0, st>>>(__VA_ARGS__);                \
+            } else {                                                                    \
+                if (ppl == 1) KERNEL<2, 1, 1><<<GRID, 256, 0, st>>>(__VA_ARGS__);       \
+                else if (ppl == 2) KERNEL<2, 2, 1><<<GRID, 256, 0, st>>>(__VA_ARGS__);  \
+                else if (ppl == 4) KERNEL<2, 4, 1><<<GRID, 256, 0, st>>>(__VA_ARGS__);  \
+                else KERNEL<2, 8, 1><<<GRID, 256, 0, st>>>(__VA_ARGS__);                \
+            }                                                                           \
+        } else {                                                                        \
+            if (mc.norm == 0) {                                                         \
+                if (ppl == 1) KERNEL<6, 1, 0><<<GRID, 256, 0, st>>>(__VA_ARGS__);       \
+                else if (ppl == 2) KERNEL<6, 2, 0><<<GRID, 256, 0, st>>>(__VA_ARGS__);  \
+                else if (ppl == 4) KERNEL<6, 4, 0><<<GRID, 256, 0, st>>>(__VA_ARGS__);  \
+                else KERNEL<6, 8, 0><<<GRID, 256, 0, st>>>(__VA_ARGS__);                \
+            } else {                                                                    \
+                if (ppl == 1) KERNEL<6, 1, 1><<<GRID, 256, 0, st>>>(__VA_ARGS__);       \
+                else if (ppl == 2) KERNEL<6, 2, 1><<<GRID, 256, 0, st>>>(__VA_ARGS__);  \
+                else if (ppl == 4) KERNEL<6, 4, 1><<<GRID, 256, 0, st>>>(__VA_ARGS__);  \
+                else KERNEL<6, 8, 1><<<GRID, 256, 0, st>>>(__VA_ARGS__);                \
+            }                                                                           \
+        }                                                                               \
+    } while (0)
+
+inline pgm_status last_status() {
+    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+}
+
+}  // namespace
+
+pgm_status launch_init(const LvlBatch& B, const MatchConst& mc, int nch, int maxP, int max_seeds,
+                       cudaStream_t st) {
+    (void)maxP;
+    if (max_seeds <= 0) return PGM_OK;
+    KScope ks(PGM_K_INIT, st);
+    dim3 g(max_seeds, 2, B.n);
+    if (nch == 2) {
+        if (mc.norm == 0) k_init<2, 0><<<g, 256, 0, st>>>(B, mc);
+        else k_init<2, 1><<<g, 256, 0, st>>>(B, mc);
+    } else {
+        if (mc.norm == 0) k_init<6, 0><<<g, 256, 0, st>>>(B, mc);
+        else k_init<6, 1><<<g, 256, 0, st>>>(B, mc);
+    }
+    return last_status();
+}
+
+pgm_status launch_cost_fill(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
+                            int max_seeds, cudaStream_t st) {
+    if (max_seeds <= 0) return PGM_OK;
+    KScope ks(PGM_K_COST, st);
+    dim3 g((max_seeds + 7) / 8, 2, B.n);
+    PGM_DISPATCH_NCH_PPL_NORM(k_cost, g, B, mc);
+    return last_status();
+}
+
+pgm_status launch_pm_phase(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
+                           int max_seeds, cudaStream_t st) {
+    if (max_seeds <= 0) return PGM_OK;
+    KScope ks(PGM_K_PM, st);
+    dim3 g((max_seeds + 7) / 8, 2, B.n);   // max_seeds: half-row width x rows
+    PGM_DISPATCH_NCH_PPL_NORM(k_pm, g, B, mc);
+    return last_status();
+}
+
+pgm_status launch_consist(const LvlBatch& B, const MatchConst& mc, int max_seeds,
+                          cudaStream_t st) {
+    if (max_seeds <= 0) return PGM_OK;
+    KScope ks(PGM_K_CONSIST, st);
+    k_consist<<<dim3((max_seeds + 255) / 256, 2, B.n), 256, 0, st>>>(B, mc);
+    return last_status();
+}
+
+pgm_status launch_transfer(const XferBatch& X, int max_seeds, cudaStream_t st) {
+    if (max_seeds <= 0) return PGM_OK;
+    KScope ks(PGM_K_TRANSFER, st);
+    k_transfer<<<dim3((max_seeds + 255) / 256, 2, X.n), 256, 0, st>>>(X);
+    return last_status();
+}
+
+}  // namespace pgm

@@ -1,0 +1,136 @@
+// pgm_device.cuh -- internal declarations shared by the CUDA translation
+// units of libpgm (host plans, kernel argument blocks, launchers).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/pgm.h"
+
+namespace pgm {
+
+constexpr int MAXL = 12;         // pyramid levels supported
+constexpr int MAXB = 32;         // pairs per batched launch
+constexpr int MAXP = 16;         // largest patch side
+constexpr int MAXVIS = 4 * MAXL + 2 * 64 + 4;
+
+// seed flag bits
+constexpr uint8_t F_VALID = 1;   // field initialised at this seed
+constexpr uint8_t F_OUTL = 2;    // outlier record O^l = yes
+constexpr uint8_t F_OINIT = 4;   // O^l came with a red arrow (Eq. 6 "initialized")
+
+enum Space { SP_GRAY = 0, SP_RGB = 1, SP_LAB = 2, SP_YCRCB = 3 };
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- plans
+struct PyrPlan {
+    int L, C, nsch, nch;
+    int W[MAXL], H[MAXL];
+    size_t img_off[MAXL];        // level image, C planes of uint8
+    int img_row[MAXL];           // bytes per row
+    size_t img_plane[MAXL];      // bytes per plane
+    int space[2][MAXL];
+    size_t cimg_off[2][MAXL];    // colour-converted image (aliases img if identity)
+    size_t desc_off[2][MAXL];    // int16 descriptors, pixel-interleaved
+    int desc_row[MAXL];          // int16 elements per row
+    size_t bytes;
+};
+
+struct WsPlan {
+    int L;
+    int nx[MAXL][2], ny[MAXL][2];
+    size_t off_u[MAXL][2], off_cost[MAXL][2], off_flags[MAXL][2];
+    size_t off_err;              // uint32 device status word
+    size_t off_label, off_size, off_bsum;   // filter scratch (level-0 forward lattice)
+    int nblk0;                   // blocks of the level-0 forward lattice scan
+    size_t bytes;
+};
+
+struct Schedule {
+    int n;
+    int level[MAXVIS];
+    int with_o[MAXVIS];          // transfer into this visit carries O (Eq. 8)
+};
+
+pgm_status check_params(const pgm_params* p);
+bool make_pyr_plan(const pgm_params* p, int w, int h, PyrPlan* pp);
+bool make_ws_plan(const pgm_params* p, int w1, int h1, int w2, int h2, WsPlan* wp);
+void make_schedule(const pgm_params* p, Schedule* s);
+inline int lattice_n(int W, int sigma) {
+    int c = sigma / 2;
+    return (W - 1 - c) >= 0 ? (W - 1 - c) / sigma + 1 : 0;
+}
+inline int rs_count(int W) { int K = 0; for (int w = W; w >= 1; w >>= 1) ++K; return K; }
+
+// ------------------------------------------------------- kernel blocks
+// One direction of one pair at one level.
+struct DirLvl {
+    const int16_t* ref;          // descriptor of the reference image (this dir)
+    const int16_t* tgt;          // descriptor of the target image
+    int32_t ref_pitch, tgt_pitch;// int16 elements per row
+    int32_t rw, rh, tw, th;      // reference / target image size
+    int32_t nx, ny;              // lattice of this direction (on the reference)
+    int32_t onx, ony;            // lattice of the other direction
+    int32_t P;                   // patch side
+    int32_t pad;
+    int32_t* u;                  // packed displacement (ux low 16, uy high 16)
+    unsigned long long* cost;
+    uint8_t* flags;
+    const int32_t* ou;           // other direction: displacement
+    const uint8_t* oflags;       //                  flags
+};
+
+struct LvlBatch {
+    int32_t n;                   // pairs in this launch
+    int32_t level, visit, pad;
+    DirLvl d[MAXB][2];
+    uint32_t stream_id[MAXB];
+    unsigned long long* evals[MAXB];       // workspace header counters (include/pgm.h)
+};
+
+// One direction of one pair for the transfer between levels.
+struct XferDir {
+    const int32_t* su; const uint8_t* sflags; int32_t snx, sny;
+    int32_t* du; unsigned long long* dcost; uint8_t* dflags; int32_t dnx, dny;
+};
+struct XferBatch {
+    int32_t n, up, with_o, prop_all;
+    XferDir d[MAXB][2];
+};
+
+struct MatchConst {              // scalars common to one launch
+    int32_t sigma, c;            // lattice stride and offset
+    int32_t norm, rs_W, rs_mode, K;
+    uint32_t key0, key1;
+    int32_t t, colour, tau2, pad;
+};
+
+// Brackets the launches of one kernel class: counts them and, while
+// pgm_profile_enable(1) is on for this thread, records an event pair.
+struct KScope {
+    KScope(int cls, cudaStream_t st, int nlaunch = 1);
+    ~KScope();
+    int cls; cudaStream_t st; int n; int slot;
+};
+
+// ------------------------------------------------------------ launchers
+// pyramid.cu
+pgm_status launch_pyramid(const pgm_params* p, const PyrPlan& pp, const uint8_t* d_img, int c,
+                          size_t pitch, uint8_t* d_pyr, cudaStream_t st);
+// match.cu
+pgm_status launch_init(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
+                       int max_seeds, cudaStream_t st);
+pgm_status launch_cost_fill(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
+                            int max_seeds, cudaStream_t st);
+pgm_status launch_pm_phase(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
+                           int max_seeds, cudaStream_t st);
+pgm_status launch_consist(const LvlBatch& B, const MatchConst& mc, int max_seeds,
+                          cudaStream_t st);
+pgm_status launch_transfer(const XferBatch& X, int max_seeds, cudaStream_t st);
+// filter.cu
+pgm_status launch_filter(const pgm_params* p, const WsPlan& wp, uint8_t* d_ws,
+                         int32_t* d_matches, int64_t max_matches, int32_t* d_count,
+                         uint8_t* d_keep, cudaStream_t st);
+
+}  // namespace pgm

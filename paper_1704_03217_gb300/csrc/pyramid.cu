@@ -1,0 +1,235 @@
+// pyramid.cu -- gradient pyramid of one image on the GPU.
+//
+// Steps (one kernel each, all integer, all HBM/L2-streaming):
+//   level 0: gray conversion (PGM-G/GD, Sec. III-F) or RGB de-interleave
+//   levels 1..L-1: 5x5 binomial [1 4 6 4 1]^2 / 256 with decimation by 2 and
+//            replicated border (Sec. III-D, downsample factor s = 1/2)
+//   per level and direction: colour space of Table 2 (Sec. III-E): RGB,
+//            CIELab or YCrCb, integer definitions
+//   per level and direction: Sobel gradients Gx, Gy (Eq. 1-2), S = 3 or 5,
+//            replicated border, int16, pixel-interleaved; for the direction
+//            descriptor (Sec. III-F) their signs.
+#include "pgm_device.cuh"
+
+namespace pgm {
+namespace {
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+__device__ __forceinline__ int gray_q14(int r, int g, int b) {
+    // BT.601 luma weights 0.299, 0.587, 0.114 in Q14 (sum 16384)
+    return (4899 * r + 9617 * g + 1868 * b + 8192) >> 14;
+}
+
+// ---------------------------------------------------------------- level 0
+// mode 0: gray input copied; mode 1: RGB -> gray; mode 2: RGB -> 3 planes
+__global__ void k_level0(const uint8_t* __restrict__ img, int w, int h, size_t pitch, int mode,
+                         uint8_t* __restrict__ out, int row, size_t plane) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= w || y >= h) return;
+    const uint8_t* src = img + (size_t)y * pitch;
+    if (mode == 0) {
+        out[(size_t)y * row + x] = src[x];
+    } else {
+        int r = src[3 * x], g = src[3 * x + 1], b = src[3 * x + 2];
+        if (mode == 1) {
+            out[(size_t)y * row + x] = (uint8_t)gray_q14(r, g, b);
+        } else {
+            out[(size_t)y * row + x] = (uint8_t)r;
+            out[plane + (size_t)y * row + x] = (uint8_t)g;
+            out[2 * plane + (size_t)y * row + x] = (uint8_t)b;
+        }
+    }
+}
+
+// ------------------------------------------------------- binomial down
+// One output pixel per thread, channel = blockIdx.z.  The separable sums are
+// exact integers, so summing rows first equals the 2D sum of the definition.
+__global__ void k_down(const uint8_t* __restrict__ in, int w, int h, int irow, size_t iplane,
+                       uint8_t* __restrict__ out, int w2, int h2, int orow, size_t oplane) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= w2 || y >= h2) return;
+    const uint8_t* src = in + blockIdx.z * iplane;
+    const int k[5] = {1, 4, 6, 4, 1};
+    int xs[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) xs[i] = clampi(2 * x + i - 2, 0, w - 1);
+    int acc = 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const uint8_t* r = src + (size_t)clampi(2 * y + j - 2, 0, h - 1) * irow;
+        int s = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) s += k[i] * r[xs[i]];
+        acc += k[j] * s;
+    }
+    out[blockIdx.z * oplane + (size_t)y * orow + x] = (uint8_t)((acc + 128) >> 8);
+}
+
+// ------------------------------------------------------- colour spaces
+// Integer cube root: float estimate, then exact correction.
+__device__ __forceinline__ uint32_t icbrt48(unsigned long long v) {
+    int c = (int)cbrtf((float)v);
+#pragma unroll
+    for (int it = 0; it < 3; ++it)
+        if (c > 0 && (unsigned long long)c * c * c > v) --c;
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+        unsigned long long n = (unsigned long long)(c + 1);
+        if (n * n * n <= v) ++c;
+    }
+    return (uint32_t)c;
+}
+
+// CIELab companding function of t = T / (255 * 2^16), result scaled by 2^16.
+__device__ __forceinline__ long long lab_f(long long T) {
+    if (T * 24389 > 216LL * 255 * 65536) {               // t > (6/29)^3
+        unsigned long long V = ((unsigned long long)T << 32) / 255ull;  // t * 2^48
+        return (long long)icbrt48(V);
+    }
+    long long num = T * (841 * 29) + 4LL * 65536 * 108 * 255;          // t * 841/108 + 4/29
+    return num / (108LL * 255 * 29);                                    // num > 0
+}
+
+__device__ __forceinline__ long long fdiv(long long a, long long b) {  // floor, b > 0
+    long long q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+
+__device__ __forceinline__ void to_lab(int r, int g, int b, int* o) {
+    // D65 RGB -> XYZ / white, Q16 rows summing to 65536, linear RGB
+    long long X = 28439LL * r + 24656LL * g + 12441LL * b;
+    long long Y = 13937LL * r + 46869LL * g + 4730LL * b;
+    long long Z = 1164LL * r + 7175LL * g + 57197LL * b;
+    long long fx = lab_f(X), fy = lab_f(Y), fz = lab_f(Z);
+    long long Ls = fdiv((116 * fy - 16 * 65536) * 255 + 3276800, 6553600);
+    long long As = fdiv(500 * (fx - fy) + 128 * 65536 + 32768, 65536);
+    long long Bs = fdiv(200 * (fy - fz) + 128 * 65536 + 32768, 65536);
+    o[0] = clampi((int)Ls, 0, 255);
+    o[1] = clampi((int)As, 0, 255);
+    o[2] = clampi((int)Bs, 0, 255);
+}
+
+__device__ __forceinline__ void to_ycrcb(int r, int g, int b, int* o) {
+    int y = gray_q14(r, g, b);
+    o[0] = y;
+    o[1] = clampi((int)fdiv((long long)(r - y) * 11682 + (128 << 14) + 8192, 16384), 0, 255);
+    o[2] = clampi((int)fdiv((long long)(b - y) * 9241 + (128 << 14) + 8192, 16384), 0, 255);
+}
+
+__global__ void k_convert(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int w, int h,
+                          int row, size_t plane, int space) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= w || y >= h) return;
+    size_t o = (size_t)y * row + x;
+    int r = in[o], g = in[plane + o], b = in[2 * plane + o];
+    int v[3];
+    if (space == SP_LAB) to_lab(r, g, b, v); else to_ycrcb(r, g, b, v);
+    out[o] = (uint8_t)v[0];
+    out[plane + o] = (uint8_t)v[1];
+    out[2 * plane + o] = (uint8_t)v[2];
+}
+
+// ----------------------------------------------------------------- Sobel
+// Gx = sum_j s_j sum_i d_i I(x+i, y+j); Gy with the roles of the axes swapped.
+template <int S, int C>
+__global__ void k_sobel(const uint8_t* __restrict__ in, int w, int h, int row, size_t plane,
+                        int16_t* __restrict__ out, int orow, int dir_only) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= w || y >= h) return;
+    constexpr int R = S / 2;
+    const int d5[5] = {-1, -2, 0, 2, 1}, s5[5] = {1, 4, 6, 4, 1};
+    const int d3[3] = {-1, 0, 1}, s3[3] = {1, 2, 1};
+    int xs[S], ys[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        xs[i] = clampi(x + i - R, 0, w - 1);
+        ys[i] = clampi(y + i - R, 0, h - 1);
+    }
+    int g[2 * C];
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) {
+        const uint8_t* src = in + ch * plane;
+        int gx = 0, gy = 0;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const uint8_t* r = src + (size_t)ys[j] * row;
+            int sd = 0, ss = 0;
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                int v = r[xs[i]];
+                sd += (S == 5 ? d5[i] : d3[i]) * v;
+                ss += (S == 5 ? s5[i] : s3[i]) * v;
+            }
+            gx += (S == 5 ? s5[j] : s3[j]) * sd;
+            gy += (S == 5 ? d5[j] : d3[j]) * ss;
+        }
+        if (dir_only) {
+            gx = (gx > 0) - (gx < 0);
+            gy = (gy > 0) - (gy < 0);
+        }
+        g[ch] = gx;
+        g[C + ch] = gy;
+    }
+    // pixel-interleaved int16, written as 32-bit words (2C is even)
+    uint32_t* dst = reinterpret_cast<uint32_t*>(out + (size_t)y * orow + (size_t)x * 2 * C);
+#pragma unroll
+    for (int k = 0; k < C; ++k)
+        dst[k] = (uint32_t)(uint16_t)g[2 * k] | ((uint32_t)(uint16_t)g[2 * k + 1] << 16);
+}
+
+}  // namespace
+
+pgm_status launch_pyramid(const pgm_params* p, const PyrPlan& pp, const uint8_t* d_img, int c,
+                          size_t pitch, uint8_t* d_pyr, cudaStream_t st) {
+    int nlaunch = pp.L;                       // level 0 + (L-1) reductions + Sobels + conversions
+    for (int s = 0; s < pp.nsch; ++s)
+        for (int l = 0; l < pp.L; ++l)
+            nlaunch += 1 + (pp.space[s][l] == SP_LAB || pp.space[s][l] == SP_YCRCB);
+    KScope ks(PGM_K_PYRAMID, st, nlaunch);
+    dim3 blk(32, 8);
+    auto grid = [&](int w, int h, int z) { return dim3((w + 31) / 32, (h + 7) / 8, z); };
+    int mode = c == 1 ? 0 : (pp.C == 1 ? 1 : 2);
+    k_level0<<<grid(pp.W[0], pp.H[0], 1), blk, 0, st>>>(d_img, pp.W[0], pp.H[0], pitch, mode,
+                                                        d_pyr + pp.img_off[0], pp.img_row[0],
+                                                        pp.img_plane[0]);
+    for (int l = 1; l < pp.L; ++l)
+        k_down<<<grid(pp.W[l], pp.H[l], pp.C), blk, 0, st>>>(
+            d_pyr + pp.img_off[l - 1], pp.W[l - 1], pp.H[l - 1], pp.img_row[l - 1],
+            pp.img_plane[l - 1], d_pyr + pp.img_off[l], pp.W[l], pp.H[l], pp.img_row[l],
+            pp.img_plane[l]);
+    for (int s = 0; s < pp.nsch; ++s)
+        for (int l = 0; l < pp.L; ++l) {
+            int sp = pp.space[s][l];
+            if (sp == SP_LAB || sp == SP_YCRCB)
+                k_convert<<<grid(pp.W[l], pp.H[l], 1), blk, 0, st>>>(
+                    d_pyr + pp.img_off[l], d_pyr + pp.cimg_off[s][l], pp.W[l], pp.H[l],
+                    pp.img_row[l], pp.img_plane[l], sp);
+            const uint8_t* ci = d_pyr + pp.cimg_off[s][l];
+            int16_t* de = reinterpret_cast<int16_t*>(d_pyr + pp.desc_off[s][l]);
+            dim3 g = grid(pp.W[l], pp.H[l], 1);
+            int dir_only = p->descriptor == PGM_DIR;
+            if (p->sobel == 5) {
+                if (pp.C == 1)
+                    k_sobel<5, 1><<<g, blk, 0, st>>>(ci, pp.W[l], pp.H[l], pp.img_row[l],
+                                                     pp.img_plane[l], de, pp.desc_row[l], dir_only);
+                else
+                    k_sobel<5, 3><<<g, blk, 0, st>>>(ci, pp.W[l], pp.H[l], pp.img_row[l],
+                                                     pp.img_plane[l], de, pp.desc_row[l], dir_only);
+            } else {
+                if (pp.C == 1)
+                    k_sobel<3, 1><<<g, blk, 0, st>>>(ci, pp.W[l], pp.H[l], pp.img_row[l],
+                                                     pp.img_plane[l], de, pp.desc_row[l], dir_only);
+                else
+                    k_sobel<3, 3><<<g, blk, 0, st>>>(ci, pp.W[l], pp.H[l], pp.img_row[l],
+                                                     pp.img_plane[l], de, pp.desc_row[l], dir_only);
+            }
+        }
+    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+}
+
+}  // namespace pgm
