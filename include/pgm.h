@@ -192,6 +192,37 @@ pgm_status pgm_filter(const pgm_params* p, int w1, int h1, int w2, int h2, void*
                       size_t ws_bytes, int32_t* d_matches, int64_t max_matches,
                       int32_t* d_count, uint8_t* d_keep, void* stream);
 
+/* The same final filter for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a deployment convenience.
+ *
+ * pgm_filter needs its scratch (region labels, region sizes, scan partial
+ * sums) inside the caller's match workspace.  Some callers cannot provide
+ * such a buffer: code that runs where allocation is forbidden or unsafe --
+ * inside another framework's enqueue callback, in a real-time loop whose
+ * memory budget is fixed up front, or next to an allocator that owns all of
+ * the device's memory -- and that only holds the level-0 forward field.
+ * This entry point takes that field and writes the matches, with its scratch
+ * in a fixed array that the library itself places in device memory when it
+ * is loaded (PGM_NOALLOC_MAX_SEEDS seeds, 8 MiB + 16 KiB per device, held
+ * until the process exits).  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   d_u, d_flags: the nx x ny level-0 forward field, laid out as
+ *                 pgm_field_layout describes (packed int32 displacement,
+ *                 uint8 flags); read only.
+ *   d_matches, max_matches, d_count: as for pgm_filter.
+ * Result: identical to pgm_filter on the workspace holding that field.
+ * The first call on each device looks up the array's device address with
+ * the device current; make that first call before any stream capture.  All
+ * calls share the one array and it keeps the last call's contents (every
+ * call re-initialises what it reads), so calls whose work overlaps on the
+ * GPU -- e.g. on two streams at once -- race and must be serialised.
+ * Errors: PGM_ERR_ARG (NULL pointer, nx or ny < 0, misaligned d_matches),
+ * PGM_ERR_UNSUPPORTED (nx * ny > PGM_NOALLOC_MAX_SEEDS), PGM_ERR_CUDA. */
+#define PGM_NOALLOC_MAX_SEEDS (1 << 20)
+pgm_status pgm_filter_noalloc(const pgm_params* p, int nx, int ny, const int32_t* d_u,
+                              const uint8_t* d_flags, int32_t* d_matches, int64_t max_matches,
+                              int32_t* d_count, void* stream);
+
 /* Wait for `stream` and return the device-side status recorded in the
  * workspace (PGM_OK, PGM_ERR_TIMEOUT or PGM_ERR_DEVICE_BOUNDS), clearing
  * it.  Synchronising call. */

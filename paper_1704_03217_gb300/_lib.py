@@ -31,7 +31,9 @@ EXPORTS = [
     "pgm_pyramid_desc_layout", "pgm_pyramid_image_layout", "pgm_match_workspace_bytes",
     "pgm_match", "pgm_match_batch", "pgm_field_layout", "pgm_filter", "pgm_sync_status",
     "pgm_nominal_evals", "pgm_launch_count", "pgm_profile_enable", "pgm_profile_read",
+    "pgm_filter_noalloc",
 ]
+NOALLOC_MAX_SEEDS = 1 << 20
 K_CLASSES = ["pyramid", "init", "cost", "pm", "consist", "transfer", "filter"]
 WS_EVALS_OFFSET, WS_EVALS_COUNT = 8, 6   # pm fwd/bwd, cost fwd/bwd, init fwd/bwd
 
@@ -75,7 +77,8 @@ def load(path: str = LIB_PATH):
     L.pgm_profile_enable.argtypes = [i32]; L.pgm_profile_enable.restype = C.c_int
     L.pgm_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.pgm_profile_read.restype = C.c_int
-    for name in ("pgm_build_pyramid", "pgm_pyramid_desc_layout", "pgm_pyramid_image_layout",
+    L.pgm_filter_noalloc.argtypes = [P, i32, i32, vp, vp, vp, i64, vp, vp]
+    for name in ("pgm_filter_noalloc", "pgm_build_pyramid", "pgm_pyramid_desc_layout", "pgm_pyramid_image_layout",
                  "pgm_match", "pgm_match_batch", "pgm_field_layout", "pgm_filter",
                  "pgm_sync_status"):
         getattr(L, name).restype = C.c_int

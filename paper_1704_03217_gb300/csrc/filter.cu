@@ -166,4 +166,28 @@ pgm_status launch_filter(const pgm_params* p, const WsPlan& wp, uint8_t* d_ws,
     return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
 }
 
+// The same sequence on explicit pointers: the field (u, flags) and the
+// scratch (label, size: nx*ny ints each; bsum: one int per 256 seeds + 1)
+// may live anywhere in device memory.
+pgm_status launch_filter_ptrs(const pgm_params* p, int nx, int ny, const int32_t* u,
+                              const uint8_t* flags, int* label, int* size, int* bsum,
+                              int32_t* d_matches, int64_t max_matches, int32_t* d_count,
+                              cudaStream_t st) {
+    const int n = nx * ny;
+    const int nb = (n + 255) / 256;
+    if (n == 0) {
+        cudaMemsetAsync(d_count, 0, sizeof(int32_t), st);
+        return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+    }
+    KScope ks(PGM_K_FILTER, st, 6);
+    k_cc_init<<<nb, 256, 0, st>>>(flags, n, label, size);
+    k_cc_link<<<nb, 256, 0, st>>>(flags, u, nx, ny, p->region_dmax2, label);
+    k_cc_flatten<<<nb, 256, 0, st>>>(n, label, size);
+    k_keep_count<<<nb, 256, 0, st>>>(n, label, size, p->min_region, bsum, nullptr);
+    k_scan_blocks<<<1, 1024, 0, st>>>(nb, bsum, d_count);
+    k_keep_write<<<nb, 256, 0, st>>>(n, nx, p->seed_stride, p->seed_stride / 2, label, size,
+                                     p->min_region, u, bsum, d_matches, max_matches);
+    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+}
+
 }  // namespace pgm

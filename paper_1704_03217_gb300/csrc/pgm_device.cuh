@@ -129,6 +129,10 @@ pgm_status launch_consist(const LvlBatch& B, const MatchConst& mc, int max_seeds
                           cudaStream_t st);
 pgm_status launch_transfer(const XferBatch& X, int max_seeds, cudaStream_t st);
 // filter.cu
+pgm_status launch_filter_ptrs(const pgm_params* p, int nx, int ny, const int32_t* u,
+                              const uint8_t* flags, int* label, int* size, int* bsum,
+                              int32_t* d_matches, int64_t max_matches, int32_t* d_count,
+                              cudaStream_t st);
 pgm_status launch_filter(const pgm_params* p, const WsPlan& wp, uint8_t* d_ws,
                          int32_t* d_matches, int64_t max_matches, int32_t* d_count,
                          uint8_t* d_keep, cudaStream_t st);
