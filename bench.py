@@ -319,7 +319,8 @@ def run_ours(a):
             "kernel_ms_per_step": kernel_ms, "kernel_launches_per_step": kernel_launches,
             "evals_per_step": {"pm": sum(sum(e["pm"]) for e in ev_counts),
                                "cost": sum(sum(e["cost"]) for e in ev_counts),
-                               "init": sum(sum(e["init"]) for e in ev_counts)},
+                               "init": sum(sum(e["init"]) for e in ev_counts),
+                               "pm_global": sum(sum(e["pm_global"]) for e in ev_counts)},
             "variants": variants,
             "clocks": clk,
             "cpu_baseline": cpu,

@@ -234,12 +234,14 @@ pgm_status pgm_sync_status(const pgm_params* p, int w1, int h1, int w2, int h2, 
 /* ------------------------------------------------------------------ */
 
 /* Workspace header: bytes [0, 4) hold the device status word; bytes
- * [8, 56) six uint64 counters of patch distances (Eq. 3) actually evaluated:
- * propagation/search forward, backward; cost refresh forward, backward;
- * exhaustive initialisation forward, backward.  pgm_match and
- * pgm_match_batch zero them at their start. */
+ * [8, 72) eight uint64 counters of patch distances (Eq. 3) actually
+ * evaluated: propagation/search forward, backward; cost refresh forward,
+ * backward; exhaustive initialisation forward, backward; and, of the
+ * propagation/search ones, those scored outside the shared-memory window
+ * (from global memory) forward, backward.  pgm_match and pgm_match_batch
+ * zero them at their start. */
 #define PGM_WS_EVALS_OFFSET 8
-#define PGM_WS_EVALS_COUNT 6
+#define PGM_WS_EVALS_COUNT 8
 
 /* Kernel classes for pgm_profile_read. */
 enum { PGM_K_PYRAMID = 0, PGM_K_INIT = 1, PGM_K_COST = 2, PGM_K_PM = 3, PGM_K_CONSIST = 4,

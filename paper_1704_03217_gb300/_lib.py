@@ -35,7 +35,7 @@ EXPORTS = [
 ]
 NOALLOC_MAX_SEEDS = 1 << 20
 K_CLASSES = ["pyramid", "init", "cost", "pm", "consist", "transfer", "filter"]
-WS_EVALS_OFFSET, WS_EVALS_COUNT = 8, 6   # pm fwd/bwd, cost fwd/bwd, init fwd/bwd
+WS_EVALS_OFFSET, WS_EVALS_COUNT = 8, 8   # pm, cost, init, pm-from-global: fwd/bwd each
 
 
 class PGMError(RuntimeError):

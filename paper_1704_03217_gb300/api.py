@@ -143,7 +143,7 @@ class Workspace:
         """Patch distances evaluated by the last match (device counters)."""
         o = _lib.WS_EVALS_OFFSET
         v = self.buf[o:o + 8 * _lib.WS_EVALS_COUNT].view(torch.int64).tolist()
-        return {"pm": v[0:2], "cost": v[2:4], "init": v[4:6]}
+        return {"pm": v[0:2], "cost": v[2:4], "init": v[4:6], "pm_global": v[6:8]}
 
     def sync_status(self, stream=None):
         check(_lib.load().pgm_sync_status(C.byref(self._cp), *self.dims,

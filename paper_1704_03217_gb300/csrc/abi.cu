@@ -109,12 +109,15 @@ bool make_pyr_plan(const pgm_params* p, int w, int h, PyrPlan* pp) {
             }
             pp->desc_off[s][l] = off;
             off = align_up(off + (size_t)pp->desc_row[l] * pp->H[l] * 2, 256);
+            pp->split_off[s][l] = off;
+            off = align_up(off + (size_t)pp->desc_row[l] * pp->H[l] * 2, 256);
         }
     for (int s = pp->nsch; s < 2; ++s)
         for (int l = 0; l < pp->L; ++l) {
             pp->space[s][l] = pp->space[0][l];
             pp->cimg_off[s][l] = pp->cimg_off[0][l];
             pp->desc_off[s][l] = pp->desc_off[0][l];
+            pp->split_off[s][l] = pp->split_off[0][l];
         }
     pp->bytes = off + 256;     // tail slack: vector loads never leave the buffer
     return true;
@@ -136,7 +139,15 @@ bool make_ws_plan(const pgm_params* p, int w1, int h1, int w2, int h2, WsPlan* w
             wp->off_u[l][d] = off;     off = align_up(off + 4 * n, 256);
             wp->off_cost[l][d] = off;  off = align_up(off + 8 * n, 256);
             wp->off_flags[l][d] = off; off = align_up(off + n, 256);
+            wp->off_sa2[l][d] = off;   off = align_up(off + 8 * n, 256);
+            const PyrPlan& t = d == 0 ? b : a;       // target image of this direction
+            wp->off_sb2[l][d] = off;   off = align_up(off + 8 * (size_t)t.W[l] * t.H[l], 256);
         }
+    for (int d = 0; d < 2; ++d) {
+        const PyrPlan& t = d == 0 ? b : a;
+        wp->off_boxtmp[d] = off;
+        off = align_up(off + 8 * (size_t)t.W[0] * t.H[0], 256);
+    }
     size_t n0 = (size_t)wp->nx[0][0] * wp->ny[0][0];
     wp->nblk0 = (int)((n0 + 255) / 256);
     wp->off_label = off; off = align_up(off + 4 * n0, 256);
@@ -184,6 +195,7 @@ void fill_dir(const pgm_params* p, const PairCtx& c, int l, int d, DirLvl* D) {
     const uint8_t* tp = d == 0 ? c.pyr2 : c.pyr1;
     int s = d < R.nsch ? d : R.nsch - 1;
     D->ref = reinterpret_cast<const int16_t*>(rp + R.desc_off[s][l]);
+    D->ref_split = reinterpret_cast<const uint32_t*>(rp + R.split_off[s][l]);
     D->tgt = reinterpret_cast<const int16_t*>(tp + T.desc_off[s][l]);
     D->ref_pitch = R.desc_row[l]; D->tgt_pitch = T.desc_row[l];
     D->rw = R.W[l]; D->rh = R.H[l]; D->tw = T.W[l]; D->th = T.H[l];
@@ -196,6 +208,9 @@ void fill_dir(const pgm_params* p, const PairCtx& c, int l, int d, DirLvl* D) {
     D->flags = c.ws + c.w.off_flags[l][d];
     D->ou = reinterpret_cast<const int32_t*>(c.ws + c.w.off_u[l][1 - d]);
     D->oflags = c.ws + c.w.off_flags[l][1 - d];
+    D->sa2 = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sa2[l][d]);
+    D->sb2 = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sb2[l][d]);
+    D->boxtmp = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_boxtmp[d]);
 }
 
 pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) {
@@ -214,6 +229,25 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
     for (int k = 0; k < n; ++k)           // reset the evaluation counters
         if (cudaMemsetAsync(ctx[k].ws + PGM_WS_EVALS_OFFSET, 0, 8 * PGM_WS_EVALS_COUNT, st) != cudaSuccess)
             return PGM_ERR_CUDA;
+    if (p->norm == PGM_L2SQ) {
+        // per level and direction: box sums of |G|^2 over the target patches
+        bool needed[MAXL] = {false};
+        for (int v = 0; v < sch.n; ++v) needed[sch.level[v]] = true;
+        for (int l = 0; l < p->levels; ++l) {
+            if (!needed[l]) continue;
+            memset(&B, 0, sizeof(B));
+            B.n = n; B.level = l;
+            int max_px = 0;
+            for (int k = 0; k < n; ++k)
+                for (int d = 0; d < 2; ++d) {
+                    fill_dir(p, ctx[k], l, d, &B.d[k][d]);
+                    int np = B.d[k][d].tw * B.d[k][d].th;
+                    if (np > max_px) max_px = np;
+                }
+            pgm_status r = launch_box(B, nch, max_px, st);
+            if (r != PGM_OK) return r;
+        }
+    }
     for (int v = 0; v < sch.n; ++v) {
         const int l = sch.level[v];
         memset(&B, 0, sizeof(B));

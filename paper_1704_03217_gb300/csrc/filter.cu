@@ -24,6 +24,20 @@ __device__ __forceinline__ int find_root(const int* L, int a) {
     return a;
 }
 
+// find with path halving: each visited node is re-pointed to its
+// grandparent.  Labels only ever decrease towards a root of the same
+// component, so the plain stores are safe under concurrent unions.
+__device__ __forceinline__ int find_halve(int* L, int a) {
+    int p = L[a];
+    while (p != a) {
+        const int g = L[p];
+        if (g != p) L[a] = g;
+        a = p;
+        p = g;
+    }
+    return a;
+}
+
 __global__ void k_cc_init(const uint8_t* __restrict__ flags, int n, int* __restrict__ label,
                           int* __restrict__ size) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -36,8 +50,8 @@ __device__ void unite(int* L, int a, int b) {
     // link the larger root below the smaller one; retry if another thread
     // re-linked the root in between
     for (;;) {
-        a = find_root(L, a);
-        b = find_root(L, b);
+        a = find_halve(L, a);
+        b = find_halve(L, b);
         if (a == b) return;
         if (a < b) { int t = a; a = b; b = t; }      // a > b: link a -> b
         int old = atomicMin(&L[a], b);
@@ -67,6 +81,8 @@ __global__ void k_cc_link(const uint8_t* __restrict__ flags, const int32_t* __re
 __global__ void k_cc_flatten(int n, int* label, int* size) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n || label[s] < 0) return;
+    // read-only find: a halving store by another thread could otherwise
+    // overwrite the root just written to label[s] with a non-root ancestor
     int r = find_root(label, s);
     label[s] = r;
     atomicAdd(&size[r], 1);

@@ -11,43 +11,10 @@
 //
 // All arithmetic is integer: descriptors are int16, a patch distance is an
 // exact uint64 sum, so the result does not depend on the reduction order.
-#include "pgm_device.cuh"
+#include "match_common.cuh"
 
 namespace pgm {
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-constexpr unsigned long long INF = ~0ull;
-
-__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
-__device__ __forceinline__ int lo16(uint32_t v) { return (int)(int16_t)(v & 0xffffu); }
-__device__ __forceinline__ int hi16(uint32_t v) { return ((int)v) >> 16; }
-__device__ __forceinline__ int32_t pack_u(int ux, int uy) {
-    return (int32_t)(((uint32_t)ux & 0xffffu) | ((uint32_t)uy << 16));
-}
-
-// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products,
-// key bumped by the Weyl constants between rounds.
-__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    }
-    return c;
-}
-
-// offset of the k-th limited random-search candidate (Eq. 5)
-__device__ __forceinline__ int rs_off(uint32_t r, int k, int W, int mode) {
-    if (mode == PGM_RS_SYMMETRIC) {
-        int rho = max(1, W >> k);
-        return (int)(((unsigned long long)r * (unsigned long long)(2 * rho + 1)) >> 32) - rho;
-    }
-    long long num = ((long long)r * 2 - 4294967295LL) * (long long)W;
-    return (int)(num >> (32 + k));      // arithmetic shift = floor division by 2^(32+k)
-}
 
 // ------------------------------------------------------------------
 // Warp-cooperative patch distance.  Lane l holds patch pixels l, l+32, ...
@@ -107,8 +74,253 @@ __device__ __forceinline__ unsigned long long warp_cost(const Ref<NCH, PPL>& R, 
     return acc;
 }
 
-__device__ __forceinline__ bool inside(const DirLvl& D, int qx, int qy) {
-    return qx >= 0 && qy >= 0 && qx < D.tw && qy < D.th;
+
+// ------------------------------------------------------------------
+// Squared-L2 path.  Over integers Eq. 3 splits exactly into
+//   D = sum |a|^2 + sum |b|^2 - 2 sum <a, b>
+// (a: reference patch, b: target patch, borders replicated in each image).
+// sum |a|^2 is computed once per seed (k_cost_x), sum |b|^2 once per target
+// pixel (box filter, k_box_h / k_box_v), so a candidate needs only the cross
+// term.  Each reference value a (|a| <= 12240) is split into two signed bytes
+// a = 128 a_h + a_l, a_l in [-64, 63], a_h in [-96, 96], so one dp2a
+// instruction multiplies a whole 32-bit target word (two int16 values) by
+// the low bytes and one by the high bytes.  Lane partial sums and their warp
+// totals stay below 2^31 for patches up to 16 x 16 x 6 values:
+//   |sum b a_l| <= 1536 * 12240 * 64 < 1.3e9,  |sum b a_h| <= 1536 * 12240 * 96 < 1.9e9.
+
+// Box filter of N(x, y) = sum_c G_c(x, y)^2 over the P x P patch with
+// replicated borders, separable: row sums, then column sums (exact, uint64).
+template <int NCH>
+__global__ void k_box_h(const __grid_constant__ LvlBatch B) {
+    const DirLvl& D = B.d[blockIdx.z][blockIdx.y];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= D.tw * D.th) return;
+    const int x = idx % D.tw, y = idx / D.tw, h = D.P / 2;
+    const uint32_t* row = reinterpret_cast<const uint32_t*>(D.tgt + (size_t)y * D.tgt_pitch);
+    unsigned long long s = 0;
+    for (int o = 0; o < D.P; ++o) {
+        const int xx = clampi(x + o - h, 0, D.tw - 1);
+        uint32_t n = 0;
+#pragma unroll
+        for (int c = 0; c < NCH / 2; ++c) {
+            const uint32_t v = __ldg(row + (size_t)xx * (NCH / 2) + c);
+            const int a = lo16(v), b = hi16(v);
+            n += (uint32_t)(a * a) + (uint32_t)(b * b);
+        }
+        s += n;
+    }
+    D.boxtmp[idx] = s;
+}
+
+__global__ void k_box_v(const __grid_constant__ LvlBatch B) {
+    const DirLvl& D = B.d[blockIdx.z][blockIdx.y];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= D.tw * D.th) return;
+    const int x = idx % D.tw, y = idx / D.tw, h = D.P / 2;
+    unsigned long long s = 0;
+    for (int o = 0; o < D.P; ++o) s += D.boxtmp[(size_t)clampi(y + o - h, 0, D.th - 1) * D.tw + x];
+    D.sb2[idx] = s;
+}
+
+// Lane l owns words l, l + 32, ... of the P x P x NCH patch, flattened row by
+// row (a patch row is P * NCH / 2 consecutive 32-bit words of the image row).
+// Word offsets of the flattened patch inside an interior target patch; the
+// same for every warp of a block (one pair, one direction), kept in shared
+// memory: s_off[k] for k = lane + 32 m.
+template <int NCH, int MMAX>
+__device__ __forceinline__ void fill_offsets(int* s_off, const DirLvl& D) {
+    constexpr int WPP = NCH / 2;
+    const int wpr = D.P * WPP, nw = D.P * wpr, pitchw = D.tgt_pitch >> 1;
+    for (int k = threadIdx.x; k < 32 * MMAX; k += blockDim.x) {
+        const int row = k / wpr, col = k - row * wpr;
+        s_off[k] = k < nw ? row * pitchw + col : 0;
+    }
+}
+
+// Loads this lane's reference words; returns the lane's partial sum of a^2
+// when WANT_SA2.
+template <int NCH, int MMAX, bool WANT_SA2>
+__device__ __forceinline__ unsigned long long xload_ref(XRef<MMAX>& R, const DirLvl& D, int px,
+                                                        int py, int lane) {
+    constexpr int WPP = NCH / 2;
+    const int P = D.P, h = P / 2, wpr = P * WPP, nw = P * wpr;
+    const int rpitchw = D.ref_pitch >> 1;
+    const uint32_t* ref32 = reinterpret_cast<const uint32_t*>(D.ref);
+    unsigned long long sa = 0;
+#pragma unroll
+    for (int m = 0; m < MMAX; ++m) {
+        const int k = lane + 32 * m;
+        R.b[m] = 0;
+        if (k < nw) {
+            const int row = k / wpr, col = k - row * wpr;
+            const int pix = col / WPP, wi = col - pix * WPP;
+            const int x = clampi(px - h + pix, 0, D.rw - 1), y = clampi(py - h + row, 0, D.rh - 1);
+            const uint32_t v = __ldg(ref32 + (size_t)y * rpitchw + (size_t)x * WPP + wi);
+            const int a0 = lo16(v), a1 = hi16(v);
+            R.b[m] = split_bytes(a0, a1);
+            if (WANT_SA2) sa += (uint32_t)(a0 * a0) + (uint32_t)(a1 * a1);
+        }
+    }
+    return sa;
+}
+
+// sum <a, b> over the patch at target centre (qx, qy), warp-uniform result
+template <int NCH, int MMAX>
+__device__ __forceinline__ long long xcross(const XRef<MMAX>& R, const int* s_off, const DirLvl& D,
+                                            int qx, int qy, int lane) {
+    constexpr int WPP = NCH / 2;
+    const int P = D.P, h = P / 2, wpr = P * WPP, nw = P * wpr;
+    const int pitchw = D.tgt_pitch >> 1;
+    const uint32_t* t32 = reinterpret_cast<const uint32_t*>(D.tgt);
+    const int x0 = qx - h, y0 = qy - h;
+    int sl = 0, sh = 0;
+    if (x0 >= 0 && y0 >= 0 && x0 + P <= D.tw && y0 + P <= D.th) {
+        const uint32_t* base = t32 + (size_t)y0 * pitchw + (size_t)x0 * WPP;
+        constexpr int CH = MMAX < 8 ? MMAX : 8;      // loads in flight per chunk
+#pragma unroll
+        for (int m0 = 0; m0 < MMAX; m0 += CH) {
+            uint32_t v[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                if (32 * (m0 + c) < nw) v[c] = __ldg(base + s_off[lane + 32 * (m0 + c)]);
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                if (32 * (m0 + c) < nw) {
+                    sl = __dp2a_lo((int)v[c], R.b[m0 + c], sl);
+                    sh = __dp2a_hi((int)v[c], R.b[m0 + c], sh);
+                }
+        }
+    } else {                                   // patch crosses the border: replicate
+#pragma unroll
+        for (int m = 0; m < MMAX; ++m)
+            if (32 * m < nw) {
+                const int k = lane + 32 * m;
+                const int row = k / wpr, col = k - row * wpr;
+                const int pix = col / WPP, wi = col - pix * WPP;
+                const int x = clampi(x0 + pix, 0, D.tw - 1), y = clampi(y0 + row, 0, D.th - 1);
+                const uint32_t v = __ldg(t32 + (size_t)y * pitchw + (size_t)x * WPP + wi);
+                sl = __dp2a_lo((int)v, R.b[m], sl);
+                sh = __dp2a_hi((int)v, R.b[m], sh);
+            }
+    }
+    sl = __reduce_add_sync(FULL, sl);
+    sh = __reduce_add_sync(FULL, sh);
+    return (long long)sh * 128 + (long long)sl;
+}
+
+template <int NCH, int MMAX>
+__global__ void __launch_bounds__(256, 3) k_cost_x(const __grid_constant__ LvlBatch B, const MatchConst mc) {
+    const int pair = blockIdx.z, dir = blockIdx.y;
+    const DirLvl& D = B.d[pair][dir];
+    __shared__ int s_off[32 * MMAX];
+    fill_offsets<NCH, MMAX>(s_off, D);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (s >= D.nx * D.ny) return;
+    const int i = s % D.nx, j = s / D.nx;
+    const int px = mc.c + mc.sigma * i, py = mc.c + mc.sigma * j;
+    XRef<MMAX> R;
+    unsigned long long sa = xload_ref<NCH, MMAX, true>(R, D, px, py, lane);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(FULL, sa, o);
+    if (lane == 0) D.sa2[s] = sa;                 // needed by every seed, valid or not
+    const uint8_t f = D.flags[s];
+    if (!(f & F_VALID)) return;
+    const int32_t u = D.u[s];
+    const int qx = px + lo16(u), qy = py + hi16(u);
+    if (!inside(D, qx, qy)) {
+        if (lane == 0) D.flags[s] = f & ~F_VALID;
+        return;
+    }
+    const unsigned long long sb = D.sb2[(size_t)qy * D.tw + qx];
+    const long long cr = xcross<NCH, MMAX>(R, s_off, D, qx, qy, lane);
+    if (lane == 0) {
+        D.cost[s] = xcost(sa, sb, cr);
+        atomicAdd(B.evals[pair] + 2 + dir, 1ull);
+    }
+}
+
+template <int NCH, int MMAX>
+__global__ void __launch_bounds__(256, 3) k_pm_x(const __grid_constant__ LvlBatch B, const MatchConst mc) {
+    const int pair = blockIdx.z, dir = blockIdx.y;
+    const DirLvl& D = B.d[pair][dir];
+    __shared__ int s_off[32 * MMAX];
+    fill_offsets<NCH, MMAX>(s_off, D);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wid = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int hw = (D.nx + 1) >> 1;
+    if (wid >= hw * D.ny) return;
+    const int j = wid / hw;
+    const int i = 2 * (wid - j * hw) + ((j + mc.colour) & 1);
+    if (i >= D.nx) return;
+    const int s = j * D.nx + i;
+    const int px = mc.c + mc.sigma * i, py = mc.c + mc.sigma * j;
+
+    const uint8_t f0 = D.flags[s];
+    bool have = f0 & F_VALID;
+    int32_t bu = D.u[s];
+    unsigned long long bc = have ? D.cost[s] : INF;
+    const int32_t u_in = bu;
+    const bool have_in = have;
+    const unsigned long long sa = D.sa2[s];
+
+    const int t4 = mc.t & 3;
+    const int sx = (t4 == 0 || t4 == 3) ? 1 : -1;
+    const int sy = (t4 == 0 || t4 == 2) ? 1 : -1;
+
+    XRef<MMAX> R;
+    bool loaded = false;
+    unsigned n_eval = 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {             // Eq. 4
+        const int ni = k == 0 ? i - sx : i, nj = k == 0 ? j : j - sy;
+        if (ni < 0 || nj < 0 || ni >= D.nx || nj >= D.ny) continue;
+        const int ns = nj * D.nx + ni;
+        if (!(D.flags[ns] & F_VALID)) continue;
+        const int32_t cu = D.u[ns];
+        if (have && cu == bu) continue;
+        const int qx = px + lo16(cu), qy = py + hi16(cu);
+        if (!inside(D, qx, qy)) continue;
+        const unsigned long long sb = D.sb2[(size_t)qy * D.tw + qx];
+        if (!loaded) { xload_ref<NCH, MMAX, false>(R, D, px, py, lane); loaded = true; }
+        const unsigned long long c = xcost(sa, sb, xcross<NCH, MMAX>(R, s_off, D, qx, qy, lane));
+        ++n_eval;
+        if (c < bc) { bc = c; bu = cu; have = true; }
+    }
+    if (!have) {
+        if (lane == 0 && n_eval) atomicAdd(B.evals[pair] + dir, (unsigned long long)n_eval);
+        return;
+    }
+    const int ux0 = lo16(bu), uy0 = hi16(bu);
+    uint4 r = make_uint4(0, 0, 0, 0);
+    for (int k = 0; k < mc.K; ++k) {          // Eq. 5
+        if ((k & 1) == 0) {
+            uint4 ctr = make_uint4((uint32_t)s,
+                                   ((uint32_t)B.visit << 16) | ((uint32_t)dir << 15) | (uint32_t)mc.t,
+                                   ((uint32_t)B.level << 16) | (uint32_t)(k >> 1),
+                                   B.stream_id[pair]);
+            r = philox(ctr, mc.key0, mc.key1);
+        }
+        const uint32_t rx = (k & 1) ? r.z : r.x, ry = (k & 1) ? r.w : r.y;
+        const int dx = rs_off(rx, k, mc.rs_W, mc.rs_mode), dy = rs_off(ry, k, mc.rs_W, mc.rs_mode);
+        if (dx == 0 && dy == 0) continue;
+        const int cx = ux0 + dx, cy = uy0 + dy;
+        const int qx = px + cx, qy = py + cy;
+        if (!inside(D, qx, qy)) continue;
+        const unsigned long long sb = D.sb2[(size_t)qy * D.tw + qx];
+        if (!loaded) { xload_ref<NCH, MMAX, false>(R, D, px, py, lane); loaded = true; }
+        const unsigned long long c = xcost(sa, sb, xcross<NCH, MMAX>(R, s_off, D, qx, qy, lane));
+        ++n_eval;
+        if (c < bc) { bc = c; bu = pack_u(cx, cy); }
+    }
+    if (lane == 0 && n_eval) atomicAdd(B.evals[pair] + dir, (unsigned long long)n_eval);
+    if (lane == 0 && (bu != u_in || !have_in)) {
+        D.u[s] = bu;
+        D.cost[s] = bc;
+        D.flags[s] = f0 | F_VALID;
+    }
 }
 
 // ---------------------------------------------------------------- init
@@ -427,12 +639,39 @@ pgm_status launch_init(const LvlBatch& B, const MatchConst& mc, int nch, int max
     return last_status();
 }
 
+// words per lane of the squared-L2 kernels, a few fixed sizes
+inline int mmax_of(int nch, int maxP) {
+    const int m = (maxP * maxP * (nch / 2) + 31) / 32;
+    const int sizes[6] = {2, 4, 8, 12, 16, 24};
+    for (int k = 0; k < 6; ++k)
+        if (m <= sizes[k]) return sizes[k];
+    return 24;
+}
+
+#define PGM_DISPATCH_X(KERNEL, GRID, ...)                                                  \
+    do {                                                                                   \
+        const int mm = mmax_of(nch, maxP);                                                 \
+        if (nch == 2) {                                                                    \
+            if (mm <= 2) KERNEL<2, 2><<<GRID, 256, 0, st>>>(__VA_ARGS__);                  \
+            else if (mm <= 4) KERNEL<2, 4><<<GRID, 256, 0, st>>>(__VA_ARGS__);             \
+            else KERNEL<2, 8><<<GRID, 256, 0, st>>>(__VA_ARGS__);                          \
+        } else {                                                                           \
+            if (mm <= 2) KERNEL<6, 2><<<GRID, 256, 0, st>>>(__VA_ARGS__);                  \
+            else if (mm <= 4) KERNEL<6, 4><<<GRID, 256, 0, st>>>(__VA_ARGS__);             \
+            else if (mm <= 8) KERNEL<6, 8><<<GRID, 256, 0, st>>>(__VA_ARGS__);             \
+            else if (mm <= 12) KERNEL<6, 12><<<GRID, 256, 0, st>>>(__VA_ARGS__);           \
+            else if (mm <= 16) KERNEL<6, 16><<<GRID, 256, 0, st>>>(__VA_ARGS__);           \
+            else KERNEL<6, 24><<<GRID, 256, 0, st>>>(__VA_ARGS__);                         \
+        }                                                                                  \
+    } while (0)
+
 pgm_status launch_cost_fill(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
                             int max_seeds, cudaStream_t st) {
     if (max_seeds <= 0) return PGM_OK;
     KScope ks(PGM_K_COST, st);
     dim3 g((max_seeds + 7) / 8, 2, B.n);
-    PGM_DISPATCH_NCH_PPL_NORM(k_cost, g, B, mc);
+    if (mc.norm == PGM_L2SQ) PGM_DISPATCH_X(k_cost_x, g, B, mc);
+    else PGM_DISPATCH_NCH_PPL_NORM(k_cost, g, B, mc);
     return last_status();
 }
 
@@ -441,7 +680,23 @@ pgm_status launch_pm_phase(const LvlBatch& B, const MatchConst& mc, int nch, int
     if (max_seeds <= 0) return PGM_OK;
     KScope ks(PGM_K_PM, st);
     dim3 g((max_seeds + 7) / 8, 2, B.n);   // max_seeds: half-row width x rows
-    PGM_DISPATCH_NCH_PPL_NORM(k_pm, g, B, mc);
+    if (mc.norm == PGM_L2SQ) {
+        bool handled = false;
+        pgm_status r = launch_pm_tile(B, mc, nch, maxP, &handled, st);
+        if (r != PGM_OK || handled) return r;
+        PGM_DISPATCH_X(k_pm_x, g, B, mc);
+    }
+    else PGM_DISPATCH_NCH_PPL_NORM(k_pm, g, B, mc);
+    return last_status();
+}
+
+pgm_status launch_box(const LvlBatch& B, int nch, int max_pixels, cudaStream_t st) {
+    if (max_pixels <= 0) return PGM_OK;
+    KScope ks(PGM_K_COST, st, 2);
+    dim3 g((max_pixels + 255) / 256, 2, B.n);
+    if (nch == 2) k_box_h<2><<<g, 256, 0, st>>>(B);
+    else k_box_h<6><<<g, 256, 0, st>>>(B);
+    k_box_v<<<g, 256, 0, st>>>(B);
     return last_status();
 }
 

@@ -33,7 +33,8 @@ struct PyrPlan {
     int space[2][MAXL];
     size_t cimg_off[2][MAXL];    // colour-converted image (aliases img if identity)
     size_t desc_off[2][MAXL];    // int16 descriptors, pixel-interleaved
-    int desc_row[MAXL];          // int16 elements per row
+    size_t split_off[2][MAXL];   // same words with each value split into two signed bytes
+    int desc_row[MAXL];          // int16 elements per row (also 16-bit halves of a split row)
     size_t bytes;
 };
 
@@ -41,6 +42,9 @@ struct WsPlan {
     int L;
     int nx[MAXL][2], ny[MAXL][2];
     size_t off_u[MAXL][2], off_cost[MAXL][2], off_flags[MAXL][2];
+    size_t off_sa2[MAXL][2];     // per seed: sum of |G|^2 over its reference patch
+    size_t off_sb2[MAXL][2];     // per target pixel: sum of |G|^2 over the patch there
+    size_t off_boxtmp[2];        // per direction: row sums of the box filter (level-0 size)
     size_t off_err;              // uint32 device status word
     size_t off_label, off_size, off_bsum;   // filter scratch (level-0 forward lattice)
     int nblk0;                   // blocks of the level-0 forward lattice scan
@@ -68,6 +72,7 @@ inline int rs_count(int W) { int K = 0; for (int w = W; w >= 1; w >>= 1) ++K; re
 struct DirLvl {
     const int16_t* ref;          // descriptor of the reference image (this dir)
     const int16_t* tgt;          // descriptor of the target image
+    const uint32_t* ref_split;   // reference descriptor in split-byte form
     int32_t ref_pitch, tgt_pitch;// int16 elements per row
     int32_t rw, rh, tw, th;      // reference / target image size
     int32_t nx, ny;              // lattice of this direction (on the reference)
@@ -79,6 +84,9 @@ struct DirLvl {
     uint8_t* flags;
     const int32_t* ou;           // other direction: displacement
     const uint8_t* oflags;       //                  flags
+    unsigned long long* sa2;     // per seed: sum over the reference patch of |G|^2
+    unsigned long long* sb2;     // per target pixel (row pitch tw): same over the target patch
+    unsigned long long* boxtmp;  // scratch of the box filter (row pitch tw)
 };
 
 struct LvlBatch {
@@ -128,6 +136,10 @@ pgm_status launch_pm_phase(const LvlBatch& B, const MatchConst& mc, int nch, int
 pgm_status launch_consist(const LvlBatch& B, const MatchConst& mc, int max_seeds,
                           cudaStream_t st);
 pgm_status launch_transfer(const XferBatch& X, int max_seeds, cudaStream_t st);
+pgm_status launch_box(const LvlBatch& B, int nch, int max_pixels, cudaStream_t st);
+// pm_tile.cu: *handled = false when the staged tile would not fit in shared memory
+pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
+                          bool* handled, cudaStream_t st);
 // filter.cu
 pgm_status launch_filter_ptrs(const pgm_params* p, int nx, int ny, const int32_t* u,
                               const uint8_t* flags, int* label, int* size, int* bsum,

@@ -1,0 +1,452 @@
+// pm_tile.cu -- one checkerboard colour phase of propagation (Eq. 4) and
+// limited random search (Eq. 5), squared-L2 cost, on seed tiles staged in
+// shared memory.
+//
+// A CTA owns an 8 x 8 tile of lattice seeds; the 32 seeds of the current
+// colour update, one warp per seed at a time.  Before any cost is computed the
+// CTA stages into shared memory
+//   - the reference region covering all patches of the tile, in the
+//     split-byte form (a = 128 a_h + a_l) that the dp2a cross products use;
+//   - a fixed-size target window around the tile's median displacement,
+//     wide enough for the random-search square plus a slack.
+// Both are staged in unclamped pixel coordinates with the image border
+// replicated, so the inner loop needs no border tests.
+//
+// Patch rows are padded to a multiple of 4 words (the padding words carry a
+// zero reference, so they add nothing), which makes every staged row 16-byte
+// aligned, and the shared row pitch is congruent to the padded row modulo 32:
+// the 32 consecutive words of a flattened patch that a warp reads fall in 32
+// different banks.  A candidate whose padded patch is not inside the window is
+// scored from global memory instead.  The cost of a candidate is
+//   D = sum |a|^2 + sum |b|^2 - 2 sum <a, b>,
+// exact in integers, with sum |a|^2 per seed and sum |b|^2 per target pixel
+// computed by other kernels of the same visit.
+#include <limits.h>
+
+#include "match_common.cuh"
+
+namespace pgm {
+
+constexpr int PT_TW = 8, PT_TH = 8;            // lattice seeds per tile
+constexpr int PT_NACT = PT_TW * PT_TH / 2;     // seeds of one colour per tile
+constexpr int PT_SLACK = 6;                    // window margin around the median match (px)
+
+struct PtGeom {
+    int wpp, wprp;         // words per pixel, padded words per patch row
+    int ref_w, ref_h;      // staged reference region (px), width a multiple of 4
+    int win_w, win_h;      // staged target window (px), width a multiple of 4
+    int sp;                // shared row pitch (words)
+    int cw, ch;            // candidate centres covered by the window
+    int words;             // 32-bit shared words in all (descriptor rows, then uint64 sums)
+};
+
+__host__ __device__ inline PtGeom pt_geom(int nch, int P, int sigma, int rs_W) {
+    PtGeom g;
+    g.wpp = nch / 2;
+    g.wprp = (P * g.wpp + 3) & ~3;
+    const int span_x = sigma * (PT_TW - 1) + P + 1;   // +1 px: padded words of the last patch
+    const int span_y = sigma * (PT_TH - 1) + P;
+    const int rho = rs_W > 1 ? rs_W : 1;
+    g.ref_w = ((span_x + 3) & ~3) + 4;                // origin is rounded down to 4 px
+    g.ref_h = span_y;
+    g.win_w = ((span_x + 2 * (rho + PT_SLACK) + 3) & ~3) + 4;
+    g.win_h = span_y + 2 * (rho + PT_SLACK);
+    const int need = (g.ref_w > g.win_w ? g.ref_w : g.win_w) * g.wpp;
+    g.sp = need + (((g.wprp - need) % 32) + 32) % 32;
+    g.cw = g.win_w - P;                               // centres whose padded patch fits
+    g.ch = g.win_h - P + 1;
+    g.words = g.sp * (g.ref_h + g.win_h) + 2 * g.cw * g.ch + 2;   // +2: 8-byte alignment
+    return g;
+}
+
+namespace {
+
+__device__ __forceinline__ int floor4(int v) { return v & ~3; }   // two's complement: floor
+
+// Copy a rows x (w px) block of 32-bit words with top-left pixel (x0, y0)
+// (x0 a multiple of 4) of an image (iw x ih px, row pitch pw words) to shared
+// memory (pitch sp), replicating the border.  Interior blocks move as 16-byte
+// vectors, others word by word.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ int lds32(unsigned addr) {
+    int v;
+    asm volatile("ld.shared.b32 %0, [%1];\n" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ unsigned long long lds64(unsigned addr) {
+    unsigned long long v;
+    asm volatile("ld.shared.b64 %0, [%1];\n" : "=l"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Start copying a rows x (w px) block of 32-bit words with top-left pixel
+// (x0, y0) (x0 a multiple of 4) of an image (iw x ih px, row pitch pw words)
+// into shared memory (pitch sp), replicating the border: asynchronous copies,
+// 16 bytes each for an interior block, one word each otherwise.  One warp per
+// row, lanes across it; completion by cp_async_wait_all.
+template <int WPP>
+__device__ __forceinline__ void stage(uint32_t* dst, int sp, const uint32_t* src, int pw, int iw,
+                                      int ih, int x0, int y0, int w, int rows) {
+    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int wwords = w * WPP;
+    if (x0 >= 0 && y0 >= 0 && x0 + w <= iw && y0 + rows <= ih) {
+        const int vec = wwords / 4;                   // w is a multiple of 4 px
+        for (int row = threadIdx.x >> 5; row < rows; row += nwarp) {
+            const uint32_t* s = src + (size_t)(y0 + row) * pw + (size_t)x0 * WPP;
+            for (int v = lane; v < vec; v += 32) cp_async16(dst + row * sp + 4 * v, s + 4 * v);
+        }
+    } else {
+        for (int row = threadIdx.x >> 5; row < rows; row += nwarp) {
+            const uint32_t* srow = src + (size_t)clampi(y0 + row, 0, ih - 1) * pw;
+            for (int wd = lane; wd < wwords; wd += 32) {
+                const int pix = wd / WPP, wi = wd - pix * WPP;      // WPP is 1 or 3
+                cp_async4(dst + row * sp + wd, srow + (size_t)clampi(x0 + pix, 0, iw - 1) * WPP + wi);
+            }
+        }
+    }
+}
+
+// Lane-owned words of the flattened (padded) patch: word k = lane + 32 m has
+// row k / wprp and column k % wprp; walked incrementally (no division).
+template <int MMAX>
+__device__ __forceinline__ void patch_walk(int lane, int wprp, int nw, int P_words, int sp,
+                                           int (&off)[MMAX], unsigned& vmask) {
+    int row = 0, col = lane;
+    while (col >= wprp) { col -= wprp; ++row; }
+    vmask = 0;
+#pragma unroll
+    for (int m = 0; m < MMAX; ++m) {
+        const int k = lane + 32 * m;
+        off[m] = k < nw ? 4 * (row * sp + col) : 0;       // byte offset
+        if (k < nw && col < P_words) vmask |= 1u << m;
+        col += 32;
+        while (col >= wprp) { col -= wprp; ++row; }
+    }
+}
+
+// cross term from global memory with replicated borders (fallback)
+template <int NCH, int MMAX>
+__device__ __forceinline__ long long cross_global(const int (&b)[MMAX], const DirLvl& D, int wprp,
+                                                  int qx, int qy, int lane) {
+    constexpr int WPP = NCH / 2;
+    const int P = D.P, h = P / 2, nw = P * wprp;
+    const int pitchw = D.tgt_pitch >> 1;
+    const uint32_t* t32 = reinterpret_cast<const uint32_t*>(D.tgt);
+    int sl = 0, sh = 0;
+#pragma unroll
+    for (int m = 0; m < MMAX; ++m)
+        if (32 * m < nw) {
+            const int k = lane + 32 * m;
+            const int row = k / wprp, col = k - row * wprp;
+            const int pix = col / WPP, wi = col - pix * WPP;
+            const int x = clampi(qx - h + pix, 0, D.tw - 1), y = clampi(qy - h + row, 0, D.th - 1);
+            const uint32_t v = __ldg(t32 + (size_t)y * pitchw + (size_t)x * WPP + wi);
+            sl = __dp2a_lo((int)v, b[m], sl);
+            sh = __dp2a_hi((int)v, b[m], sh);
+        }
+    sl = __reduce_add_sync(FULL, sl);
+    sh = __reduce_add_sync(FULL, sh);
+    return (long long)sh * 128 + (long long)sl;
+}
+
+struct TileCtx {
+    const uint32_t* s_ref; const uint32_t* s_tw; const unsigned long long* s_sb;
+    const int* s_seed; const int* s_u; const int (*s_nb)[2]; const unsigned char* s_f;
+    const unsigned long long* s_cost; const unsigned long long* s_sa; const uint4* s_rnd;
+    int i0, j0, rx0, wx0, wy0;
+    bool use_win;
+    int sig, h, P, nw, sx, sy, lane, warp;
+};
+
+constexpr int NO_CAND = INT_MIN;            // no propagated candidate
+
+// The seeds of one tile and colour, one warp each.  M = number of 32-word
+// groups of the flattened patch: no per-group test is needed, the words of
+// the last group that lie past the patch read a valid shared word and
+// multiply it by a zero reference.
+template <int NCH, int M>
+__device__ __forceinline__ void seeds(const LvlBatch& B, const MatchConst& mc, const DirLvl& D,
+                                      const PtGeom& G, const TileCtx& T) {
+    constexpr int WPP = NCH / 2;
+    const int lane = T.lane, P = T.P, h = T.h, sig = T.sig;
+    const int pair = blockIdx.z, dir = blockIdx.y;
+    const unsigned a_ref = (unsigned)__cvta_generic_to_shared(T.s_ref);
+    const unsigned a_tw = (unsigned)__cvta_generic_to_shared(T.s_tw);
+    const unsigned a_sb = (unsigned)__cvta_generic_to_shared(T.s_sb);
+    int off[M];                             // byte offsets of the lane's patch words
+    unsigned vmask;                         // bit m: word lane + 32 m is a real patch word
+    patch_walk<M>(lane, G.wprp, T.nw, P * WPP, G.sp, off, vmask);
+
+    for (int a = T.warp; a < PT_NACT; a += 8) {
+        const int s = T.s_seed[a];
+        if (s < 0) continue;
+        const int j = T.j0 + a / (PT_TW / 2);
+        const int i = T.i0 + 2 * (a % (PT_TW / 2)) + ((j + mc.colour) & 1);
+        const int px = mc.c + sig * i, py = mc.c + sig * j;
+        const uint8_t f0 = T.s_f[a];
+        bool have = f0 & F_VALID;
+        int32_t bu = T.s_u[a];
+        unsigned long long bc = have ? T.s_cost[a] : INF;
+        const int32_t u_in = bu;
+        const bool have_in = have;
+        const unsigned long long sa = T.s_sa[a];
+
+        int b[M];
+        bool loaded = false;
+        unsigned n_eval = 0, n_glob = 0;
+        auto score = [&](int qx, int qy) -> unsigned long long {
+            if (!loaded) {
+                const unsigned rbase =
+                    a_ref + 4u * (unsigned)(sig * (j - T.j0) * G.sp + (mc.c + sig * i - h - T.rx0) * WPP);
+#pragma unroll
+                for (int m = 0; m < M; ++m)         // masked, branch-free
+                    b[m] = lds32(rbase + (unsigned)off[m]) & (int)(0u - ((vmask >> m) & 1u));
+                loaded = true;
+            }
+            unsigned long long sb;
+            long long cr;
+            const int x0 = qx - h - T.wx0, y0 = qy - h - T.wy0;
+            if (T.use_win && x0 >= 0 && y0 >= 0 && x0 + P + 1 <= G.win_w && y0 + P <= G.win_h) {
+                sb = lds64(a_sb + 8u * (unsigned)(y0 * G.cw + x0));
+                const unsigned base = a_tw + 4u * (unsigned)(y0 * G.sp + x0 * WPP);
+                int sl0 = 0, sh0 = 0, sl1 = 0, sh1 = 0;     // two chains each
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const int v = lds32(base + (unsigned)off[m]);
+                    if (m & 1) { sl1 = __dp2a_lo(v, b[m], sl1); sh1 = __dp2a_hi(v, b[m], sh1); }
+                    else { sl0 = __dp2a_lo(v, b[m], sl0); sh0 = __dp2a_hi(v, b[m], sh0); }
+                }
+                const int sl = __reduce_add_sync(FULL, sl0 + sl1);
+                const int sh = __reduce_add_sync(FULL, sh0 + sh1);
+                cr = (long long)sh * 128 + (long long)sl;
+            } else {
+                sb = D.sb2[(size_t)qy * D.tw + qx];
+                cr = cross_global<NCH, M>(b, D, G.wprp, qx, qy, lane);
+                ++n_glob;
+            }
+            ++n_eval;
+            return xcost(sa, sb, cr);
+        };
+
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {           // Eq. 4
+            const int32_t cu = T.s_nb[a][k];
+            if (cu == NO_CAND) continue;
+            if (have && cu == bu) continue;
+            const int qx = px + lo16((uint32_t)cu), qy = py + hi16((uint32_t)cu);
+            if (!inside(D, qx, qy)) continue;
+            const unsigned long long c = score(qx, qy);
+            if (c < bc) { bc = c; bu = cu; have = true; }
+        }
+        if (have) {
+            const int ux0 = lo16((uint32_t)bu), uy0 = hi16((uint32_t)bu);
+            uint4 r = T.s_rnd[a];
+            for (int k = 0; k < mc.K; ++k) {    // Eq. 5
+                if (k > 0 && (k & 1) == 0)
+                    r = philox(make_uint4((uint32_t)s,
+                                          ((uint32_t)B.visit << 16) | ((uint32_t)dir << 15) | (uint32_t)mc.t,
+                                          ((uint32_t)B.level << 16) | (uint32_t)(k >> 1),
+                                          B.stream_id[pair]),
+                               mc.key0, mc.key1);
+                const uint32_t rx = (k & 1) ? r.z : r.x, ry = (k & 1) ? r.w : r.y;
+                const int dx = rs_off(rx, k, mc.rs_W, mc.rs_mode), dy = rs_off(ry, k, mc.rs_W, mc.rs_mode);
+                if (dx == 0 && dy == 0) continue;
+                const int cx = ux0 + dx, cy = uy0 + dy;
+                const int qx = px + cx, qy = py + cy;
+                if (!inside(D, qx, qy)) continue;
+                const unsigned long long c = score(qx, qy);
+                if (c < bc) { bc = c; bu = pack_u(cx, cy); }
+            }
+        }
+        if (lane == 0) {
+            if (n_eval) atomicAdd(B.evals[pair] + dir, (unsigned long long)n_eval);
+            if (n_glob) atomicAdd(B.evals[pair] + 6 + dir, (unsigned long long)n_glob);
+            if (have && (bu != u_in || !have_in)) {
+                D.u[s] = bu;
+                D.cost[s] = bc;
+                D.flags[s] = f0 | F_VALID;
+            }
+        }
+    }
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(256, (NCH == 6 ? 2 : 3))
+k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
+    constexpr int WPP = NCH / 2;
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ int s_seed[PT_NACT];         // seed index, -1 if none
+    __shared__ int s_u[PT_NACT];            // current displacement
+    __shared__ int s_nb[PT_NACT][2];        // propagated displacement, or the sentinel
+    __shared__ unsigned char s_f[PT_NACT];  // flags
+    __shared__ unsigned long long s_cost[PT_NACT], s_sa[PT_NACT];
+    __shared__ uint4 s_rnd[PT_NACT];        // Philox block 0 of the seed (random search)
+    __shared__ int s_med[2];
+
+    const int pair = blockIdx.z, dir = blockIdx.y;
+    const DirLvl& D = B.d[pair][dir];
+    const int tiles_x = (D.nx + PT_TW - 1) / PT_TW, tiles_y = (D.ny + PT_TH - 1) / PT_TH;
+    if ((int)blockIdx.x >= tiles_x * tiles_y) return;
+    const int i0 = ((int)blockIdx.x % tiles_x) * PT_TW, j0 = ((int)blockIdx.x / tiles_x) * PT_TH;
+    const int P = D.P, h = P / 2;
+    const int sig = mc.sigma;
+    const PtGeom G = pt_geom(NCH, P, sig, mc.rs_W);
+    const int nw = P * G.wprp;
+    uint32_t* s_ref = sm;
+    uint32_t* s_tw = sm + G.ref_h * G.sp;
+    const int t4 = mc.t & 3;
+    const int sx = (t4 == 0 || t4 == 3) ? 1 : -1, sy = (t4 == 0 || t4 == 2) ? 1 : -1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // ---- C1: start staging the reference region (independent of the seeds)
+    const int rx0 = floor4(mc.c + sig * i0 - h), ry0 = mc.c + sig * j0 - h;
+    stage<WPP>(s_ref, G.sp, D.ref_split, D.ref_pitch >> 1, D.rw, D.rh, rx0, ry0, G.ref_w, G.ref_h);
+
+    // ---- A: the active seeds (warp 0, one lane per seed)
+    if (warp == 0) {
+        const int a = lane, r = a / (PT_TW / 2), k = a % (PT_TW / 2);
+        const int j = j0 + r, i = i0 + 2 * k + ((j + mc.colour) & 1);
+        int s = -1, u = 0, f = 0;
+        if (i < D.nx && j < D.ny) {
+            s = j * D.nx + i;
+            const int ni = i - sx, nj = j - sy;
+            const bool okx = ni >= 0 && ni < D.nx, oky = nj >= 0 && nj < D.ny;
+            const int sn0 = okx ? j * D.nx + ni : s, sn1 = oky ? nj * D.nx + i : s;
+            // independent loads, issued together
+            f = D.flags[s];
+            u = D.u[s];
+            const unsigned long long cst = D.cost[s], sa2 = D.sa2[s];
+            const int f0 = D.flags[sn0], f1 = D.flags[sn1];
+            const int u0 = D.u[sn0], u1 = D.u[sn1];
+            s_cost[a] = cst;
+            s_sa[a] = sa2;
+            s_nb[a][0] = (okx && (f0 & F_VALID)) ? u0 : NO_CAND;
+            s_nb[a][1] = (oky && (f1 & F_VALID)) ? u1 : NO_CAND;
+            if (mc.K > 0)
+                s_rnd[a] = philox(make_uint4((uint32_t)s,
+                                             ((uint32_t)B.visit << 16) | ((uint32_t)dir << 15) | (uint32_t)mc.t,
+                                             ((uint32_t)B.level << 16), B.stream_id[pair]),
+                                  mc.key0, mc.key1);
+        }
+        s_seed[a] = s;
+        s_u[a] = u;
+        s_f[a] = (unsigned char)f;
+        // median of the valid current displacements: rank by (value, lane)
+        const bool v = s >= 0 && (f & F_VALID);
+        const unsigned vm = __ballot_sync(FULL, v);
+        const int nv = __popc(vm);
+        const int ux = lo16((uint32_t)u), uy = hi16((uint32_t)u);
+        int rx = 0, ry = 0;
+        for (int o = 0; o < 32; ++o) {
+            const int ox = __shfl_sync(FULL, ux, o), oy = __shfl_sync(FULL, uy, o);
+            if ((vm >> o) & 1) {
+                rx += ox < ux || (ox == ux && o < lane);
+                ry += oy < uy || (oy == uy && o < lane);
+            }
+        }
+        if (lane == 0) { s_med[0] = INT_MIN; s_med[1] = INT_MIN; }
+        __syncwarp();
+        if (v && rx == nv / 2) s_med[0] = ux;
+        if (v && ry == nv / 2) s_med[1] = uy;
+    }
+    __syncthreads();
+
+    // ---- B: window around the median match (unclamped pixel coordinates)
+    const int rho = max(1, mc.rs_W);
+    const bool use_win = s_med[0] != INT_MIN;
+    const int wx0 = use_win ? floor4(mc.c + sig * i0 - h + s_med[0] - rho - PT_SLACK) : 0;
+    const int wy0 = use_win ? mc.c + sig * j0 - h + s_med[1] - rho - PT_SLACK : 0;
+
+    // ---- C2: stage the window and its sums of |b|^2
+    unsigned long long* s_sb = reinterpret_cast<unsigned long long*>(
+        sm + ((G.sp * (G.ref_h + G.win_h) + 1) & ~1));
+    if (use_win) {
+        stage<WPP>(s_tw, G.sp, reinterpret_cast<const uint32_t*>(D.tgt), D.tgt_pitch >> 1, D.tw,
+                   D.th, wx0, wy0, G.win_w, G.win_h);
+        // sum |b|^2 of every centre whose patch lies in the window (centres
+        // outside the image are never scored; their entries are don't-care)
+        const int cx0 = wx0 + h, cy0 = wy0 + h;
+        for (int row = warp; row < G.ch; row += 8) {
+            const unsigned long long* srow = D.sb2 + (size_t)clampi(cy0 + row, 0, D.th - 1) * D.tw;
+            for (int col = lane; col < G.cw; col += 32)
+                cp_async8(s_sb + row * G.cw + col, srow + clampi(cx0 + col, 0, D.tw - 1));
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    // ---- D: one warp per active seed, specialised on the exact number of
+    // 32-word groups of this direction's patch
+    TileCtx T{s_ref, s_tw, s_sb, s_seed, s_u, s_nb, s_f, s_cost, s_sa, s_rnd,
+              i0, j0, rx0, wx0, wy0, use_win, sig, h, P, nw, sx, sy, lane, warp};
+    const int groups = (nw + 31) / 32;
+    if (NCH == 6) {
+        if (groups <= 4) seeds<NCH, 4>(B, mc, D, G, T);
+        else if (groups <= 8) seeds<NCH, 8>(B, mc, D, G, T);
+        else if (groups <= 13) seeds<NCH, 13>(B, mc, D, G, T);
+        else if (groups <= 16) seeds<NCH, 16>(B, mc, D, G, T);
+        else if (groups <= 23) seeds<NCH, 23>(B, mc, D, G, T);
+        else seeds<NCH, 24>(B, mc, D, G, T);
+    } else {
+        if (groups <= 2) seeds<NCH, 2>(B, mc, D, G, T);
+        else if (groups <= 5) seeds<NCH, 5>(B, mc, D, G, T);
+        else seeds<NCH, 8>(B, mc, D, G, T);
+    }
+}
+
+template <int NCH>
+pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, int tiles, int smem_bytes,
+                    cudaStream_t st) {
+    static int configured = 0;                 // opt-in above 48 KB once per instantiation
+    if (configured < smem_bytes) {
+        if (cudaFuncSetAttribute(k_pm_t<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_bytes) != cudaSuccess) return PGM_ERR_CUDA;
+        configured = smem_bytes;
+    }
+    k_pm_t<NCH><<<dim3(tiles, 2, B.n), 256, smem_bytes, st>>>(B, mc);
+    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+}
+
+}  // namespace
+
+// *handled = false when the staged tile would not fit in shared memory; the
+// caller then uses the per-seed kernel.
+pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
+                          bool* handled, cudaStream_t st) {
+    (void)maxP;
+    *handled = false;
+    int tiles = 0, words = 0, maxw = 0;
+    for (int k = 0; k < B.n; ++k)
+        for (int d = 0; d < 2; ++d) {
+            const DirLvl& D = B.d[k][d];
+            const int t = ((D.nx + PT_TW - 1) / PT_TW) * ((D.ny + PT_TH - 1) / PT_TH);
+            if (t > tiles) tiles = t;
+            const PtGeom g = pt_geom(nch, D.P, mc.sigma, mc.rs_W);
+            if (g.words > words) words = g.words;
+            const int nwp = D.P * g.wprp;
+            if (nwp > maxw) maxw = nwp;
+        }
+    const int smem_bytes = words * 4;
+    if (smem_bytes > 160 * 1024) return PGM_OK;
+    *handled = true;
+    if (tiles == 0) return PGM_OK;
+    if ((maxw + 31) / 32 > 24) return PGM_ERR_UNSUPPORTED;
+    return nch == 2 ? launch_t<2>(B, mc, tiles, smem_bytes, st)
+                    : launch_t<6>(B, mc, tiles, smem_bytes, st);
+}
+
+}  // namespace pgm

@@ -9,12 +9,10 @@
 //   per level and direction: Sobel gradients Gx, Gy (Eq. 1-2), S = 3 or 5,
 //            replicated border, int16, pixel-interleaved; for the direction
 //            descriptor (Sec. III-F) their signs.
-#include "pgm_device.cuh"
+#include "match_common.cuh"
 
 namespace pgm {
 namespace {
-
-__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
 __device__ __forceinline__ int gray_q14(int r, int g, int b) {
     // BT.601 luma weights 0.299, 0.587, 0.114 in Q14 (sum 16384)
@@ -137,7 +135,8 @@ __global__ void k_convert(const uint8_t* __restrict__ in, uint8_t* __restrict__ 
 // Gx = sum_j s_j sum_i d_i I(x+i, y+j); Gy with the roles of the axes swapped.
 template <int S, int C>
 __global__ void k_sobel(const uint8_t* __restrict__ in, int w, int h, int row, size_t plane,
-                        int16_t* __restrict__ out, int orow, int dir_only) {
+                        int16_t* __restrict__ out, uint32_t* __restrict__ split, int orow,
+                        int dir_only) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= w || y >= h) return;
@@ -176,10 +175,15 @@ __global__ void k_sobel(const uint8_t* __restrict__ in, int w, int h, int row, s
         g[C + ch] = gy;
     }
     // pixel-interleaved int16, written as 32-bit words (2C is even)
-    uint32_t* dst = reinterpret_cast<uint32_t*>(out + (size_t)y * orow + (size_t)x * 2 * C);
+    // and the same words with every value a split into signed bytes
+    // a = 128 a_h + a_l (a_l in [-64, 63]) for the dp2a cross products
+    const size_t w0 = ((size_t)y * orow + (size_t)x * 2 * C) / 2;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(out) + w0;
 #pragma unroll
-    for (int k = 0; k < C; ++k)
+    for (int k = 0; k < C; ++k) {
         dst[k] = (uint32_t)(uint16_t)g[2 * k] | ((uint32_t)(uint16_t)g[2 * k + 1] << 16);
+        split[w0 + k] = (uint32_t)split_bytes(g[2 * k], g[2 * k + 1]);
+    }
 }
 
 }  // namespace
@@ -211,22 +215,23 @@ pgm_status launch_pyramid(const pgm_params* p, const PyrPlan& pp, const uint8_t*
                     pp.img_row[l], pp.img_plane[l], sp);
             const uint8_t* ci = d_pyr + pp.cimg_off[s][l];
             int16_t* de = reinterpret_cast<int16_t*>(d_pyr + pp.desc_off[s][l]);
+            uint32_t* sp_ = reinterpret_cast<uint32_t*>(d_pyr + pp.split_off[s][l]);
             dim3 g = grid(pp.W[l], pp.H[l], 1);
             int dir_only = p->descriptor == PGM_DIR;
             if (p->sobel == 5) {
                 if (pp.C == 1)
                     k_sobel<5, 1><<<g, blk, 0, st>>>(ci, pp.W[l], pp.H[l], pp.img_row[l],
-                                                     pp.img_plane[l], de, pp.desc_row[l], dir_only);
+                                                     pp.img_plane[l], de, sp_, pp.desc_row[l], dir_only);
                 else
                     k_sobel<5, 3><<<g, blk, 0, st>>>(ci, pp.W[l], pp.H[l], pp.img_row[l],
-                                                     pp.img_plane[l], de, pp.desc_row[l], dir_only);
+                                                     pp.img_plane[l], de, sp_, pp.desc_row[l], dir_only);
             } else {
                 if (pp.C == 1)
                     k_sobel<3, 1><<<g, blk, 0, st>>>(ci, pp.W[l], pp.H[l], pp.img_row[l],
-                                                     pp.img_plane[l], de, pp.desc_row[l], dir_only);
+                                                     pp.img_plane[l], de, sp_, pp.desc_row[l], dir_only);
                 else
                     k_sobel<3, 3><<<g, blk, 0, st>>>(ci, pp.W[l], pp.H[l], pp.img_row[l],
-                                                     pp.img_plane[l], de, pp.desc_row[l], dir_only);
+                                                     pp.img_plane[l], de, sp_, pp.desc_row[l], dir_only);
             }
         }
     return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
