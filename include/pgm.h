@@ -111,6 +111,16 @@ size_t pgm_pyramid_bytes(const pgm_params* p, int w, int h);
 pgm_status pgm_build_pyramid(const pgm_params* p, const uint8_t* d_img, int w, int h, int c,
                              size_t pitch, void* d_pyr, size_t pyr_bytes, void* stream);
 
+/* Build the pyramids of n images (same params, sizes may differ) in shared
+ * launches: one launch per pyramid step for the whole batch.  Host arrays of
+ * length n: d_imgs[i]; dims[3*i..3*i+2] = (w, h, c); pitches[i] (bytes);
+ * d_pyrs[i] (256-byte aligned); pyr_bytes[i].  Each result equals
+ * pgm_build_pyramid on that image alone.  Every image is checked before any
+ * launch; errors as pgm_build_pyramid. */
+pgm_status pgm_build_pyramid_batch(const pgm_params* p, int n, const uint8_t* const* d_imgs,
+                                   const int32_t* dims, const size_t* pitches,
+                                   void* const* d_pyrs, const size_t* pyr_bytes, void* stream);
+
 /* Where one level's descriptor lives inside a pyramid buffer (for tests and
  * tools): int16 values, pixel-interleaved, `nch` = 2C channels per pixel in
  * the order Gx of each colour channel, then Gy of each; rows `row_elems`
@@ -191,6 +201,15 @@ pgm_status pgm_field_layout(const pgm_params* p, int w1, int h1, int w2, int h2,
 pgm_status pgm_filter(const pgm_params* p, int w1, int h1, int w2, int h2, void* d_ws,
                       size_t ws_bytes, int32_t* d_matches, int64_t max_matches,
                       int32_t* d_count, uint8_t* d_keep, void* stream);
+
+/* pgm_filter on n workspaces in shared launches (six in all).  Host arrays
+ * of length n: dims[4*i..4*i+3] = (w1, h1, w2, h2); d_ws[i], ws_bytes[i];
+ * d_matches[i] ([max_matches[i]][4] int32, 16-byte aligned); d_counts[i]
+ * (device int32).  Each result equals pgm_filter on that workspace alone.
+ * Every pair is checked before any launch; errors as pgm_filter. */
+pgm_status pgm_filter_batch(const pgm_params* p, int n, const int32_t* dims, void* const* d_ws,
+                            const size_t* ws_bytes, int32_t* const* d_matches,
+                            const int64_t* max_matches, int32_t* const* d_counts, void* stream);
 
 /* The same final filter for callers that cannot allocate device memory.
  * The paper has no counterpart; this is a deployment convenience.

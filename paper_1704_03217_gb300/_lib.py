@@ -31,7 +31,7 @@ EXPORTS = [
     "pgm_pyramid_desc_layout", "pgm_pyramid_image_layout", "pgm_match_workspace_bytes",
     "pgm_match", "pgm_match_batch", "pgm_field_layout", "pgm_filter", "pgm_sync_status",
     "pgm_nominal_evals", "pgm_launch_count", "pgm_profile_enable", "pgm_profile_read",
-    "pgm_filter_noalloc",
+    "pgm_filter_noalloc", "pgm_build_pyramid_batch", "pgm_filter_batch",
 ]
 NOALLOC_MAX_SEEDS = 1 << 20
 K_CLASSES = ["pyramid", "init", "cost", "pm", "consist", "transfer", "filter"]
@@ -78,7 +78,12 @@ def load(path: str = LIB_PATH):
     L.pgm_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.pgm_profile_read.restype = C.c_int
     L.pgm_filter_noalloc.argtypes = [P, i32, i32, vp, vp, vp, i64, vp, vp]
-    for name in ("pgm_filter_noalloc", "pgm_build_pyramid", "pgm_pyramid_desc_layout", "pgm_pyramid_image_layout",
+    L.pgm_build_pyramid_batch.argtypes = [P, i32, C.POINTER(vp), C.POINTER(C.c_int32), psz,
+                                          C.POINTER(vp), psz, vp]
+    L.pgm_filter_batch.argtypes = [P, i32, C.POINTER(C.c_int32), C.POINTER(vp), psz,
+                                   C.POINTER(vp), C.POINTER(C.c_int64), C.POINTER(vp), vp]
+    for name in ("pgm_filter_noalloc", "pgm_build_pyramid_batch", "pgm_filter_batch",
+                 "pgm_build_pyramid", "pgm_pyramid_desc_layout", "pgm_pyramid_image_layout",
                  "pgm_match", "pgm_match_batch", "pgm_field_layout", "pgm_filter",
                  "pgm_sync_status"):
         getattr(L, name).restype = C.c_int

@@ -185,6 +185,39 @@ def match_batch(params: Params, pyrs1, pyrs2, stream_ids, wss, stream=None):
     return wss
 
 
+def build_pyramids(params: Params, imgs, pyrs, stream=None):
+    """Build many pyramids in shared launches (pgm_build_pyramid_batch)."""
+    n = len(imgs)
+    cp = params.cstruct()
+    for img, p in zip(imgs, pyrs):
+        if img.dtype != torch.uint8 or not img.is_cuda or img.shape[0] != p.h or img.shape[1] != p.w:
+            raise ValueError("image/pyramid mismatch")
+    I = (C.c_void_p * n)(*[x.data_ptr() for x in imgs])
+    dims = (C.c_int32 * (3 * n))(*[v for x in imgs
+                                     for v in (x.shape[1], x.shape[0], 1 if x.dim() == 2 else x.shape[2])])
+    pit = (C.c_size_t * n)(*[x.stride(0) for x in imgs])
+    P = (C.c_void_p * n)(*[p.buf.data_ptr() for p in pyrs])
+    PB = (C.c_size_t * n)(*[p.buf.numel() for p in pyrs])
+    check(_lib.load().pgm_build_pyramid_batch(C.byref(cp), n, I, dims, pit, P, PB, _stream(stream)),
+          "pgm_build_pyramid_batch")
+    return pyrs
+
+
+def filter_batch(params: Params, wss, rows, counts, stream=None):
+    """pgm_filter on many workspaces in shared launches.  rows[k]: [max, 4]
+    int32, counts[k]: [1] int32 (device)."""
+    n = len(wss)
+    cp = params.cstruct()
+    dims = (C.c_int32 * (4 * n))(*[v for w in wss for v in w.dims])
+    W = (C.c_void_p * n)(*[w.buf.data_ptr() for w in wss])
+    WB = (C.c_size_t * n)(*[w.buf.numel() for w in wss])
+    R = (C.c_void_p * n)(*[r.data_ptr() for r in rows])
+    RM = (C.c_int64 * n)(*[r.shape[0] for r in rows])
+    CN = (C.c_void_p * n)(*[c.data_ptr() for c in counts])
+    check(_lib.load().pgm_filter_batch(C.byref(cp), n, dims, W, WB, R, RM, CN, _stream(stream)),
+          "pgm_filter_batch")
+
+
 def filter_into(params: Params, ws: Workspace, matches: torch.Tensor, count: torch.Tensor,
                 keep: torch.Tensor = None, stream=None):
     """Enqueue the final filter into preallocated matches [max, 4] int32 and
@@ -226,14 +259,12 @@ class PairMatcher:
 
     def enqueue(self, imgs1, imgs2, stream_ids=None, stream=None):
         """Whole hot path on the device for the batch: pyramids, matching,
-        filter.  imgs*: lists of uint8 CUDA tensors."""
-        for k in range(self.batch):
-            self.p1[k].build(imgs1[k], stream)
-            self.p2[k].build(imgs2[k], stream)
+        filter (three C-ABI calls).  imgs*: lists of uint8 CUDA tensors."""
+        build_pyramids(self.params, list(imgs1) + list(imgs2), self.p1 + self.p2, stream)
         sids = list(range(self.batch)) if stream_ids is None else stream_ids
         match_batch(self.params, self.p1, self.p2, sids, self.ws, stream)
-        for k in range(self.batch):
-            filter_into(self.params, self.ws[k], self.rows[k], self.count[k], None, stream)
+        filter_batch(self.params, self.ws, [self.rows[k] for k in range(self.batch)],
+                     [self.count[k] for k in range(self.batch)], stream)
 
     def results(self):
         counts = self.count[:, 0].tolist()

@@ -374,8 +374,48 @@ pgm_status pgm_build_pyramid(const pgm_params* p, const uint8_t* d_img, int w, i
     PyrPlan pp;
     if (!make_pyr_plan(p, w, h, &pp)) return PGM_ERR_ARG;
     if (pyr_bytes < pp.bytes) return PGM_ERR_WORKSPACE;
-    return launch_pyramid(p, pp, d_img, c, pitch, static_cast<uint8_t*>(d_pyr),
-                          static_cast<cudaStream_t>(stream));
+    uint8_t* pyr = static_cast<uint8_t*>(d_pyr);
+    return launch_pyramid_batch(p, 1, &pp, &d_img, &c, &pitch, &pyr,
+                                static_cast<cudaStream_t>(stream));
+}
+
+pgm_status pgm_build_pyramid_batch(const pgm_params* p, int n, const uint8_t* const* d_imgs,
+                                   const int32_t* dims, const size_t* pitches,
+                                   void* const* d_pyrs, const size_t* pyr_bytes, void* stream) {
+    pgm_status r = check_params(p);
+    if (r != PGM_OK) return r;
+    if (n < 0 || (n > 0 && (!d_imgs || !dims || !pitches || !d_pyrs || !pyr_bytes)))
+        return PGM_ERR_ARG;
+    if (n == 0) return PGM_OK;
+    static thread_local PyrPlan plans[PYR_MAXB];
+    static thread_local int cs[PYR_MAXB];
+    static thread_local uint8_t* pyrs[PYR_MAXB];
+    for (int base = 0; base < n; base += PYR_MAXB) {
+        const int m = n - base < PYR_MAXB ? n - base : PYR_MAXB;
+        for (int k = 0; k < m; ++k) {          // every image is checked before any launch
+            const int i = base + k;
+            const int w = dims[3 * i], h = dims[3 * i + 1], c = dims[3 * i + 2];
+            if (!d_imgs[i] || !d_pyrs[i] || (c != 1 && c != 3) || (p->color == PGM_RGB && c != 3))
+                return PGM_ERR_ARG;
+            if (w < 1 || h < 1 || w > 32767 || h > 32767) return PGM_ERR_SIZE;
+            if (pitches[i] < (size_t)w * c || ((uintptr_t)d_pyrs[i] & 255u)) return PGM_ERR_ARG;
+            if (!make_pyr_plan(p, w, h, &plans[k])) return PGM_ERR_ARG;
+            if (pyr_bytes[i] < plans[k].bytes) return PGM_ERR_WORKSPACE;
+        }
+    }
+    for (int base = 0; base < n; base += PYR_MAXB) {
+        const int m = n - base < PYR_MAXB ? n - base : PYR_MAXB;
+        for (int k = 0; k < m; ++k) {
+            const int i = base + k;
+            make_pyr_plan(p, dims[3 * i], dims[3 * i + 1], &plans[k]);
+            cs[k] = dims[3 * i + 2];
+            pyrs[k] = static_cast<uint8_t*>(d_pyrs[i]);
+        }
+        r = launch_pyramid_batch(p, m, plans, d_imgs + base, cs, pitches + base, pyrs,
+                                 static_cast<cudaStream_t>(stream));
+        if (r != PGM_OK) return r;
+    }
+    return PGM_OK;
 }
 
 pgm_status pgm_pyramid_desc_layout(const pgm_params* p, int w, int h, int scheme, int level,
@@ -475,6 +515,43 @@ pgm_status pgm_filter(const pgm_params* p, int w1, int h1, int w2, int h2, void*
     if (ws_bytes < wp.bytes) return PGM_ERR_WORKSPACE;
     return launch_filter(p, wp, static_cast<uint8_t*>(d_ws), d_matches, max_matches, d_count,
                          d_keep, static_cast<cudaStream_t>(stream));
+}
+
+pgm_status pgm_filter_batch(const pgm_params* p, int n, const int32_t* dims, void* const* d_ws,
+                            const size_t* ws_bytes, int32_t* const* d_matches,
+                            const int64_t* max_matches, int32_t* const* d_counts, void* stream) {
+    pgm_status r = check_params(p);
+    if (r != PGM_OK) return r;
+    if (n < 0 || (n > 0 && (!dims || !d_ws || !ws_bytes || !d_matches || !max_matches ||
+                            !d_counts)))
+        return PGM_ERR_ARG;
+    static thread_local FiltBatch F;
+    static thread_local WsPlan wp;
+    for (int i = 0; i < n; ++i) {               // every pair is checked before any launch
+        if (!d_ws[i] || !d_counts[i] || max_matches[i] < 0 ||
+            (max_matches[i] > 0 && !d_matches[i]) || (((uintptr_t)d_matches[i]) & 15u))
+            return PGM_ERR_ARG;
+        if (!make_ws_plan(p, dims[4 * i], dims[4 * i + 1], dims[4 * i + 2], dims[4 * i + 3], &wp))
+            return PGM_ERR_ARG;
+        if (ws_bytes[i] < wp.bytes) return PGM_ERR_WORKSPACE;
+    }
+    filter_consts(p, &F);
+    for (int base = 0; base < n; base += MAXB) {
+        const int m = n - base < MAXB ? n - base : MAXB;
+        F.n = m;
+        int max_seeds = 0;
+        for (int k = 0; k < m; ++k) {
+            const int i = base + k;
+            make_ws_plan(p, dims[4 * i], dims[4 * i + 1], dims[4 * i + 2], dims[4 * i + 3], &wp);
+            filter_item(wp, static_cast<uint8_t*>(d_ws[i]), d_matches[i], max_matches[i],
+                        d_counts[i], nullptr, &F.it[k]);
+            const int ns = F.it[k].nx * F.it[k].ny;
+            if (ns > max_seeds) max_seeds = ns;
+        }
+        r = launch_filter_batch(p, F, max_seeds, static_cast<cudaStream_t>(stream));
+        if (r != PGM_OK) return r;
+    }
+    return PGM_OK;
 }
 
 pgm_status pgm_sync_status(const pgm_params* p, int w1, int h1, int w2, int h2, void* d_ws,

@@ -38,14 +38,6 @@ __device__ __forceinline__ int find_halve(int* L, int a) {
     return a;
 }
 
-__global__ void k_cc_init(const uint8_t* __restrict__ flags, int n, int* __restrict__ label,
-                          int* __restrict__ size) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    label[s] = inlier(flags[s]) ? s : -1;
-    size[s] = 0;
-}
-
 __device__ void unite(int* L, int a, int b) {
     // link the larger root below the smaller one; retry if another thread
     // re-linked the root in between
@@ -60,126 +52,166 @@ __device__ void unite(int* L, int a, int b) {
     }
 }
 
-__global__ void k_cc_link(const uint8_t* __restrict__ flags, const int32_t* __restrict__ u,
-                          int nx, int ny, int dmax2, int* label) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nx * ny || !inlier(flags[s])) return;
-    int i = s % nx, j = s / nx;
-    int32_t us = u[s];
-    if (i + 1 < nx && inlier(flags[s + 1])) {
-        int32_t ut = u[s + 1];
-        long long dx = lo16(us) - lo16(ut), dy = hi16(us) - hi16(ut);
-        if (dx * dx + dy * dy < dmax2) unite(label, s, s + 1);
+// All kernels take a batch of fields: blockIdx.y (blockIdx.x for the scan)
+// selects the pair; blocks past a pair's seed count return.
+__global__ void k_cc_init(const __grid_constant__ FiltBatch F) {
+    const FiltItem& it = F.it[blockIdx.y];
+    const int n = it.nx * it.ny;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    it.label[s] = inlier(it.flags[s]) ? s : -1;
+    it.size[s] = 0;
+}
+
+__global__ void k_cc_link(const __grid_constant__ FiltBatch F) {
+    const FiltItem& it = F.it[blockIdx.y];
+    const int nx = it.nx, ny = it.ny;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nx * ny || !inlier(it.flags[s])) return;
+    const int i = s % nx, j = s / nx;
+    const int32_t us = it.u[s];
+    if (i + 1 < nx && inlier(it.flags[s + 1])) {
+        const int32_t ut = it.u[s + 1];
+        const long long dx = lo16(us) - lo16(ut), dy = hi16(us) - hi16(ut);
+        if (dx * dx + dy * dy < F.dmax2) unite(it.label, s, s + 1);
     }
-    if (j + 1 < ny && inlier(flags[s + nx])) {
-        int32_t ut = u[s + nx];
-        long long dx = lo16(us) - lo16(ut), dy = hi16(us) - hi16(ut);
-        if (dx * dx + dy * dy < dmax2) unite(label, s, s + nx);
+    if (j + 1 < ny && inlier(it.flags[s + nx])) {
+        const int32_t ut = it.u[s + nx];
+        const long long dx = lo16(us) - lo16(ut), dy = hi16(us) - hi16(ut);
+        if (dx * dx + dy * dy < F.dmax2) unite(it.label, s, s + nx);
     }
 }
 
-__global__ void k_cc_flatten(int n, int* label, int* size) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n || label[s] < 0) return;
+__global__ void k_cc_flatten(const __grid_constant__ FiltBatch F) {
+    const FiltItem& it = F.it[blockIdx.y];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= it.nx * it.ny || it.label[s] < 0) return;
     // read-only find: a halving store by another thread could otherwise
     // overwrite the root just written to label[s] with a non-root ancestor
-    int r = find_root(label, s);
-    label[s] = r;
-    atomicAdd(&size[r], 1);
+    const int r = find_root(it.label, s);
+    it.label[s] = r;
+    atomicAdd(&it.size[r], 1);
 }
 
 // pass 1: survivors per block of 256 seeds
-__global__ void k_keep_count(int n, const int* __restrict__ label, const int* __restrict__ size,
-                             int min_region, int* __restrict__ bsum, uint8_t* keep_out) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_keep_count(const __grid_constant__ FiltBatch F) {
+    const FiltItem& it = F.it[blockIdx.y];
+    const int n = it.nx * it.ny;
+    if ((int)blockIdx.x * (int)blockDim.x >= n) return;          // whole block
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     int keep = 0;
     if (s < n) {
-        int r = label[s];
-        keep = r >= 0 && size[r] >= min_region;
-        if (keep_out) keep_out[s] = (uint8_t)keep;
+        const int r = it.label[s];
+        keep = r >= 0 && it.size[r] >= F.min_region;
+        if (it.keep) it.keep[s] = (uint8_t)keep;
     }
-    int c = __syncthreads_count(keep);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = c;
+    const int c = __syncthreads_count(keep);
+    if (threadIdx.x == 0) it.bsum[blockIdx.x] = c;
 }
 
-// pass 2: exclusive scan of the block counts (one block, any count)
-__global__ void k_scan_blocks(int nb, int* bsum, int32_t* d_count) {
+// pass 2: exclusive scan of the block counts, one block per pair
+__global__ void k_scan_blocks(const __grid_constant__ FiltBatch F) {
+    const FiltItem& it = F.it[blockIdx.x];
+    const int nb = (it.nx * it.ny + 255) / 256;
     __shared__ int part[1024];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int base = 0; base < nb; base += 1024) {
-        int idx = base + threadIdx.x;
-        int v = idx < nb ? bsum[idx] : 0;
+        const int idx = base + threadIdx.x;
+        const int v = idx < nb ? it.bsum[idx] : 0;
         part[threadIdx.x] = v;
         __syncthreads();
         for (int off = 1; off < 1024; off <<= 1) {      // Hillis-Steele inclusive scan
-            int t = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+            const int t = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
             __syncthreads();
             part[threadIdx.x] += t;
             __syncthreads();
         }
-        if (idx < nb) bsum[idx] = carry + part[threadIdx.x] - v;
+        if (idx < nb) it.bsum[idx] = carry + part[threadIdx.x] - v;
         __syncthreads();
         if (threadIdx.x == 0) carry += part[1023];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *d_count = carry;
+    if (threadIdx.x == 0) *it.count = carry;
 }
 
 // pass 3: write survivors in raster order
-__global__ void k_keep_write(int n, int nx, int sigma, int c, const int* __restrict__ label,
-                             const int* __restrict__ size, int min_region,
-                             const int32_t* __restrict__ u, const int* __restrict__ bsum,
-                             int32_t* __restrict__ rows, long long max_rows) {
+__global__ void k_keep_write(const __grid_constant__ FiltBatch F) {
+    const FiltItem& it = F.it[blockIdx.y];
+    const int n = it.nx * it.ny;
+    if ((int)blockIdx.x * (int)blockDim.x >= n) return;          // whole block
     __shared__ int warp_tot[8];
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     int keep = 0;
     if (s < n) {
-        int r = label[s];
-        keep = r >= 0 && size[r] >= min_region;
+        const int r = it.label[s];
+        keep = r >= 0 && it.size[r] >= F.min_region;
     }
-    unsigned m = __ballot_sync(0xffffffffu, keep);
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) warp_tot[w] = __popc(m);
     __syncthreads();
-    int off = bsum[blockIdx.x];
+    int off = it.bsum[blockIdx.x];
     for (int k = 0; k < w; ++k) off += warp_tot[k];
     off += __popc(m & ((1u << lane) - 1u));
-    if (keep && off < max_rows) {
-        int i = s % nx, j = s / nx;
-        int x = c + sigma * i, y = c + sigma * j;
-        int32_t uu = u[s];
-        int4 row = make_int4(x, y, x + lo16(uu), y + hi16(uu));
-        reinterpret_cast<int4*>(rows)[off] = row;
+    if (keep && off < it.max_rows) {
+        const int i = s % it.nx, j = s / it.nx;
+        const int x = F.c + F.sigma * i, y = F.c + F.sigma * j;
+        const int32_t uu = it.u[s];
+        reinterpret_cast<int4*>(it.rows)[off] = make_int4(x, y, x + lo16(uu), y + hi16(uu));
     }
 }
 
 }  // namespace
 
+// The whole filter for a batch of fields: six launches in all.
+pgm_status launch_filter_batch(const pgm_params* p, const FiltBatch& F, int max_seeds,
+                               cudaStream_t st) {
+    if (F.n == 0) return PGM_OK;
+    KScope ks(PGM_K_FILTER, st, 6);
+    const int nb = (max_seeds + 255) / 256;
+    const dim3 g(nb > 0 ? nb : 1, F.n);
+    k_cc_init<<<g, 256, 0, st>>>(F);
+    k_cc_link<<<g, 256, 0, st>>>(F);
+    k_cc_flatten<<<g, 256, 0, st>>>(F);
+    k_keep_count<<<g, 256, 0, st>>>(F);
+    k_scan_blocks<<<F.n, 1024, 0, st>>>(F);
+    k_keep_write<<<g, 256, 0, st>>>(F);
+    (void)p;
+    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+}
+
+void filter_item(const WsPlan& wp, uint8_t* d_ws, int32_t* d_matches, int64_t max_matches,
+                 int32_t* d_count, uint8_t* d_keep, FiltItem* it) {
+    it->flags = d_ws + wp.off_flags[0][0];
+    it->u = reinterpret_cast<const int32_t*>(d_ws + wp.off_u[0][0]);
+    it->label = reinterpret_cast<int*>(d_ws + wp.off_label);
+    it->size = reinterpret_cast<int*>(d_ws + wp.off_size);
+    it->bsum = reinterpret_cast<int*>(d_ws + wp.off_bsum);
+    it->nx = wp.nx[0][0];
+    it->ny = wp.ny[0][0];
+    it->rows = d_matches;
+    it->max_rows = max_matches;
+    it->count = d_count;
+    it->keep = d_keep;
+}
+
+void filter_consts(const pgm_params* p, FiltBatch* F) {
+    F->sigma = p->seed_stride;
+    F->c = p->seed_stride / 2;
+    F->dmax2 = p->region_dmax2;
+    F->min_region = p->min_region;
+}
+
 pgm_status launch_filter(const pgm_params* p, const WsPlan& wp, uint8_t* d_ws,
                          int32_t* d_matches, int64_t max_matches, int32_t* d_count,
                          uint8_t* d_keep, cudaStream_t st) {
-    const int nx = wp.nx[0][0], ny = wp.ny[0][0], n = nx * ny;
-    const uint8_t* flags = d_ws + wp.off_flags[0][0];
-    const int32_t* u = reinterpret_cast<const int32_t*>(d_ws + wp.off_u[0][0]);
-    int* label = reinterpret_cast<int*>(d_ws + wp.off_label);
-    int* size = reinterpret_cast<int*>(d_ws + wp.off_size);
-    int* bsum = reinterpret_cast<int*>(d_ws + wp.off_bsum);
-    const int nb = (n + 255) / 256;
-    if (n == 0) {
-        cudaMemsetAsync(d_count, 0, sizeof(int32_t), st);
-        return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
-    }
-    KScope ks(PGM_K_FILTER, st, 6);
-    k_cc_init<<<nb, 256, 0, st>>>(flags, n, label, size);
-    k_cc_link<<<nb, 256, 0, st>>>(flags, u, nx, ny, p->region_dmax2, label);
-    k_cc_flatten<<<nb, 256, 0, st>>>(n, label, size);
-    k_keep_count<<<nb, 256, 0, st>>>(n, label, size, p->min_region, bsum, d_keep);
-    k_scan_blocks<<<1, 1024, 0, st>>>(nb, bsum, d_count);
-    k_keep_write<<<nb, 256, 0, st>>>(n, nx, p->seed_stride, p->seed_stride / 2, label, size,
-                                     p->min_region, u, bsum, d_matches, max_matches);
-    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+    static thread_local FiltBatch F;
+    F.n = 1;
+    filter_consts(p, &F);
+    filter_item(wp, d_ws, d_matches, max_matches, d_count, d_keep, &F.it[0]);
+    return launch_filter_batch(p, F, F.it[0].nx * F.it[0].ny, st);
 }
 
 // The same sequence on explicit pointers: the field (u, flags) and the
@@ -189,21 +221,14 @@ pgm_status launch_filter_ptrs(const pgm_params* p, int nx, int ny, const int32_t
                               const uint8_t* flags, int* label, int* size, int* bsum,
                               int32_t* d_matches, int64_t max_matches, int32_t* d_count,
                               cudaStream_t st) {
-    const int n = nx * ny;
-    const int nb = (n + 255) / 256;
-    if (n == 0) {
-        cudaMemsetAsync(d_count, 0, sizeof(int32_t), st);
-        return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
-    }
-    KScope ks(PGM_K_FILTER, st, 6);
-    k_cc_init<<<nb, 256, 0, st>>>(flags, n, label, size);
-    k_cc_link<<<nb, 256, 0, st>>>(flags, u, nx, ny, p->region_dmax2, label);
-    k_cc_flatten<<<nb, 256, 0, st>>>(n, label, size);
-    k_keep_count<<<nb, 256, 0, st>>>(n, label, size, p->min_region, bsum, nullptr);
-    k_scan_blocks<<<1, 1024, 0, st>>>(nb, bsum, d_count);
-    k_keep_write<<<nb, 256, 0, st>>>(n, nx, p->seed_stride, p->seed_stride / 2, label, size,
-                                     p->min_region, u, bsum, d_matches, max_matches);
-    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+    static thread_local FiltBatch F;
+    F.n = 1;
+    filter_consts(p, &F);
+    FiltItem& it = F.it[0];
+    it.flags = flags; it.u = u; it.label = label; it.size = size; it.bsum = bsum;
+    it.nx = nx; it.ny = ny; it.rows = d_matches; it.max_rows = max_matches;
+    it.count = d_count; it.keep = nullptr;
+    return launch_filter_batch(p, F, nx * ny, st);
 }
 
 }  // namespace pgm

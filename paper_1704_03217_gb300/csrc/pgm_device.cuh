@@ -124,8 +124,22 @@ struct KScope {
 
 // ------------------------------------------------------------ launchers
 // pyramid.cu
-pgm_status launch_pyramid(const pgm_params* p, const PyrPlan& pp, const uint8_t* d_img, int c,
-                          size_t pitch, uint8_t* d_pyr, cudaStream_t st);
+constexpr int PYR_MAXB = 64;      // images per pyramid launch
+struct PyrItem {                  // one image in one pyramid launch
+    const uint8_t* src;
+    uint8_t* dst;
+    uint32_t* split;              // Sobel: split-byte copy of the descriptor
+    int sw, sh, srow;             // source level size and row bytes
+    int dw, dh, drow;             // destination level size and row bytes / int16 elements
+    size_t splane, dplane;        // plane strides
+    size_t pitch;                 // level 0: input row bytes
+    int mode;                     // level 0: input mode; colour conversion: target space
+    int pad;
+};
+struct PyrBatch { int n; int pad; PyrItem it[PYR_MAXB]; };
+pgm_status launch_pyramid_batch(const pgm_params* p, int n, const PyrPlan* plans,
+                                const uint8_t* const* imgs, const int* cs, const size_t* pitches,
+                                uint8_t* const* pyrs, cudaStream_t st);
 // match.cu
 pgm_status launch_init(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
                        int max_seeds, cudaStream_t st);
@@ -141,6 +155,25 @@ pgm_status launch_box(const LvlBatch& B, int nch, int max_pixels, cudaStream_t s
 pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
                           bool* handled, cudaStream_t st);
 // filter.cu
+struct FiltItem {                 // the level-0 forward field of one pair
+    const uint8_t* flags;
+    const int32_t* u;
+    int* label; int* size; int* bsum;   // scratch
+    int nx, ny;
+    int32_t* rows;
+    long long max_rows;
+    int32_t* count;
+    uint8_t* keep;                // optional
+};
+struct FiltBatch {
+    int n, sigma, c, dmax2, min_region, pad;
+    FiltItem it[MAXB];
+};
+pgm_status launch_filter_batch(const pgm_params* p, const FiltBatch& F, int max_seeds,
+                               cudaStream_t st);
+void filter_item(const WsPlan& wp, uint8_t* d_ws, int32_t* d_matches, int64_t max_matches,
+                 int32_t* d_count, uint8_t* d_keep, FiltItem* it);
+void filter_consts(const pgm_params* p, FiltBatch* F);
 pgm_status launch_filter_ptrs(const pgm_params* p, int nx, int ny, const int32_t* u,
                               const uint8_t* flags, int* label, int* size, int* bsum,
                               int32_t* d_matches, int64_t max_matches, int32_t* d_count,

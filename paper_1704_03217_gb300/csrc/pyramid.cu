@@ -9,6 +9,8 @@
 //   per level and direction: Sobel gradients Gx, Gy (Eq. 1-2), S = 3 or 5,
 //            replicated border, int16, pixel-interleaved; for the direction
 //            descriptor (Sec. III-F) their signs.
+#include <string.h>
+
 #include "match_common.cuh"
 
 namespace pgm {
@@ -19,51 +21,58 @@ __device__ __forceinline__ int gray_q14(int r, int g, int b) {
     return (4899 * r + 9617 * g + 1868 * b + 8192) >> 14;
 }
 
+// Every kernel takes a batch of images (blockIdx.z); the grid covers the
+// largest image and blocks outside an image's extent return.
+
 // ---------------------------------------------------------------- level 0
 // mode 0: gray input copied; mode 1: RGB -> gray; mode 2: RGB -> 3 planes
-__global__ void k_level0(const uint8_t* __restrict__ img, int w, int h, size_t pitch, int mode,
-                         uint8_t* __restrict__ out, int row, size_t plane) {
+__global__ void k_level0(const __grid_constant__ PyrBatch B) {
+    const PyrItem& it = B.it[blockIdx.z];
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= w || y >= h) return;
-    const uint8_t* src = img + (size_t)y * pitch;
-    if (mode == 0) {
-        out[(size_t)y * row + x] = src[x];
+    if (x >= it.sw || y >= it.sh) return;
+    const uint8_t* src = it.src + (size_t)y * it.pitch;
+    uint8_t* out = it.dst;
+    const size_t o = (size_t)y * it.drow + x;
+    if (it.mode == 0) {
+        out[o] = src[x];
     } else {
         int r = src[3 * x], g = src[3 * x + 1], b = src[3 * x + 2];
-        if (mode == 1) {
-            out[(size_t)y * row + x] = (uint8_t)gray_q14(r, g, b);
+        if (it.mode == 1) {
+            out[o] = (uint8_t)gray_q14(r, g, b);
         } else {
-            out[(size_t)y * row + x] = (uint8_t)r;
-            out[plane + (size_t)y * row + x] = (uint8_t)g;
-            out[2 * plane + (size_t)y * row + x] = (uint8_t)b;
+            out[o] = (uint8_t)r;
+            out[it.dplane + o] = (uint8_t)g;
+            out[2 * it.dplane + o] = (uint8_t)b;
         }
     }
 }
 
 // ------------------------------------------------------- binomial down
-// One output pixel per thread, channel = blockIdx.z.  The separable sums are
-// exact integers, so summing rows first equals the 2D sum of the definition.
-__global__ void k_down(const uint8_t* __restrict__ in, int w, int h, int irow, size_t iplane,
-                       uint8_t* __restrict__ out, int w2, int h2, int orow, size_t oplane) {
+// One output pixel per thread; blockIdx.z = image * C + channel.  The
+// separable sums are exact integers, so summing rows first equals the 2D sum
+// of the definition.
+__global__ void k_down(const __grid_constant__ PyrBatch B, int C) {
+    const PyrItem& it = B.it[blockIdx.z / C];
+    const int ch = blockIdx.z % C;
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= w2 || y >= h2) return;
-    const uint8_t* src = in + blockIdx.z * iplane;
+    if (x >= it.dw || y >= it.dh) return;
+    const uint8_t* src = it.src + ch * it.splane;
     const int k[5] = {1, 4, 6, 4, 1};
     int xs[5];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) xs[i] = clampi(2 * x + i - 2, 0, w - 1);
+    for (int i = 0; i < 5; ++i) xs[i] = clampi(2 * x + i - 2, 0, it.sw - 1);
     int acc = 0;
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-        const uint8_t* r = src + (size_t)clampi(2 * y + j - 2, 0, h - 1) * irow;
+        const uint8_t* r = src + (size_t)clampi(2 * y + j - 2, 0, it.sh - 1) * it.srow;
         int s = 0;
 #pragma unroll
         for (int i = 0; i < 5; ++i) s += k[i] * r[xs[i]];
         acc += k[j] * s;
     }
-    out[blockIdx.z * oplane + (size_t)y * orow + x] = (uint8_t)((acc + 128) >> 8);
+    it.dst[ch * it.dplane + (size_t)y * it.drow + x] = (uint8_t)((acc + 128) >> 8);
 }
 
 // ------------------------------------------------------- colour spaces
@@ -117,28 +126,30 @@ __device__ __forceinline__ void to_ycrcb(int r, int g, int b, int* o) {
     o[2] = clampi((int)fdiv((long long)(b - y) * 9241 + (128 << 14) + 8192, 16384), 0, 255);
 }
 
-__global__ void k_convert(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int w, int h,
-                          int row, size_t plane, int space) {
+__global__ void k_convert(const __grid_constant__ PyrBatch B) {
+    const PyrItem& it = B.it[blockIdx.z];
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= w || y >= h) return;
-    size_t o = (size_t)y * row + x;
-    int r = in[o], g = in[plane + o], b = in[2 * plane + o];
+    if (x >= it.sw || y >= it.sh) return;
+    const size_t o = (size_t)y * it.srow + x, plane = it.splane;
+    int r = it.src[o], g = it.src[plane + o], b = it.src[2 * plane + o];
     int v[3];
-    if (space == SP_LAB) to_lab(r, g, b, v); else to_ycrcb(r, g, b, v);
-    out[o] = (uint8_t)v[0];
-    out[plane + o] = (uint8_t)v[1];
-    out[2 * plane + o] = (uint8_t)v[2];
+    if (it.mode == SP_LAB) to_lab(r, g, b, v); else to_ycrcb(r, g, b, v);
+    it.dst[o] = (uint8_t)v[0];
+    it.dst[plane + o] = (uint8_t)v[1];
+    it.dst[2 * plane + o] = (uint8_t)v[2];
 }
 
 // ----------------------------------------------------------------- Sobel
 // Gx = sum_j s_j sum_i d_i I(x+i, y+j); Gy with the roles of the axes swapped.
 template <int S, int C>
-__global__ void k_sobel(const uint8_t* __restrict__ in, int w, int h, int row, size_t plane,
-                        int16_t* __restrict__ out, uint32_t* __restrict__ split, int orow,
-                        int dir_only) {
+__global__ void k_sobel(const __grid_constant__ PyrBatch B, int dir_only) {
+    const PyrItem& it = B.it[blockIdx.z];
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int w = it.sw, h = it.sh, row = it.srow;
+    const size_t plane = it.splane;
+    const uint8_t* in = it.src;
     if (x >= w || y >= h) return;
     constexpr int R = S / 2;
     const int d5[5] = {-1, -2, 0, 2, 1}, s5[5] = {1, 4, 6, 4, 1};
@@ -177,64 +188,103 @@ __global__ void k_sobel(const uint8_t* __restrict__ in, int w, int h, int row, s
     // pixel-interleaved int16, written as 32-bit words (2C is even)
     // and the same words with every value a split into signed bytes
     // a = 128 a_h + a_l (a_l in [-64, 63]) for the dp2a cross products
-    const size_t w0 = ((size_t)y * orow + (size_t)x * 2 * C) / 2;
-    uint32_t* dst = reinterpret_cast<uint32_t*>(out) + w0;
+    const size_t w0 = ((size_t)y * it.drow + (size_t)x * 2 * C) / 2;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(it.dst) + w0;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
         dst[k] = (uint32_t)(uint16_t)g[2 * k] | ((uint32_t)(uint16_t)g[2 * k + 1] << 16);
-        split[w0 + k] = (uint32_t)split_bytes(g[2 * k], g[2 * k + 1]);
+        it.split[w0 + k] = (uint32_t)split_bytes(g[2 * k], g[2 * k + 1]);
     }
 }
 
 }  // namespace
 
-pgm_status launch_pyramid(const pgm_params* p, const PyrPlan& pp, const uint8_t* d_img, int c,
-                          size_t pitch, uint8_t* d_pyr, cudaStream_t st) {
-    int nlaunch = pp.L;                       // level 0 + (L-1) reductions + Sobels + conversions
-    for (int s = 0; s < pp.nsch; ++s)
-        for (int l = 0; l < pp.L; ++l)
-            nlaunch += 1 + (pp.space[s][l] == SP_LAB || pp.space[s][l] == SP_YCRCB);
-    KScope ks(PGM_K_PYRAMID, st, nlaunch);
+// One launch per step of the pyramid for a whole batch of images (all with
+// the same parameters; sizes may differ).
+pgm_status launch_pyramid_batch(const pgm_params* p, int n, const PyrPlan* plans,
+                                const uint8_t* const* imgs, const int* cs, const size_t* pitches,
+                                uint8_t* const* pyrs, cudaStream_t st) {
+    static thread_local PyrBatch B;
+    const PyrPlan& p0 = plans[0];
+    const int L = p0.L, C = p0.C, nsch = p0.nsch;
     dim3 blk(32, 8);
     auto grid = [&](int w, int h, int z) { return dim3((w + 31) / 32, (h + 7) / 8, z); };
-    int mode = c == 1 ? 0 : (pp.C == 1 ? 1 : 2);
-    k_level0<<<grid(pp.W[0], pp.H[0], 1), blk, 0, st>>>(d_img, pp.W[0], pp.H[0], pitch, mode,
-                                                        d_pyr + pp.img_off[0], pp.img_row[0],
-                                                        pp.img_plane[0]);
-    for (int l = 1; l < pp.L; ++l)
-        k_down<<<grid(pp.W[l], pp.H[l], pp.C), blk, 0, st>>>(
-            d_pyr + pp.img_off[l - 1], pp.W[l - 1], pp.H[l - 1], pp.img_row[l - 1],
-            pp.img_plane[l - 1], d_pyr + pp.img_off[l], pp.W[l], pp.H[l], pp.img_row[l],
-            pp.img_plane[l]);
-    for (int s = 0; s < pp.nsch; ++s)
-        for (int l = 0; l < pp.L; ++l) {
-            int sp = pp.space[s][l];
-            if (sp == SP_LAB || sp == SP_YCRCB)
-                k_convert<<<grid(pp.W[l], pp.H[l], 1), blk, 0, st>>>(
-                    d_pyr + pp.img_off[l], d_pyr + pp.cimg_off[s][l], pp.W[l], pp.H[l],
-                    pp.img_row[l], pp.img_plane[l], sp);
-            const uint8_t* ci = d_pyr + pp.cimg_off[s][l];
-            int16_t* de = reinterpret_cast<int16_t*>(d_pyr + pp.desc_off[s][l]);
-            uint32_t* sp_ = reinterpret_cast<uint32_t*>(d_pyr + pp.split_off[s][l]);
-            dim3 g = grid(pp.W[l], pp.H[l], 1);
-            int dir_only = p->descriptor == PGM_DIR;
-            if (p->sobel == 5) {
-                if (pp.C == 1)
-                    k_sobel<5, 1><<<g, blk, 0, st>>>(ci, pp.W[l], pp.H[l], pp.img_row[l],
-                                                     pp.img_plane[l], de, sp_, pp.desc_row[l], dir_only);
-                else
-                    k_sobel<5, 3><<<g, blk, 0, st>>>(ci, pp.W[l], pp.H[l], pp.img_row[l],
-                                                     pp.img_plane[l], de, sp_, pp.desc_row[l], dir_only);
-            } else {
-                if (pp.C == 1)
-                    k_sobel<3, 1><<<g, blk, 0, st>>>(ci, pp.W[l], pp.H[l], pp.img_row[l],
-                                                     pp.img_plane[l], de, sp_, pp.desc_row[l], dir_only);
-                else
-                    k_sobel<3, 3><<<g, blk, 0, st>>>(ci, pp.W[l], pp.H[l], pp.img_row[l],
-                                                     pp.img_plane[l], de, sp_, pp.desc_row[l], dir_only);
-            }
+    const int dir_only = p->descriptor == PGM_DIR;
+    for (int base = 0; base < n; base += PYR_MAXB) {
+        const int m = n - base < PYR_MAXB ? n - base : PYR_MAXB;
+        int nlaunch = L + nsch * L;
+        for (int s = 0; s < nsch; ++s)
+            for (int l = 0; l < L; ++l)
+                nlaunch += p0.space[s][l] == SP_LAB || p0.space[s][l] == SP_YCRCB;
+        KScope ks(PGM_K_PYRAMID, st, nlaunch);
+        // level 0
+        int mw = 0, mh = 0;
+        memset(&B, 0, sizeof(B));
+        B.n = m;
+        for (int k = 0; k < m; ++k) {
+            const PyrPlan& pp = plans[base + k];
+            PyrItem& it = B.it[k];
+            it.src = imgs[base + k]; it.pitch = pitches[base + k];
+            it.sw = pp.W[0]; it.sh = pp.H[0];
+            it.dst = pyrs[base + k] + pp.img_off[0]; it.drow = pp.img_row[0];
+            it.dplane = pp.img_plane[0];
+            it.mode = cs[base + k] == 1 ? 0 : (C == 1 ? 1 : 2);
+            mw = pp.W[0] > mw ? pp.W[0] : mw; mh = pp.H[0] > mh ? pp.H[0] : mh;
         }
-    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+        k_level0<<<grid(mw, mh, m), blk, 0, st>>>(B);
+        for (int l = 1; l < L; ++l) {
+            mw = mh = 0;
+            for (int k = 0; k < m; ++k) {
+                const PyrPlan& pp = plans[base + k];
+                const uint8_t* pyr = pyrs[base + k];
+                PyrItem& it = B.it[k];
+                it.src = pyr + pp.img_off[l - 1]; it.sw = pp.W[l - 1]; it.sh = pp.H[l - 1];
+                it.srow = pp.img_row[l - 1]; it.splane = pp.img_plane[l - 1];
+                it.dst = pyrs[base + k] + pp.img_off[l]; it.dw = pp.W[l]; it.dh = pp.H[l];
+                it.drow = pp.img_row[l]; it.dplane = pp.img_plane[l];
+                mw = pp.W[l] > mw ? pp.W[l] : mw; mh = pp.H[l] > mh ? pp.H[l] : mh;
+            }
+            k_down<<<grid(mw, mh, m * C), blk, 0, st>>>(B, C);
+        }
+        for (int s = 0; s < nsch; ++s)
+            for (int l = 0; l < L; ++l) {
+                const int sp = p0.space[s][l];
+                mw = mh = 0;
+                for (int k = 0; k < m; ++k) {
+                    const PyrPlan& pp = plans[base + k];
+                    mw = pp.W[l] > mw ? pp.W[l] : mw; mh = pp.H[l] > mh ? pp.H[l] : mh;
+                }
+                if (sp == SP_LAB || sp == SP_YCRCB) {
+                    for (int k = 0; k < m; ++k) {
+                        const PyrPlan& pp = plans[base + k];
+                        PyrItem& it = B.it[k];
+                        it.src = pyrs[base + k] + pp.img_off[l]; it.sw = pp.W[l]; it.sh = pp.H[l];
+                        it.srow = pp.img_row[l]; it.splane = pp.img_plane[l];
+                        it.dst = pyrs[base + k] + pp.cimg_off[s][l];
+                        it.mode = sp;
+                    }
+                    k_convert<<<grid(mw, mh, m), blk, 0, st>>>(B);
+                }
+                for (int k = 0; k < m; ++k) {
+                    const PyrPlan& pp = plans[base + k];
+                    PyrItem& it = B.it[k];
+                    it.src = pyrs[base + k] + pp.cimg_off[s][l]; it.sw = pp.W[l]; it.sh = pp.H[l];
+                    it.srow = pp.img_row[l]; it.splane = pp.img_plane[l];
+                    it.dst = pyrs[base + k] + pp.desc_off[s][l]; it.drow = pp.desc_row[l];
+                    it.split = reinterpret_cast<uint32_t*>(pyrs[base + k] + pp.split_off[s][l]);
+                }
+                dim3 g = grid(mw, mh, m);
+                if (p->sobel == 5) {
+                    if (C == 1) k_sobel<5, 1><<<g, blk, 0, st>>>(B, dir_only);
+                    else k_sobel<5, 3><<<g, blk, 0, st>>>(B, dir_only);
+                } else {
+                    if (C == 1) k_sobel<3, 1><<<g, blk, 0, st>>>(B, dir_only);
+                    else k_sobel<3, 3><<<g, blk, 0, st>>>(B, dir_only);
+                }
+            }
+        if (cudaGetLastError() != cudaSuccess) return PGM_ERR_CUDA;
+    }
+    return PGM_OK;
 }
 
 }  // namespace pgm

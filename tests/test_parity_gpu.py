@@ -173,3 +173,32 @@ def test_max_matches_truncates(api):
     api.filter_into(p, ws, out, cnt)
     torch.cuda.synchronize()
     assert int(cnt.item()) == len(rows) and (out.cpu().numpy() == rows[:17]).all()
+
+
+def test_batched_pyramid_and_filter_equal_single(api):
+    """pgm_build_pyramid_batch / pgm_filter_batch over images of different
+    sizes give each exactly what the single calls give."""
+    prm = api.Params(levels=4, color=1)
+    imgs = [_rgb_pair(30 + k, w, h)[k % 2] for k, (w, h) in
+            enumerate([(320, 240), (257, 131), (400, 150), (199, 301)])]
+    T = [torch.from_numpy(x).cuda() for x in imgs]
+    batched = [api.Pyramid(prm, x.shape[1], x.shape[0]) for x in imgs]
+    api.build_pyramids(prm, T, batched)
+    single = [api.build_pyramid(prm, t) for t in T]
+    torch.cuda.synchronize()
+    for a, b in zip(batched, single):
+        for s in range(2):
+            for l in range(4):
+                assert torch.equal(a.desc(s, l), b.desc(s, l))
+                assert torch.equal(a.cimage(s, l), b.cimage(s, l))
+    pairs = [(0, 2), (1, 3)]
+    W = [api.match(prm, single[i], single[j], stream_id=k) for k, (i, j) in enumerate(pairs)]
+    rows = [torch.full((w.layout(0, 0)[0] * w.layout(0, 0)[1], 4), -1, dtype=torch.int32,
+                       device="cuda") for w in W]
+    cnts = [torch.zeros(1, dtype=torch.int32, device="cuda") for _ in W]
+    api.filter_batch(prm, W, rows, cnts)
+    for w, r, c in zip(W, rows, cnts):
+        want, _ = api.filter_matches(prm, w)
+        torch.cuda.synchronize()
+        n = int(c.item())
+        assert n == want.shape[0] and torch.equal(r[:n], want)
