@@ -142,11 +142,16 @@ bool make_ws_plan(const pgm_params* p, int w1, int h1, int w2, int h2, WsPlan* w
             wp->off_sa2[l][d] = off;   off = align_up(off + 8 * n, 256);
             const PyrPlan& t = d == 0 ? b : a;       // target image of this direction
             wp->off_sb2[l][d] = off;   off = align_up(off + 8 * (size_t)t.W[l] * t.H[l], 256);
+            wp->off_sa2img[l][d] = off;
+            off = align_up(off + 8 * (size_t)r.W[l] * r.H[l], 256);
         }
     for (int d = 0; d < 2; ++d) {
         const PyrPlan& t = d == 0 ? b : a;
         wp->off_boxtmp[d] = off;
         off = align_up(off + 8 * (size_t)t.W[0] * t.H[0], 256);
+        const PyrPlan& r = d == 0 ? a : b;
+        wp->off_boxtmp_ref[d] = off;
+        off = align_up(off + 8 * (size_t)r.W[0] * r.H[0], 256);
     }
     size_t n0 = (size_t)wp->nx[0][0] * wp->ny[0][0];
     wp->nblk0 = (int)((n0 + 255) / 256);
@@ -211,6 +216,8 @@ void fill_dir(const pgm_params* p, const PairCtx& c, int l, int d, DirLvl* D) {
     D->sa2 = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sa2[l][d]);
     D->sb2 = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sb2[l][d]);
     D->boxtmp = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_boxtmp[d]);
+    D->sa2img = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sa2img[l][d]);
+    D->boxtmp_ref = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_boxtmp_ref[d]);
 }
 
 pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) {
@@ -242,6 +249,8 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
                 for (int d = 0; d < 2; ++d) {
                     fill_dir(p, ctx[k], l, d, &B.d[k][d]);
                     int np = B.d[k][d].tw * B.d[k][d].th;
+                    if (np > max_px) max_px = np;
+                    np = B.d[k][d].rw * B.d[k][d].rh;
                     if (np > max_px) max_px = np;
                 }
             pgm_status r = launch_box(B, nch, max_px, st);

@@ -90,16 +90,21 @@ __device__ __forceinline__ unsigned long long warp_cost(const Ref<NCH, PPL>& R, 
 
 // Box filter of N(x, y) = sum_c G_c(x, y)^2 over the P x P patch with
 // replicated borders, separable: row sums, then column sums (exact, uint64).
+// blockIdx.y = 2 * direction + (0: target image -> sb2, 1: reference -> sa2img)
 template <int NCH>
 __global__ void k_box_h(const __grid_constant__ LvlBatch B) {
-    const DirLvl& D = B.d[blockIdx.z][blockIdx.y];
+    const DirLvl& D = B.d[blockIdx.z][blockIdx.y >> 1];
+    const bool ref = blockIdx.y & 1;
+    const int w = ref ? D.rw : D.tw, hh = ref ? D.rh : D.th;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= D.tw * D.th) return;
-    const int x = idx % D.tw, y = idx / D.tw, h = D.P / 2;
-    const uint32_t* row = reinterpret_cast<const uint32_t*>(D.tgt + (size_t)y * D.tgt_pitch);
+    if (idx >= w * hh) return;
+    const int x = idx % w, y = idx / w, h = D.P / 2;
+    const int16_t* img = ref ? D.ref : D.tgt;
+    const int pitch = ref ? D.ref_pitch : D.tgt_pitch;
+    const uint32_t* row = reinterpret_cast<const uint32_t*>(img + (size_t)y * pitch);
     unsigned long long s = 0;
     for (int o = 0; o < D.P; ++o) {
-        const int xx = clampi(x + o - h, 0, D.tw - 1);
+        const int xx = clampi(x + o - h, 0, w - 1);
         uint32_t n = 0;
 #pragma unroll
         for (int c = 0; c < NCH / 2; ++c) {
@@ -109,17 +114,20 @@ __global__ void k_box_h(const __grid_constant__ LvlBatch B) {
         }
         s += n;
     }
-    D.boxtmp[idx] = s;
+    (ref ? D.boxtmp_ref : D.boxtmp)[idx] = s;
 }
 
 __global__ void k_box_v(const __grid_constant__ LvlBatch B) {
-    const DirLvl& D = B.d[blockIdx.z][blockIdx.y];
+    const DirLvl& D = B.d[blockIdx.z][blockIdx.y >> 1];
+    const bool ref = blockIdx.y & 1;
+    const int w = ref ? D.rw : D.tw, hh = ref ? D.rh : D.th;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= D.tw * D.th) return;
-    const int x = idx % D.tw, y = idx / D.tw, h = D.P / 2;
+    if (idx >= w * hh) return;
+    const int x = idx % w, y = idx / w, h = D.P / 2;
+    const unsigned long long* tmp = ref ? D.boxtmp_ref : D.boxtmp;
     unsigned long long s = 0;
-    for (int o = 0; o < D.P; ++o) s += D.boxtmp[(size_t)clampi(y + o - h, 0, D.th - 1) * D.tw + x];
-    D.sb2[idx] = s;
+    for (int o = 0; o < D.P; ++o) s += tmp[(size_t)clampi(y + o - h, 0, hh - 1) * w + x];
+    (ref ? D.sa2img : D.sb2)[idx] = s;
 }
 
 // Lane l owns words l, l + 32, ... of the P x P x NCH patch, flattened row by
@@ -670,7 +678,12 @@ pgm_status launch_cost_fill(const LvlBatch& B, const MatchConst& mc, int nch, in
     if (max_seeds <= 0) return PGM_OK;
     KScope ks(PGM_K_COST, st);
     dim3 g((max_seeds + 7) / 8, 2, B.n);
-    if (mc.norm == PGM_L2SQ) PGM_DISPATCH_X(k_cost_x, g, B, mc);
+    if (mc.norm == PGM_L2SQ) {
+        bool handled = false;
+        pgm_status r = launch_cost_tile(B, mc, nch, &handled, st);
+        if (r != PGM_OK || handled) return r;
+        PGM_DISPATCH_X(k_cost_x, g, B, mc);
+    }
     else PGM_DISPATCH_NCH_PPL_NORM(k_cost, g, B, mc);
     return last_status();
 }
@@ -693,7 +706,7 @@ pgm_status launch_pm_phase(const LvlBatch& B, const MatchConst& mc, int nch, int
 pgm_status launch_box(const LvlBatch& B, int nch, int max_pixels, cudaStream_t st) {
     if (max_pixels <= 0) return PGM_OK;
     KScope ks(PGM_K_COST, st, 2);
-    dim3 g((max_pixels + 255) / 256, 2, B.n);
+    dim3 g((max_pixels + 255) / 256, 4, B.n);
     if (nch == 2) k_box_h<2><<<g, 256, 0, st>>>(B);
     else k_box_h<6><<<g, 256, 0, st>>>(B);
     k_box_v<<<g, 256, 0, st>>>(B);

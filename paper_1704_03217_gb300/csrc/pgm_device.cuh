@@ -45,6 +45,8 @@ struct WsPlan {
     size_t off_sa2[MAXL][2];     // per seed: sum of |G|^2 over its reference patch
     size_t off_sb2[MAXL][2];     // per target pixel: sum of |G|^2 over the patch there
     size_t off_boxtmp[2];        // per direction: row sums of the box filter (level-0 size)
+    size_t off_sa2img[MAXL][2];  // per reference pixel: sum of |G|^2 over the patch there
+    size_t off_boxtmp_ref[2];    // per direction: row sums for the reference box filter
     size_t off_err;              // uint32 device status word
     size_t off_label, off_size, off_bsum;   // filter scratch (level-0 forward lattice)
     int nblk0;                   // blocks of the level-0 forward lattice scan
@@ -87,6 +89,8 @@ struct DirLvl {
     unsigned long long* sa2;     // per seed: sum over the reference patch of |G|^2
     unsigned long long* sb2;     // per target pixel (row pitch tw): same over the target patch
     unsigned long long* boxtmp;  // scratch of the box filter (row pitch tw)
+    unsigned long long* sa2img;  // per reference pixel (row pitch rw): sum over its patch
+    unsigned long long* boxtmp_ref;  // scratch of the reference box filter (row pitch rw)
 };
 
 struct LvlBatch {
@@ -154,6 +158,8 @@ pgm_status launch_box(const LvlBatch& B, int nch, int max_pixels, cudaStream_t s
 // pm_tile.cu: *handled = false when the staged tile would not fit in shared memory
 pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
                           bool* handled, cudaStream_t st);
+pgm_status launch_cost_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
+                            cudaStream_t st);
 // filter.cu
 struct FiltItem {                 // the level-0 forward field of one pair
     const uint8_t* flags;

@@ -163,6 +163,39 @@ __device__ __forceinline__ long long cross_global(const int (&b)[MMAX], const Di
     return (long long)sh * 128 + (long long)sl;
 }
 
+// Cost of target centre (qx, qy) for the reference words b: from the staged
+// window when the padded patch lies inside it, else from global memory.
+template <int NCH, int M>
+__device__ __forceinline__ unsigned long long tile_cost(
+    const int (&b)[M], const int (&off)[M], const DirLvl& D, const PtGeom& G, unsigned a_tw,
+    unsigned a_sb, bool use_win, int wx0, int wy0, unsigned long long sa, int qx, int qy, int lane,
+    unsigned& n_glob) {
+    constexpr int WPP = NCH / 2;
+    const int P = D.P, h = P / 2;
+    unsigned long long sb;
+    long long cr;
+    const int x0 = qx - h - wx0, y0 = qy - h - wy0;
+    if (use_win && x0 >= 0 && y0 >= 0 && x0 + P + 1 <= G.win_w && y0 + P <= G.win_h) {
+        sb = lds64(a_sb + 8u * (unsigned)(y0 * G.cw + x0));
+        const unsigned base = a_tw + 4u * (unsigned)(y0 * G.sp + x0 * WPP);
+        int sl0 = 0, sh0 = 0, sl1 = 0, sh1 = 0;     // two chains each
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int v = lds32(base + (unsigned)off[m]);
+            if (m & 1) { sl1 = __dp2a_lo(v, b[m], sl1); sh1 = __dp2a_hi(v, b[m], sh1); }
+            else { sl0 = __dp2a_lo(v, b[m], sl0); sh0 = __dp2a_hi(v, b[m], sh0); }
+        }
+        const int sl = __reduce_add_sync(FULL, sl0 + sl1);
+        const int sh = __reduce_add_sync(FULL, sh0 + sh1);
+        cr = (long long)sh * 128 + (long long)sl;
+    } else {
+        sb = D.sb2[(size_t)qy * D.tw + qx];
+        cr = cross_global<NCH, M>(b, D, G.wprp, qx, qy, lane);
+        ++n_glob;
+    }
+    return xcost(sa, sb, cr);
+}
+
 struct TileCtx {
     const uint32_t* s_ref; const uint32_t* s_tw; const unsigned long long* s_sb;
     const int* s_seed; const int* s_u; const int (*s_nb)[2]; const unsigned char* s_f;
@@ -217,29 +250,9 @@ __device__ __forceinline__ void seeds(const LvlBatch& B, const MatchConst& mc, c
                     b[m] = lds32(rbase + (unsigned)off[m]) & (int)(0u - ((vmask >> m) & 1u));
                 loaded = true;
             }
-            unsigned long long sb;
-            long long cr;
-            const int x0 = qx - h - T.wx0, y0 = qy - h - T.wy0;
-            if (T.use_win && x0 >= 0 && y0 >= 0 && x0 + P + 1 <= G.win_w && y0 + P <= G.win_h) {
-                sb = lds64(a_sb + 8u * (unsigned)(y0 * G.cw + x0));
-                const unsigned base = a_tw + 4u * (unsigned)(y0 * G.sp + x0 * WPP);
-                int sl0 = 0, sh0 = 0, sl1 = 0, sh1 = 0;     // two chains each
-#pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    const int v = lds32(base + (unsigned)off[m]);
-                    if (m & 1) { sl1 = __dp2a_lo(v, b[m], sl1); sh1 = __dp2a_hi(v, b[m], sh1); }
-                    else { sl0 = __dp2a_lo(v, b[m], sl0); sh0 = __dp2a_hi(v, b[m], sh0); }
-                }
-                const int sl = __reduce_add_sync(FULL, sl0 + sl1);
-                const int sh = __reduce_add_sync(FULL, sh0 + sh1);
-                cr = (long long)sh * 128 + (long long)sl;
-            } else {
-                sb = D.sb2[(size_t)qy * D.tw + qx];
-                cr = cross_global<NCH, M>(b, D, G.wprp, qx, qy, lane);
-                ++n_glob;
-            }
             ++n_eval;
-            return xcost(sa, sb, cr);
+            return tile_cost<NCH, M>(b, off, D, G, a_tw, a_sb, T.use_win, T.wx0, T.wy0, sa, qx, qy,
+                                     lane, n_glob);
         };
 
 #pragma unroll
@@ -408,6 +421,163 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     }
 }
 
+// ------------------------------------------------------------------
+// Cost refresh at the start of a visit, tile form: all 64 seeds of a tile
+// score their current match with the same staging as the search kernel (the
+// window sits at the median of the tile's current matches).  A seed whose
+// match centre lies outside the target becomes uninitialised.  Every seed's
+// sum |a|^2 is copied from the reference box image for the search kernel.
+constexpr int PC_N = PT_TW * PT_TH;
+
+template <int NCH, int M>
+__device__ __forceinline__ void cost_seeds(const LvlBatch& B, const MatchConst& mc,
+                                           const DirLvl& D, const PtGeom& G, const int* s_seed,
+                                           const int* s_u, const unsigned char* s_f,
+                                           const unsigned long long* s_sa, const uint32_t* s_ref,
+                                           const uint32_t* s_tw, const unsigned long long* s_sb,
+                                           int i0, int j0, int rx0, bool use_win, int wx0,
+                                           int wy0) {
+    constexpr int WPP = NCH / 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pair = blockIdx.z, dir = blockIdx.y;
+    const int P = D.P, h = P / 2, sig = mc.sigma, nw = P * G.wprp;
+    const unsigned a_ref = (unsigned)__cvta_generic_to_shared(s_ref);
+    const unsigned a_tw = (unsigned)__cvta_generic_to_shared(s_tw);
+    const unsigned a_sb = (unsigned)__cvta_generic_to_shared(s_sb);
+    int off[M];
+    unsigned vmask;
+    patch_walk<M>(lane, G.wprp, nw, P * WPP, G.sp, off, vmask);
+    unsigned n_eval = 0, n_glob = 0;
+    for (int a = warp; a < PC_N; a += 8) {
+        const int s = s_seed[a];
+        if (s < 0 || !(s_f[a] & F_VALID)) continue;
+        const int i = i0 + a % PT_TW, j = j0 + a / PT_TW;
+        const int px = mc.c + sig * i, py = mc.c + sig * j;
+        const int qx = px + lo16((uint32_t)s_u[a]), qy = py + hi16((uint32_t)s_u[a]);
+        if (!inside(D, qx, qy)) {
+            if (lane == 0) D.flags[s] = s_f[a] & ~F_VALID;
+            continue;
+        }
+        const unsigned rbase = a_ref + 4u * (unsigned)(sig * (j - j0) * G.sp + (px - h - rx0) * WPP);
+        int b[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            b[m] = lds32(rbase + (unsigned)off[m]) & (int)(0u - ((vmask >> m) & 1u));
+        const unsigned long long c = tile_cost<NCH, M>(b, off, D, G, a_tw, a_sb, use_win, wx0, wy0,
+                                                       s_sa[a], qx, qy, lane, n_glob);
+        ++n_eval;
+        if (lane == 0) D.cost[s] = c;
+    }
+    if (lane == 0 && n_eval) atomicAdd(B.evals[pair] + 2 + dir, (unsigned long long)n_eval);
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(256, (NCH == 6 ? 2 : 3))
+k_cost_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
+    constexpr int WPP = NCH / 2;
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ int s_seed[PC_N], s_u[PC_N], s_ux[PC_N], s_uy[PC_N];
+    __shared__ unsigned char s_f[PC_N];
+    __shared__ unsigned long long s_sa[PC_N];
+    __shared__ int s_med[2];
+    const int dir = blockIdx.y;
+    const DirLvl& D = B.d[blockIdx.z][dir];
+    const int tiles_x = (D.nx + PT_TW - 1) / PT_TW, tiles_y = (D.ny + PT_TH - 1) / PT_TH;
+    if ((int)blockIdx.x >= tiles_x * tiles_y) return;
+    const int i0 = ((int)blockIdx.x % tiles_x) * PT_TW, j0 = ((int)blockIdx.x / tiles_x) * PT_TH;
+    const int P = D.P, h = P / 2, sig = mc.sigma;
+    const PtGeom G = pt_geom(NCH, P, sig, mc.rs_W);
+    uint32_t* s_ref = sm;
+    uint32_t* s_tw = sm + G.ref_h * G.sp;
+    unsigned long long* s_sb = reinterpret_cast<unsigned long long*>(
+        sm + ((G.sp * (G.ref_h + G.win_h) + 1) & ~1));
+    const int rx0 = floor4(mc.c + sig * i0 - h), ry0 = mc.c + sig * j0 - h;
+    stage<WPP>(s_ref, G.sp, D.ref_split, D.ref_pitch >> 1, D.rw, D.rh, rx0, ry0, G.ref_w, G.ref_h);
+
+    bool valid = false;
+    if (threadIdx.x < PC_N) {
+        const int a = threadIdx.x;
+        const int i = i0 + a % PT_TW, j = j0 + a / PT_TW;
+        int s = -1, u = 0, f = 0;
+        if (i < D.nx && j < D.ny) {
+            s = j * D.nx + i;
+            f = D.flags[s];
+            u = D.u[s];
+            const unsigned long long sa =
+                D.sa2img[(size_t)(mc.c + sig * j) * D.rw + (mc.c + sig * i)];
+            s_sa[a] = sa;
+            D.sa2[s] = sa;
+        }
+        s_seed[a] = s;
+        s_u[a] = u;
+        s_f[a] = (unsigned char)f;
+        valid = s >= 0 && (f & F_VALID);
+        s_ux[a] = valid ? lo16((uint32_t)u) : INT_MAX;
+        s_uy[a] = valid ? hi16((uint32_t)u) : INT_MAX;
+        if (a == 0) { s_med[0] = INT_MIN; s_med[1] = INT_MIN; }
+    }
+    const int nv = __syncthreads_count(valid);
+    // median of the valid current displacements: rank by (value, index)
+    if (threadIdx.x < PC_N && valid) {
+        const int a = threadIdx.x, ux = s_ux[a], uy = s_uy[a];
+        int rx = 0, ry = 0;
+        for (int o = 0; o < PC_N; ++o) {          // invalid entries hold INT_MAX
+            const int ox = s_ux[o], oy = s_uy[o];
+            rx += ox < ux || (ox == ux && o < a);
+            ry += oy < uy || (oy == uy && o < a);
+        }
+        if (rx == nv / 2) s_med[0] = ux;
+        if (ry == nv / 2) s_med[1] = uy;
+    }
+    __syncthreads();
+    const int rho = max(1, mc.rs_W);
+    const bool use_win = s_med[0] != INT_MIN;
+    const int wx0 = use_win ? floor4(mc.c + sig * i0 - h + s_med[0] - rho - PT_SLACK) : 0;
+    const int wy0 = use_win ? mc.c + sig * j0 - h + s_med[1] - rho - PT_SLACK : 0;
+    if (use_win) {
+        stage<WPP>(s_tw, G.sp, reinterpret_cast<const uint32_t*>(D.tgt), D.tgt_pitch >> 1, D.tw,
+                   D.th, wx0, wy0, G.win_w, G.win_h);
+        const int cx0 = wx0 + h, cy0 = wy0 + h, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int row = warp; row < G.ch; row += 8) {
+            const unsigned long long* srow = D.sb2 + (size_t)clampi(cy0 + row, 0, D.th - 1) * D.tw;
+            for (int col = lane; col < G.cw; col += 32)
+                cp_async8(s_sb + row * G.cw + col, srow + clampi(cx0 + col, 0, D.tw - 1));
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int groups = (P * G.wprp + 31) / 32;
+#define PGM_COST_SEEDS(MM)                                                                     \
+    cost_seeds<NCH, MM>(B, mc, D, G, s_seed, s_u, s_f, s_sa, s_ref, s_tw, s_sb, i0, j0, rx0,   \
+                        use_win, wx0, wy0)
+    if (NCH == 6) {
+        if (groups <= 4) PGM_COST_SEEDS(4);
+        else if (groups <= 8) PGM_COST_SEEDS(8);
+        else if (groups <= 13) PGM_COST_SEEDS(13);
+        else if (groups <= 16) PGM_COST_SEEDS(16);
+        else if (groups <= 23) PGM_COST_SEEDS(23);
+        else PGM_COST_SEEDS(24);
+    } else {
+        if (groups <= 2) PGM_COST_SEEDS(2);
+        else if (groups <= 5) PGM_COST_SEEDS(5);
+        else PGM_COST_SEEDS(8);
+    }
+#undef PGM_COST_SEEDS
+}
+
+template <int NCH>
+pgm_status launch_c(const LvlBatch& B, const MatchConst& mc, int tiles, int smem_bytes,
+                    cudaStream_t st) {
+    static int configured = 0;
+    if (configured < smem_bytes) {
+        if (cudaFuncSetAttribute(k_cost_t<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_bytes) != cudaSuccess) return PGM_ERR_CUDA;
+        configured = smem_bytes;
+    }
+    k_cost_t<NCH><<<dim3(tiles, 2, B.n), 256, smem_bytes, st>>>(B, mc);
+    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+}
+
 template <int NCH>
 pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, int tiles, int smem_bytes,
                     cudaStream_t st) {
@@ -447,6 +617,27 @@ pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int 
     if ((maxw + 31) / 32 > 24) return PGM_ERR_UNSUPPORTED;
     return nch == 2 ? launch_t<2>(B, mc, tiles, smem_bytes, st)
                     : launch_t<6>(B, mc, tiles, smem_bytes, st);
+}
+
+pgm_status launch_cost_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
+                            cudaStream_t st) {
+    *handled = false;
+    int tiles = 0, words = 0, maxw = 0;
+    for (int k = 0; k < B.n; ++k)
+        for (int d = 0; d < 2; ++d) {
+            const DirLvl& D = B.d[k][d];
+            const int t = ((D.nx + PT_TW - 1) / PT_TW) * ((D.ny + PT_TH - 1) / PT_TH);
+            if (t > tiles) tiles = t;
+            const PtGeom g = pt_geom(nch, D.P, mc.sigma, mc.rs_W);
+            if (g.words > words) words = g.words;
+            if (D.P * g.wprp > maxw) maxw = D.P * g.wprp;
+        }
+    const int smem_bytes = words * 4;
+    if (smem_bytes > 160 * 1024 || (maxw + 31) / 32 > 24) return PGM_OK;
+    *handled = true;
+    if (tiles == 0) return PGM_OK;
+    return nch == 2 ? launch_c<2>(B, mc, tiles, smem_bytes, st)
+                    : launch_c<6>(B, mc, tiles, smem_bytes, st);
 }
 
 }  // namespace pgm
