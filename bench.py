@@ -102,6 +102,40 @@ def run_reference(a):
     return 0
 
 
+# ------------------------------------------------------- ncu traffic record
+def pm_traffic_per_launch(pairs):
+    """DRAM bytes per k_pm_t launch from the committed ncu record, scaled to
+    `pairs` per step; None when the kernel source changed since the capture."""
+    import hashlib
+    rec = os.path.join(ROOT, "profiles", "k_pm_t_traffic.json")
+    src = os.path.join(ROOT, "paper_1704_03217_gb300", "csrc", "pm_tile.cu")
+    try:
+        r = json.load(open(rec))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if r.get("pm_tile_sha256") != h:
+        return None
+    return r["dram_bytes_per_launch"] * pairs / r["pairs"]
+
+
+# ------------------------------------------------------------- multi-rank
+def rank_seeds(rank, batch):
+    """Synthetic pair seeds of one rank: disjoint across ranks."""
+    return [10 * rank * batch + k for k in range(batch)]
+
+
+def max_over_ranks(value, world, device=None):
+    """Max of a float over all ranks (timing only; no data-path collective)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -177,7 +211,7 @@ def run_ours(a):
     dev = torch.device("cuda", local)
     B = a.batch
     prm = api.Params(**PARAMS)
-    pairs = [synth.sintel_like_pair(10 * rank * B + k, W_IMG, H_IMG) for k in range(B)]
+    pairs = [synth.sintel_like_pair(sd, W_IMG, H_IMG) for sd in rank_seeds(rank, B)]
     imgs1 = [torch.from_numpy(p[0]).to(dev) for p in pairs]
     imgs2 = [torch.from_numpy(p[1]).to(dev) for p in pairs]
     m = api.PairMatcher(prm, W_IMG, H_IMG, batch=B, device=dev)
@@ -211,10 +245,7 @@ def run_ours(a):
     launches = L.pgm_launch_count() - launches0
     clk = clocks.stop()
     ms = sum(s.elapsed_time(e) for s, e in ev)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     value = world * B * a.steps / (ms_max * 1e-3)
     nominal = api.nominal_evals(prm, W_IMG, H_IMG, W_IMG, H_IMG)
     counts = [int(c) for c in m.count[:, 0].tolist()]
@@ -242,7 +273,7 @@ def run_ours(a):
             e2e_t += time.perf_counter() - t0
     h2d = sum(x.numel() for x in host1) + sum(x.numel() for x in host2)
     d2h = out_rows.numel() * 4 + out_cnt.numel() * 4
-    e2e = world * B * e2e_steps / e2e_t
+    e2e = world * B * e2e_steps / max_over_ranks(e2e_t, world, dev)
 
     # -------- per-kernel times (profiling pass, not the timed one)
     import ctypes as C
@@ -267,10 +298,12 @@ def run_ours(a):
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-    peak_tops = sms * 128 * sm_mhz * 1e6 / 1e12        # INT32 lanes x clock
-    achieved_tops = 3 * el_per_launch / (pm_launch_ms * 1e-3) / 1e12
+    # integer multiply pipe: 64 lanes/clk/SM, one int16 x int16 element-MAC per lane-op
+    peak_tmac = sms * 64 * sm_mhz * 1e6 / 1e12
+    achieved_tmac = el_per_launch / (pm_launch_ms * 1e-3) / 1e12
     l1_gbs = 2 * el_per_launch / (pm_launch_ms * 1e-3) / 1e9
     l1_peak = sms * 128 * sm_mhz * 1e6 / 1e9
+    traffic = pm_traffic_per_launch(B)
 
     variants = {}
     if not a.no_variants:
@@ -309,13 +342,15 @@ def run_ours(a):
             "e2e": {"value": e2e, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "kernel": "k_pm (propagation + random search)",
-                         "achieved": achieved_tops, "peak": peak_tops, "unit": "Top/s (int32)",
-                         "frac": achieved_tops / peak_tops, "traffic": None,
-                         "peak_source": "derived: %d SMs x 128 INT32 lanes x %.0f MHz" % (sms, sm_mhz),
-                         "ops_per_element": 3,
+            "roofline": {"bound": "alu", "kernel": "k_pm_t (propagation + limited random search)",
+                         "achieved": achieved_tmac, "peak": peak_tmac,
+                         "unit": "Tmac/s (int16 x int16 element multiply-accumulates)",
+                         "frac": achieved_tmac / peak_tmac, "traffic": traffic,
+                         "peak_source": "derived: %d SMs x 64 integer-multiply lanes x %.0f MHz"
+                                        % (sms, sm_mhz),
                          "l1_GBps": l1_gbs, "l1_peak_GBps": l1_peak, "l1_frac": l1_gbs / l1_peak,
-                         "pm_ms_per_launch": pm_launch_ms, "pm_launches_per_step": kernel_launches["pm"]},
+                         "pm_ms_per_launch": pm_launch_ms,
+                         "pm_launches_per_step": kernel_launches["pm"]},
             "kernel_ms_per_step": kernel_ms, "kernel_launches_per_step": kernel_launches,
             "evals_per_step": {"pm": sum(sum(e["pm"]) for e in ev_counts),
                                "cost": sum(sum(e["cost"]) for e in ev_counts),
