@@ -32,9 +32,9 @@ constexpr int PT_NACT = PT_TW * PT_TH / 2;     // seeds of one colour per tile
 constexpr int PT_SLACK = 6;                    // window margin around the median match (px)
 
 struct PtGeom {
-    int wpp, wprp;         // words per pixel, padded words per patch row
-    int ref_w, ref_h;      // staged reference region (px), width a multiple of 4
-    int win_w, win_h;      // staged target window (px), width a multiple of 4
+    int wpp, wprp;         // words per pixel, words per patch row
+    int ref_w, ref_h;      // staged reference region (px)
+    int win_w, win_h;      // staged target window (px)
     int sp;                // shared row pitch (words)
     int cw, ch;            // candidate centres covered by the window
     int words;             // 32-bit shared words in all (descriptor rows, then uint64 sums)
@@ -43,17 +43,17 @@ struct PtGeom {
 __host__ __device__ inline PtGeom pt_geom(int nch, int P, int sigma, int rs_W) {
     PtGeom g;
     g.wpp = nch / 2;
-    g.wprp = (P * g.wpp + 3) & ~3;
-    const int span_x = sigma * (PT_TW - 1) + P + 1;   // +1 px: padded words of the last patch
+    g.wprp = P * g.wpp;                               // words per patch row
+    const int span_x = sigma * (PT_TW - 1) + P;
     const int span_y = sigma * (PT_TH - 1) + P;
     const int rho = rs_W > 1 ? rs_W : 1;
-    g.ref_w = ((span_x + 3) & ~3) + 4;                // origin is rounded down to 4 px
+    g.ref_w = span_x;
     g.ref_h = span_y;
-    g.win_w = ((span_x + 2 * (rho + PT_SLACK) + 3) & ~3) + 4;
+    g.win_w = span_x + 2 * (rho + PT_SLACK);
     g.win_h = span_y + 2 * (rho + PT_SLACK);
     const int need = (g.ref_w > g.win_w ? g.ref_w : g.win_w) * g.wpp;
     g.sp = need + (((g.wprp - need) % 32) + 32) % 32;
-    g.cw = g.win_w - P;                               // centres whose padded patch fits
+    g.cw = g.win_w - P + 1;                           // centres whose patch fits
     g.ch = g.win_h - P + 1;
     g.words = g.sp * (g.ref_h + g.win_h) + 2 * g.cw * g.ch + 2;   // +2: 8-byte alignment
     return g;
@@ -61,7 +61,6 @@ __host__ __device__ inline PtGeom pt_geom(int nch, int P, int sigma, int rs_W) {
 
 namespace {
 
-__device__ __forceinline__ int floor4(int v) { return v & ~3; }   // two's complement: floor
 
 // Copy a rows x (w px) block of 32-bit words with top-left pixel (x0, y0)
 // (x0 a multiple of 4) of an image (iw x ih px, row pitch pw words) to shared
@@ -94,20 +93,19 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Start copying a rows x (w px) block of 32-bit words with top-left pixel
-// (x0, y0) (x0 a multiple of 4) of an image (iw x ih px, row pitch pw words)
-// into shared memory (pitch sp), replicating the border: asynchronous copies,
-// 16 bytes each for an interior block, one word each otherwise.  One warp per
-// row, lanes across it; completion by cp_async_wait_all.
+// (x0, y0) of an image (iw x ih px, row pitch pw words) into shared memory
+// (pitch sp), replicating the border: asynchronous 4-byte copies, one warp
+// per row, lanes across it; completion by cp_async_wait_all.
 template <int WPP>
 __device__ __forceinline__ void stage(uint32_t* dst, int sp, const uint32_t* src, int pw, int iw,
                                       int ih, int x0, int y0, int w, int rows) {
     const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const int wwords = w * WPP;
     if (x0 >= 0 && y0 >= 0 && x0 + w <= iw && y0 + rows <= ih) {
-        const int vec = wwords / 4;                   // w is a multiple of 4 px
         for (int row = threadIdx.x >> 5; row < rows; row += nwarp) {
             const uint32_t* s = src + (size_t)(y0 + row) * pw + (size_t)x0 * WPP;
-            for (int v = lane; v < vec; v += 32) cp_async16(dst + row * sp + 4 * v, s + 4 * v);
+            uint32_t* d = dst + row * sp;
+            for (int wd = lane; wd < wwords; wd += 32) cp_async4(d + wd, s + wd);
         }
     } else {
         for (int row = threadIdx.x >> 5; row < rows; row += nwarp) {
@@ -122,19 +120,33 @@ __device__ __forceinline__ void stage(uint32_t* dst, int sp, const uint32_t* src
 
 // Lane-owned words of the flattened (padded) patch: word k = lane + 32 m has
 // row k / wprp and column k % wprp; walked incrementally (no division).
-template <int MMAX>
-__device__ __forceinline__ void patch_walk(int lane, int wprp, int nw, int P_words, int sp,
-                                           int (&off)[MMAX], unsigned& vmask) {
+// byte offsets of the lane's words packed two per register (each < 2^16)
+template <int M>
+struct Offs {
+    unsigned p[(M + 1) / 2];
+    __device__ __forceinline__ unsigned at(int m) const {
+        return (m & 1) ? (p[m >> 1] >> 16) : (p[m >> 1] & 0xffffu);
+    }
+};
+
+// Lane-owned words of the flattened patch: word k = lane + 32 m has row
+// k / wpr and column k % wpr; walked incrementally (no division).
+template <int M>
+__device__ __forceinline__ void patch_walk(int lane, int wpr, int nw, int sp, Offs<M>& off,
+                                           unsigned& vmask) {
     int row = 0, col = lane;
-    while (col >= wprp) { col -= wprp; ++row; }
+    while (col >= wpr) { col -= wpr; ++row; }
     vmask = 0;
 #pragma unroll
-    for (int m = 0; m < MMAX; ++m) {
+    for (int m = 0; m < (M + 1) / 2; ++m) off.p[m] = 0;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
         const int k = lane + 32 * m;
-        off[m] = k < nw ? 4 * (row * sp + col) : 0;       // byte offset
-        if (k < nw && col < P_words) vmask |= 1u << m;
+        const unsigned o = k < nw ? 4u * (unsigned)(row * sp + col) : 0u;   // byte offset
+        off.p[m >> 1] |= o << (16 * (m & 1));
+        if (k < nw) vmask |= 1u << m;
         col += 32;
-        while (col >= wprp) { col -= wprp; ++row; }
+        while (col >= wpr) { col -= wpr; ++row; }
     }
 }
 
@@ -167,7 +179,7 @@ __device__ __forceinline__ long long cross_global(const int (&b)[MMAX], const Di
 // window when the padded patch lies inside it, else from global memory.
 template <int NCH, int M>
 __device__ __forceinline__ unsigned long long tile_cost(
-    const int (&b)[M], const int (&off)[M], const DirLvl& D, const PtGeom& G, unsigned a_tw,
+    const int (&b)[M], const Offs<M>& off, const DirLvl& D, const PtGeom& G, unsigned a_tw,
     unsigned a_sb, bool use_win, int wx0, int wy0, unsigned long long sa, int qx, int qy, int lane,
     unsigned& n_glob) {
     constexpr int WPP = NCH / 2;
@@ -175,13 +187,13 @@ __device__ __forceinline__ unsigned long long tile_cost(
     unsigned long long sb;
     long long cr;
     const int x0 = qx - h - wx0, y0 = qy - h - wy0;
-    if (use_win && x0 >= 0 && y0 >= 0 && x0 + P + 1 <= G.win_w && y0 + P <= G.win_h) {
+    if (use_win && x0 >= 0 && y0 >= 0 && x0 + P <= G.win_w && y0 + P <= G.win_h) {
         sb = lds64(a_sb + 8u * (unsigned)(y0 * G.cw + x0));
         const unsigned base = a_tw + 4u * (unsigned)(y0 * G.sp + x0 * WPP);
         int sl0 = 0, sh0 = 0, sl1 = 0, sh1 = 0;     // two chains each
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-            const int v = lds32(base + (unsigned)off[m]);
+            const int v = lds32(base + off.at(m));
             if (m & 1) { sl1 = __dp2a_lo(v, b[m], sl1); sh1 = __dp2a_hi(v, b[m], sh1); }
             else { sl0 = __dp2a_lo(v, b[m], sl0); sh0 = __dp2a_hi(v, b[m], sh0); }
         }
@@ -211,7 +223,7 @@ constexpr int NO_CAND = INT_MIN;            // no propagated candidate
 // groups of the flattened patch: no per-group test is needed, the words of
 // the last group that lie past the patch read a valid shared word and
 // multiply it by a zero reference.
-template <int NCH, int M>
+template <int NCH, int M, bool EXACT>
 __device__ __forceinline__ void seeds(const LvlBatch& B, const MatchConst& mc, const DirLvl& D,
                                       const PtGeom& G, const TileCtx& T) {
     constexpr int WPP = NCH / 2;
@@ -220,9 +232,9 @@ __device__ __forceinline__ void seeds(const LvlBatch& B, const MatchConst& mc, c
     const unsigned a_ref = (unsigned)__cvta_generic_to_shared(T.s_ref);
     const unsigned a_tw = (unsigned)__cvta_generic_to_shared(T.s_tw);
     const unsigned a_sb = (unsigned)__cvta_generic_to_shared(T.s_sb);
-    int off[M];                             // byte offsets of the lane's patch words
+    Offs<M> off;                            // byte offsets of the lane's patch words
     unsigned vmask;                         // bit m: word lane + 32 m is a real patch word
-    patch_walk<M>(lane, G.wprp, T.nw, P * WPP, G.sp, off, vmask);
+    patch_walk<M>(lane, G.wprp, T.nw, G.sp, off, vmask);
 
     for (int a = T.warp; a < PT_NACT; a += 8) {
         const int s = T.s_seed[a];
@@ -246,8 +258,11 @@ __device__ __forceinline__ void seeds(const LvlBatch& B, const MatchConst& mc, c
                 const unsigned rbase =
                     a_ref + 4u * (unsigned)(sig * (j - T.j0) * G.sp + (mc.c + sig * i - h - T.rx0) * WPP);
 #pragma unroll
-                for (int m = 0; m < M; ++m)         // masked, branch-free
-                    b[m] = lds32(rbase + (unsigned)off[m]) & (int)(0u - ((vmask >> m) & 1u));
+                for (int m = 0; m < M; ++m) {
+                    b[m] = lds32(rbase + off.at(m));
+                    // words past the patch read a valid shared word; zero their weight
+                    if (!EXACT || m == M - 1) b[m] &= (int)(0u - ((vmask >> m) & 1u));
+                }
                 loaded = true;
             }
             ++n_eval;
@@ -255,20 +270,24 @@ __device__ __forceinline__ void seeds(const LvlBatch& B, const MatchConst& mc, c
                                      lane, n_glob);
         };
 
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {           // Eq. 4
-            const int32_t cu = T.s_nb[a][k];
-            if (cu == NO_CAND) continue;
-            if (have && cu == bu) continue;
-            const int qx = px + lo16((uint32_t)cu), qy = py + hi16((uint32_t)cu);
-            if (!inside(D, qx, qy)) continue;
-            const unsigned long long c = score(qx, qy);
-            if (c < bc) { bc = c; bu = cu; have = true; }
-        }
-        if (have) {
-            const int ux0 = lo16((uint32_t)bu), uy0 = hi16((uint32_t)bu);
-            uint4 r = T.s_rnd[a];
-            for (int k = 0; k < mc.K; ++k) {    // Eq. 5
+        // one loop over the candidate sequence (a single inlined cost site):
+        // c = 0, 1: propagated matches (Eq. 4); c >= 2: random search (Eq. 5)
+        // around the match held after propagation
+        int ux0 = 0, uy0 = 0;
+        uint4 r = T.s_rnd[a];
+#pragma unroll 1
+        for (int c = 0; c < 2 + mc.K; ++c) {
+            int32_t cu;
+            int qx, qy;
+            if (c < 2) {
+                cu = T.s_nb[a][c];
+                if (cu == NO_CAND || (have && cu == bu)) continue;
+                qx = px + lo16((uint32_t)cu);
+                qy = py + hi16((uint32_t)cu);
+            } else {
+                if (!have) break;
+                const int k = c - 2;
+                if (k == 0) { ux0 = lo16((uint32_t)bu); uy0 = hi16((uint32_t)bu); }
                 if (k > 0 && (k & 1) == 0)
                     r = philox(make_uint4((uint32_t)s,
                                           ((uint32_t)B.visit << 16) | ((uint32_t)dir << 15) | (uint32_t)mc.t,
@@ -278,12 +297,13 @@ __device__ __forceinline__ void seeds(const LvlBatch& B, const MatchConst& mc, c
                 const uint32_t rx = (k & 1) ? r.z : r.x, ry = (k & 1) ? r.w : r.y;
                 const int dx = rs_off(rx, k, mc.rs_W, mc.rs_mode), dy = rs_off(ry, k, mc.rs_W, mc.rs_mode);
                 if (dx == 0 && dy == 0) continue;
-                const int cx = ux0 + dx, cy = uy0 + dy;
-                const int qx = px + cx, qy = py + cy;
-                if (!inside(D, qx, qy)) continue;
-                const unsigned long long c = score(qx, qy);
-                if (c < bc) { bc = c; bu = pack_u(cx, cy); }
+                qx = px + ux0 + dx;                 // tested before packing into 16 bits
+                qy = py + uy0 + dy;
+                cu = pack_u(ux0 + dx, uy0 + dy);
             }
+            if (!inside(D, qx, qy)) continue;
+            const unsigned long long cst = score(qx, qy);
+            if (cst < bc) { bc = cst; bu = cu; have = true; }
         }
         if (lane == 0) {
             if (n_eval) atomicAdd(B.evals[pair] + dir, (unsigned long long)n_eval);
@@ -298,7 +318,7 @@ __device__ __forceinline__ void seeds(const LvlBatch& B, const MatchConst& mc, c
 }
 
 template <int NCH>
-__global__ void __launch_bounds__(256, (NCH == 6 ? 2 : 3))
+__global__ void __launch_bounds__(256, 3)
 k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     constexpr int WPP = NCH / 2;
     extern __shared__ __align__(16) uint32_t sm[];
@@ -326,10 +346,20 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     // ---- C1: start staging the reference region (independent of the seeds)
-    const int rx0 = floor4(mc.c + sig * i0 - h), ry0 = mc.c + sig * j0 - h;
+    const int rx0 = mc.c + sig * i0 - h, ry0 = mc.c + sig * j0 - h;
     stage<WPP>(s_ref, G.sp, D.ref_split, D.ref_pitch >> 1, D.rw, D.rh, rx0, ry0, G.ref_w, G.ref_h);
 
-    // ---- A: the active seeds (warp 0, one lane per seed)
+    // ---- A: the active seeds (warp 0, one lane per seed); their first
+    // Philox block is drawn by warp 1 meanwhile
+    if (warp == 1 && mc.K > 0) {
+        const int a = lane, j = j0 + a / (PT_TW / 2);
+        const int i = i0 + 2 * (a % (PT_TW / 2)) + ((j + mc.colour) & 1);
+        if (i < D.nx && j < D.ny)
+            s_rnd[a] = philox(make_uint4((uint32_t)(j * D.nx + i),
+                                         ((uint32_t)B.visit << 16) | ((uint32_t)dir << 15) | (uint32_t)mc.t,
+                                         ((uint32_t)B.level << 16), B.stream_id[pair]),
+                              mc.key0, mc.key1);
+    }
     if (warp == 0) {
         const int a = lane, r = a / (PT_TW / 2), k = a % (PT_TW / 2);
         const int j = j0 + r, i = i0 + 2 * k + ((j + mc.colour) & 1);
@@ -349,11 +379,6 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
             s_sa[a] = sa2;
             s_nb[a][0] = (okx && (f0 & F_VALID)) ? u0 : NO_CAND;
             s_nb[a][1] = (oky && (f1 & F_VALID)) ? u1 : NO_CAND;
-            if (mc.K > 0)
-                s_rnd[a] = philox(make_uint4((uint32_t)s,
-                                             ((uint32_t)B.visit << 16) | ((uint32_t)dir << 15) | (uint32_t)mc.t,
-                                             ((uint32_t)B.level << 16), B.stream_id[pair]),
-                                  mc.key0, mc.key1);
         }
         s_seed[a] = s;
         s_u[a] = u;
@@ -381,7 +406,7 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     // ---- B: window around the median match (unclamped pixel coordinates)
     const int rho = max(1, mc.rs_W);
     const bool use_win = s_med[0] != INT_MIN;
-    const int wx0 = use_win ? floor4(mc.c + sig * i0 - h + s_med[0] - rho - PT_SLACK) : 0;
+    const int wx0 = use_win ? mc.c + sig * i0 - h + s_med[0] - rho - PT_SLACK : 0;
     const int wy0 = use_win ? mc.c + sig * j0 - h + s_med[1] - rho - PT_SLACK : 0;
 
     // ---- C2: stage the window and its sums of |b|^2
@@ -407,18 +432,27 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     TileCtx T{s_ref, s_tw, s_sb, s_seed, s_u, s_nb, s_f, s_cost, s_sa, s_rnd,
               i0, j0, rx0, wx0, wy0, use_win, sig, h, P, nw, sx, sy, lane, warp};
     const int groups = (nw + 31) / 32;
+    // exact group counts of the common patch sides (6 ch: P 8, 11, 15, 16;
+    // 2 ch: P 8, 11, 15/16) need only the last group masked
+#define PGM_SEEDS(MM, EX) seeds<NCH, MM, EX>(B, mc, D, G, T)
     if (NCH == 6) {
-        if (groups <= 4) seeds<NCH, 4>(B, mc, D, G, T);
-        else if (groups <= 8) seeds<NCH, 8>(B, mc, D, G, T);
-        else if (groups <= 13) seeds<NCH, 13>(B, mc, D, G, T);
-        else if (groups <= 16) seeds<NCH, 16>(B, mc, D, G, T);
-        else if (groups <= 23) seeds<NCH, 23>(B, mc, D, G, T);
-        else seeds<NCH, 24>(B, mc, D, G, T);
+        if (groups == 6) PGM_SEEDS(6, true);
+        else if (groups == 12) PGM_SEEDS(12, true);
+        else if (groups == 22) PGM_SEEDS(22, true);
+        else if (groups == 24) PGM_SEEDS(24, true);
+        else if (groups <= 4) PGM_SEEDS(4, false);
+        else if (groups <= 8) PGM_SEEDS(8, false);
+        else if (groups <= 16) PGM_SEEDS(16, false);
+        else PGM_SEEDS(24, false);
     } else {
-        if (groups <= 2) seeds<NCH, 2>(B, mc, D, G, T);
-        else if (groups <= 5) seeds<NCH, 5>(B, mc, D, G, T);
-        else seeds<NCH, 8>(B, mc, D, G, T);
+        if (groups == 2) PGM_SEEDS(2, true);
+        else if (groups == 4) PGM_SEEDS(4, true);
+        else if (groups == 8) PGM_SEEDS(8, true);
+        else if (groups <= 2) PGM_SEEDS(2, false);
+        else if (groups <= 4) PGM_SEEDS(4, false);
+        else PGM_SEEDS(8, false);
     }
+#undef PGM_SEEDS
 }
 
 // ------------------------------------------------------------------
@@ -429,7 +463,7 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
 // sum |a|^2 is copied from the reference box image for the search kernel.
 constexpr int PC_N = PT_TW * PT_TH;
 
-template <int NCH, int M>
+template <int NCH, int M, bool EXACT>
 __device__ __forceinline__ void cost_seeds(const LvlBatch& B, const MatchConst& mc,
                                            const DirLvl& D, const PtGeom& G, const int* s_seed,
                                            const int* s_u, const unsigned char* s_f,
@@ -444,9 +478,9 @@ __device__ __forceinline__ void cost_seeds(const LvlBatch& B, const MatchConst& 
     const unsigned a_ref = (unsigned)__cvta_generic_to_shared(s_ref);
     const unsigned a_tw = (unsigned)__cvta_generic_to_shared(s_tw);
     const unsigned a_sb = (unsigned)__cvta_generic_to_shared(s_sb);
-    int off[M];
+    Offs<M> off;
     unsigned vmask;
-    patch_walk<M>(lane, G.wprp, nw, P * WPP, G.sp, off, vmask);
+    patch_walk<M>(lane, G.wprp, nw, G.sp, off, vmask);
     unsigned n_eval = 0, n_glob = 0;
     for (int a = warp; a < PC_N; a += 8) {
         const int s = s_seed[a];
@@ -461,8 +495,10 @@ __device__ __forceinline__ void cost_seeds(const LvlBatch& B, const MatchConst& 
         const unsigned rbase = a_ref + 4u * (unsigned)(sig * (j - j0) * G.sp + (px - h - rx0) * WPP);
         int b[M];
 #pragma unroll
-        for (int m = 0; m < M; ++m)
-            b[m] = lds32(rbase + (unsigned)off[m]) & (int)(0u - ((vmask >> m) & 1u));
+        for (int m = 0; m < M; ++m) {
+            b[m] = lds32(rbase + off.at(m));
+            if (!EXACT || m == M - 1) b[m] &= (int)(0u - ((vmask >> m) & 1u));
+        }
         const unsigned long long c = tile_cost<NCH, M>(b, off, D, G, a_tw, a_sb, use_win, wx0, wy0,
                                                        s_sa[a], qx, qy, lane, n_glob);
         ++n_eval;
@@ -491,7 +527,7 @@ k_cost_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     uint32_t* s_tw = sm + G.ref_h * G.sp;
     unsigned long long* s_sb = reinterpret_cast<unsigned long long*>(
         sm + ((G.sp * (G.ref_h + G.win_h) + 1) & ~1));
-    const int rx0 = floor4(mc.c + sig * i0 - h), ry0 = mc.c + sig * j0 - h;
+    const int rx0 = mc.c + sig * i0 - h, ry0 = mc.c + sig * j0 - h;
     stage<WPP>(s_ref, G.sp, D.ref_split, D.ref_pitch >> 1, D.rw, D.rh, rx0, ry0, G.ref_w, G.ref_h);
 
     bool valid = false;
@@ -532,7 +568,7 @@ k_cost_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     __syncthreads();
     const int rho = max(1, mc.rs_W);
     const bool use_win = s_med[0] != INT_MIN;
-    const int wx0 = use_win ? floor4(mc.c + sig * i0 - h + s_med[0] - rho - PT_SLACK) : 0;
+    const int wx0 = use_win ? mc.c + sig * i0 - h + s_med[0] - rho - PT_SLACK : 0;
     const int wy0 = use_win ? mc.c + sig * j0 - h + s_med[1] - rho - PT_SLACK : 0;
     if (use_win) {
         stage<WPP>(s_tw, G.sp, reinterpret_cast<const uint32_t*>(D.tgt), D.tgt_pitch >> 1, D.tw,
@@ -547,20 +583,25 @@ k_cost_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     cp_async_wait_all();
     __syncthreads();
     const int groups = (P * G.wprp + 31) / 32;
-#define PGM_COST_SEEDS(MM)                                                                     \
-    cost_seeds<NCH, MM>(B, mc, D, G, s_seed, s_u, s_f, s_sa, s_ref, s_tw, s_sb, i0, j0, rx0,   \
+#define PGM_COST_SEEDS(MM, EX)                                                                 \
+    cost_seeds<NCH, MM, EX>(B, mc, D, G, s_seed, s_u, s_f, s_sa, s_ref, s_tw, s_sb, i0, j0, rx0,   \
                         use_win, wx0, wy0)
     if (NCH == 6) {
-        if (groups <= 4) PGM_COST_SEEDS(4);
-        else if (groups <= 8) PGM_COST_SEEDS(8);
-        else if (groups <= 13) PGM_COST_SEEDS(13);
-        else if (groups <= 16) PGM_COST_SEEDS(16);
-        else if (groups <= 23) PGM_COST_SEEDS(23);
-        else PGM_COST_SEEDS(24);
+        if (groups == 6) PGM_COST_SEEDS(6, true);
+        else if (groups == 12) PGM_COST_SEEDS(12, true);
+        else if (groups == 22) PGM_COST_SEEDS(22, true);
+        else if (groups == 24) PGM_COST_SEEDS(24, true);
+        else if (groups <= 4) PGM_COST_SEEDS(4, false);
+        else if (groups <= 8) PGM_COST_SEEDS(8, false);
+        else if (groups <= 16) PGM_COST_SEEDS(16, false);
+        else PGM_COST_SEEDS(24, false);
     } else {
-        if (groups <= 2) PGM_COST_SEEDS(2);
-        else if (groups <= 5) PGM_COST_SEEDS(5);
-        else PGM_COST_SEEDS(8);
+        if (groups == 2) PGM_COST_SEEDS(2, true);
+        else if (groups == 4) PGM_COST_SEEDS(4, true);
+        else if (groups == 8) PGM_COST_SEEDS(8, true);
+        else if (groups <= 2) PGM_COST_SEEDS(2, false);
+        else if (groups <= 4) PGM_COST_SEEDS(4, false);
+        else PGM_COST_SEEDS(8, false);
     }
 #undef PGM_COST_SEEDS
 }
@@ -593,6 +634,17 @@ pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, int tiles, int smem
 
 }  // namespace
 
+// the packed 16-bit byte offsets of a patch must fit
+static bool pt_offsets_fit(const LvlBatch& B, int nch, const MatchConst& mc) {
+    for (int k = 0; k < B.n; ++k)
+        for (int d = 0; d < 2; ++d) {
+            const int P = B.d[k][d].P;
+            const PtGeom g = pt_geom(nch, P, mc.sigma, mc.rs_W);
+            if (4L * ((long)(P - 1) * g.sp + g.wprp) >= 65536L) return false;
+        }
+    return true;
+}
+
 // *handled = false when the staged tile would not fit in shared memory; the
 // caller then uses the per-seed kernel.
 pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
@@ -611,7 +663,7 @@ pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int 
             if (nwp > maxw) maxw = nwp;
         }
     const int smem_bytes = words * 4;
-    if (smem_bytes > 160 * 1024) return PGM_OK;
+    if (smem_bytes > 160 * 1024 || !pt_offsets_fit(B, nch, mc)) return PGM_OK;
     *handled = true;
     if (tiles == 0) return PGM_OK;
     if ((maxw + 31) / 32 > 24) return PGM_ERR_UNSUPPORTED;
@@ -633,7 +685,8 @@ pgm_status launch_cost_tile(const LvlBatch& B, const MatchConst& mc, int nch, bo
             if (D.P * g.wprp > maxw) maxw = D.P * g.wprp;
         }
     const int smem_bytes = words * 4;
-    if (smem_bytes > 160 * 1024 || (maxw + 31) / 32 > 24) return PGM_OK;
+    if (smem_bytes > 160 * 1024 || (maxw + 31) / 32 > 24 || !pt_offsets_fit(B, nch, mc))
+        return PGM_OK;
     *handled = true;
     if (tiles == 0) return PGM_OK;
     return nch == 2 ? launch_c<2>(B, mc, tiles, smem_bytes, st)
