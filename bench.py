@@ -219,8 +219,11 @@ def run_ours(a):
     stream = torch.cuda.current_stream(dev)
     sids = [rank * B + k for k in range(B)]
 
+    # the whole step is captured once as a CUDA graph and replayed
+    per_step_launches = m.capture(imgs1, imgs2, sids)
+
     def step():
-        m.enqueue(imgs1, imgs2, sids)
+        m.replay()
 
     for _ in range(a.warmup):
         step()
@@ -235,14 +238,13 @@ def run_ours(a):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    launches0 = L.pgm_launch_count()
     for k in range(a.steps):
         flush.fill_(k & 0xff)                      # L2 flush, outside the events
         ev[k][0].record(stream)
         step()
         ev[k][1].record(stream)
     torch.cuda.synchronize()
-    launches = L.pgm_launch_count() - launches0
+    launches = per_step_launches * a.steps
     clk = clocks.stop()
     ms = sum(s.elapsed_time(e) for s, e in ev)
     ms_max = max_over_ranks(ms, world, dev)
@@ -279,9 +281,9 @@ def run_ours(a):
     import ctypes as C
     L.pgm_profile_enable(1)
     prof_steps = 2
-    for _ in range(prof_steps):
+    for _ in range(prof_steps):                 # eager launches: events bracket each kernel
         flush.fill_(1)
-        step()
+        m.enqueue(imgs1, imgs2, sids)
     torch.cuda.synchronize()
     kms = (C.c_double * 7)()
     kn = (C.c_int64 * 7)()
@@ -310,15 +312,16 @@ def run_ours(a):
         for name, kw in VARIANTS.items():
             pv = prm.replace(**kw)
             mv = api.PairMatcher(pv, W_IMG, H_IMG, batch=B, device=dev)
+            mv.capture(imgs1, imgs2, sids)
             for _ in range(2):
-                mv.enqueue(imgs1, imgs2, sids)
+                mv.replay()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             tot = 0.0
             for k in range(max(3, a.steps // 4)):
                 flush.fill_(k)
                 e0.record(stream)
-                mv.enqueue(imgs1, imgs2, sids)
+                mv.replay()
                 e1.record(stream)
                 torch.cuda.synchronize()
                 tot += e0.elapsed_time(e1)
@@ -335,6 +338,7 @@ def run_ours(a):
             "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "pairs_per_step": B, "image": "1024x436x3 uint8",
                        "l2": "flushed (256 MB write) before every timed step",
+                       "launch": "whole step captured once as a CUDA graph, replayed",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "gcand_evals_per_s": nominal * value / 1e9,
             "nominal_evals_per_pair": nominal,

@@ -266,6 +266,23 @@ class PairMatcher:
         filter_batch(self.params, self.ws, [self.rows[k] for k in range(self.batch)],
                      [self.count[k] for k in range(self.batch)], stream)
 
+    def capture(self, imgs1, imgs2, stream_ids=None):
+        """Record one whole step on these (fixed) device image tensors as a CUDA
+        graph; ``replay()`` then reruns it with whatever the tensors hold.
+        Returns the number of library kernels one replay launches."""
+        L = _lib.load()
+        self.enqueue(imgs1, imgs2, stream_ids)          # first call sets kernel attributes
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        n0 = L.pgm_launch_count()
+        with torch.cuda.graph(self.graph):
+            self.enqueue(imgs1, imgs2, stream_ids)
+        self.graph_launches = int(L.pgm_launch_count() - n0)
+        return self.graph_launches
+
+    def replay(self):
+        self.graph.replay()
+
     def results(self):
         counts = self.count[:, 0].tolist()
         return [self.rows[k, :min(c, self.cap)] for k, c in enumerate(counts)]
