@@ -47,7 +47,7 @@ typedef enum {
 } pgm_status;
 
 enum { PGM_GRAY = 0, PGM_RGB = 1 };                 /* params.color           */
-enum { PGM_FULL = 0, PGM_DIR = 1 };                 /* params.descriptor      */
+enum { PGM_FULL = 0, PGM_DIR = 1, PGM_SECTOR = 2 }; /* params.descriptor      */
 enum { PGM_CS_PAPER = 0, PGM_CS_PLAIN = 1 };        /* params.cs_sched        */
 enum { PGM_L2SQ = 0, PGM_L1 = 1 };                  /* params.norm            */
 enum { PGM_RS_SYMMETRIC = 0, PGM_RS_PAPER_FLOOR = 1 }; /* params.rs_mode      */
@@ -65,7 +65,9 @@ typedef struct {
     int32_t patch_bwd;     /* patch side P (1..16) of the backward field   */
     int32_t sobel;         /* S in {3, 5} (Eq. 1)                          */
     int32_t color;         /* PGM_GRAY (PGM-G/GD) or PGM_RGB (PGM-C/CD)    */
-    int32_t descriptor;    /* PGM_FULL gradient or PGM_DIR (G ./ |G|)      */
+    int32_t descriptor;    /* PGM_FULL gradient, PGM_DIR (G ./ |G|) or
+                              PGM_SECTOR (uniform 8-sector angle, coded as
+                              integer unit vectors; beyond the paper)      */
     int32_t cs_sched;      /* PGM_CS_PAPER: Table 2 colour spaces per level
                               and direction; PGM_CS_PLAIN: RGB throughout  */
     int32_t norm;          /* PGM_L2SQ (Eq. 3) or PGM_L1                   */
@@ -79,7 +81,9 @@ typedef struct {
     int32_t region_dmax2;  /* 4-neighbours join a region iff |du|^2 < this */
     int32_t max_visits;    /* 0: whole schedule; k > 0: stop after k visits */
     int32_t ablation;      /* PGM_ABL_* bits (Table 1 rows)                */
-    int32_t reserved;      /* must be 0                                    */
+    int32_t rs_grid;       /* 0: random search at every seed; g > 0: at
+                              level 0 only at seeds whose pixel x and y are
+                              both == g/2 (mod g) (PGM-C3/G3: g = 3)       */
     uint64_t philox_key;   /* key of the random-search stream              */
 } pgm_params;
 

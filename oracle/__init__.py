@@ -23,7 +23,7 @@ FIELDS = [
     ("sobel", 5), ("color", 0), ("descriptor", 0), ("cs_sched", 0), ("norm", 0),
     ("iters_coarse", 4), ("iters_fine", 6), ("refine_rounds", 2), ("rs_W", 2),
     ("rs_mode", 0), ("tau2", 1), ("min_region", 9), ("region_dmax2", 144),
-    ("max_visits", 0), ("ablation", 0), ("reserved", 0),
+    ("max_visits", 0), ("ablation", 0), ("rs_grid", 0),
 ]
 
 
@@ -63,6 +63,7 @@ def lib():
         L.orc_patch_dist.restype = C.c_uint64
         L.orc_rs_offset.argtypes = [C.c_uint32, C.c_int, C.c_int, C.c_int]
         L.orc_rs_offset.restype = C.c_int32
+        L.orc_sector.argtypes = [C.c_int, C.c_int, i16p]
         L.orc_pyr_build.argtypes = [P, u8p, C.c_int, C.c_int, C.c_int]
         L.orc_pyr_build.restype = C.c_void_p
         L.orc_pyr_free.argtypes = [C.c_void_p]
@@ -137,6 +138,12 @@ def patch_dist(A, B, a, b, P, norm=0):
     return int(lib().orc_patch_dist(_ptr(A, C.c_int16), A.shape[2], A.shape[1],
                                     _ptr(B, C.c_int16), B.shape[2], B.shape[1], A.shape[0],
                                     a[0], a[1], b[0], b[1], P, norm))
+
+
+def sector(gx: int, gy: int):
+    o = np.zeros(2, np.int16)
+    lib().orc_sector(gx, gy, _ptr(o, C.c_int16))
+    return int(o[0]), int(o[1])
 
 
 def rs_offset(r: int, k: int, W: int, mode: int) -> int:

@@ -177,6 +177,25 @@ void orc_sobel(const uint8_t* in, int w, int h, int S, int16_t* gx, int16_t* gy)
         }
 }
 
+/* Uniform 8-sector angle descriptor (an extension beyond the paper's two
+ * descriptors): the angle of (gx, gy) is binned into 8 sectors of 45 degrees
+ * centred on the axes and diagonals, by integer comparisons of |gx| and |gy|
+ * against tan(22.5 deg) ~ 169/408 (boundaries go to the axis sectors); the
+ * sector is coded as the integer unit vector 64 (cos, sin) of its centre,
+ * (45, 45) on the diagonals; a zero gradient is (0, 0).  The squared L2 cost of
+ * Eq. 3 then grows with the circular distance between sectors. */
+void orc_sector(int gx, int gy, int16_t out[2]) {
+    static const int16_t code[8][2] = {{64, 0}, {45, 45}, {0, 64}, {-45, 45},
+                                       {-64, 0}, {-45, -45}, {0, -64}, {45, -45}};
+    int ax = gx < 0 ? -gx : gx, ay = gy < 0 ? -gy : gy, s;
+    if (gx == 0 && gy == 0) { out[0] = 0; out[1] = 0; return; }
+    if (408 * ay <= 169 * ax) s = gx > 0 ? 0 : 4;
+    else if (408 * ax <= 169 * ay) s = gy > 0 ? 2 : 6;
+    else if (gx > 0) s = gy > 0 ? 1 : 7;
+    else s = gy > 0 ? 3 : 5;
+    out[0] = code[s][0]; out[1] = code[s][1];
+}
+
 /* ------------------------------------------------------------------ */
 /* Patch distance D_r, Eq. 3 (Sec. III-B): the sum over the patch of the */
 /* squared L2 norm of the gradient-vector difference (norm = 0), or the  */
@@ -289,6 +308,14 @@ orc_pyr* orc_pyr_build(const orc_params* p, const uint8_t* img, int w, int h, in
             if (p->descriptor == 1) {      /* direction only, Sec. III-F: G ./ |G| */
                 for (int64_t i = 0; i < 2 * C * n; ++i)
                     d[i] = (int16_t)(d[i] > 0 ? 1 : (d[i] < 0 ? -1 : 0));   /* R5: 0/0 := 0 */
+            } else if (p->descriptor == 2) {   /* 8-sector angle per colour channel */
+                for (int ch = 0; ch < C; ++ch)
+                    for (int64_t i = 0; i < n; ++i) {
+                        int16_t v[2];
+                        orc_sector(d[ch * n + i], d[(C + ch) * n + i], v);
+                        d[ch * n + i] = v[0];
+                        d[(C + ch) * n + i] = v[1];
+                    }
             }
             py->desc[s][l] = d;
         }
@@ -430,7 +457,11 @@ static void update_seed(orc_match* m, int l, int dir, int visit, int t, int i, i
         uint64_t d = dist(m, l, dir, px, py, px + cx, py + cy);
         if (d < bc) { bc = d; bux = cx; buy = cy; have = 1; }
     }
-    if (have) {
+    /* PGM-C3/G3 (Sec. IV): at full resolution, random search only at the
+     * points of a grid of spacing rs_grid */
+    int g = m->prm.rs_grid;
+    int search = !(l == 0 && g > 0 && !(px % g == g / 2 && py % g == g / 2));
+    if (have && search) {
         /* Eq. 5: Psi = {F(p)} u {F(p) + floor(R_i W / 2^i)}, i = 0..floor(log2 W),
          * all around the post-propagation F(p) */
         int K = 0;
@@ -453,8 +484,8 @@ static void update_seed(orc_match* m, int l, int dir, int visit, int t, int i, i
             uint64_t d = dist(m, l, dir, px, py, px + cx, py + cy);
             if (d < bc) { bc = d; bux = cx; buy = cy; }
         }
-        F->ux[s] = bux; F->uy[s] = buy; F->valid[s] = 1; F->cost[s] = bc;
     }
+    if (have) { F->ux[s] = bux; F->uy[s] = buy; F->valid[s] = 1; F->cost[s] = bc; }
 }
 
 /* Step 1, basic gradient matching: T iterations of propagation + search.

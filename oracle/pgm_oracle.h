@@ -29,7 +29,8 @@ typedef struct {
     int32_t patch_bwd;     /* P for the backward field (r=5 -> 11)        */
     int32_t sobel;         /* S: 3 or 5                                   */
     int32_t color;         /* 0 gray (PGM-G/GD), 1 colour (PGM-C/CD)      */
-    int32_t descriptor;    /* 0 full gradient, 1 direction only           */
+    int32_t descriptor;    /* 0 full gradient, 1 direction only,
+                              2 uniform 8-sector angle                    */
     int32_t cs_sched;      /* 0 Table 2 colour-space schedule, 1 RGB only */
     int32_t norm;          /* 0 squared L2 (Eq. 3), 1 L1                  */
     int32_t iters_coarse;  /* propagation+search iterations at l > 0      */
@@ -43,7 +44,8 @@ typedef struct {
     int32_t max_visits;    /* 0: whole schedule; k > 0: stop after k visits */
     int32_t ablation;      /* bit 0: no refinement, bit 1: propagate all,
                               bit 2: no outlier-record propagation        */
-    int32_t reserved;
+    int32_t rs_grid;       /* 0: search at every seed; g > 0: at level 0 only
+                              where x and y are both == g/2 (mod g)        */
     uint64_t philox_key;
 } orc_params;
 
@@ -57,6 +59,8 @@ uint32_t orc_icbrt(uint64_t v);
 void     orc_convert(int space, const uint8_t* rgb, int64_t n, uint8_t* out);
 void     orc_pyr_down(const uint8_t* in, int w, int h, uint8_t* out);
 void     orc_sobel(const uint8_t* in, int w, int h, int S, int16_t* gx, int16_t* gy);
+/* 8-sector angle code of a gradient as an integer unit vector (x64) */
+void     orc_sector(int gx, int gy, int16_t out[2]);
 uint64_t orc_patch_dist(const int16_t* A, int wa, int ha, const int16_t* B, int wb, int hb,
                         int nch, int ax, int ay, int bx, int by, int P, int norm);
 int32_t  orc_rs_offset(uint32_t r, int k, int W, int mode);

@@ -13,7 +13,7 @@ PARAM_FIELDS = [
     ("color", 1), ("descriptor", 0), ("cs_sched", 0), ("norm", 0), ("iters_coarse", 4),
     ("iters_fine", 6), ("refine_rounds", 2), ("rs_W", 2), ("rs_mode", 0), ("tau2", 1),
     ("min_region", 9), ("region_dmax2", 144), ("max_visits", 0), ("ablation", 0),
-    ("reserved", 0),
+    ("rs_grid", 0),
 ]
 
 

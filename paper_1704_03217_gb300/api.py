@@ -38,7 +38,7 @@ class Params:
     region_dmax2: int = 144
     max_visits: int = 0
     ablation: int = 0
-    reserved: int = 0
+    rs_grid: int = 0
     philox_key: int = 0x5EED5EED1234ABCD
 
     def cstruct(self) -> _lib.CParams:

@@ -57,7 +57,8 @@ pgm_status check_params(const pgm_params* p) {
     if (p->patch_fwd > MAXP || p->patch_bwd > MAXP) return PGM_ERR_UNSUPPORTED;
     if (p->sobel != 3 && p->sobel != 5) return PGM_ERR_ARG;
     if (p->color != PGM_GRAY && p->color != PGM_RGB) return PGM_ERR_ARG;
-    if (p->descriptor != PGM_FULL && p->descriptor != PGM_DIR) return PGM_ERR_ARG;
+    if (p->descriptor != PGM_FULL && p->descriptor != PGM_DIR && p->descriptor != PGM_SECTOR)
+        return PGM_ERR_ARG;
     if (p->cs_sched != PGM_CS_PAPER && p->cs_sched != PGM_CS_PLAIN) return PGM_ERR_ARG;
     if (p->norm != PGM_L2SQ && p->norm != PGM_L1) return PGM_ERR_ARG;
     if (p->iters_coarse < 0 || p->iters_fine < 0 || p->iters_coarse > 32767 ||
@@ -67,7 +68,8 @@ pgm_status check_params(const pgm_params* p) {
     if (p->rs_mode != PGM_RS_SYMMETRIC && p->rs_mode != PGM_RS_PAPER_FLOOR) return PGM_ERR_ARG;
     if (p->tau2 < 0 || p->min_region < 0 || p->region_dmax2 < 0 || p->max_visits < 0)
         return PGM_ERR_ARG;
-    if (p->ablation < 0 || p->ablation > 7 || p->reserved != 0) return PGM_ERR_ARG;
+    if (p->ablation < 0 || p->ablation > 7 || p->rs_grid < 0 || p->rs_grid > 64)
+        return PGM_ERR_ARG;
     return PGM_OK;
 }
 
@@ -231,6 +233,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
     mc.norm = p->norm; mc.rs_W = p->rs_W; mc.rs_mode = p->rs_mode; mc.K = rs_count(p->rs_W);
     mc.key0 = (uint32_t)(p->philox_key & 0xffffffffu); mc.key1 = (uint32_t)(p->philox_key >> 32);
     mc.tau2 = p->tau2;
+    mc.rs_grid = p->rs_grid;
     static thread_local LvlBatch B;       // ~8 KB: kept off the stack
     static thread_local XferBatch X;
     for (int k = 0; k < n; ++k)           // reset the evaluation counters
@@ -349,7 +352,7 @@ void pgm_default_params(pgm_params* p) {
     p->color = PGM_RGB; p->descriptor = PGM_FULL; p->cs_sched = PGM_CS_PAPER; p->norm = PGM_L2SQ;
     p->iters_coarse = 4; p->iters_fine = 6; p->refine_rounds = 2; p->rs_W = 2;
     p->rs_mode = PGM_RS_SYMMETRIC; p->tau2 = 1; p->min_region = 9; p->region_dmax2 = 144;
-    p->max_visits = 0; p->ablation = 0; p->reserved = 0;
+    p->max_visits = 0; p->ablation = 0; p->rs_grid = 0;
     p->philox_key = 0x5EED5EED1234ABCDull;
 }
 
@@ -628,7 +631,15 @@ int64_t pgm_nominal_evals(const pgm_params* p, int w1, int h1, int w2, int h2) {
         const int64_t T = l == 0 ? p->iters_fine : p->iters_coarse;
         for (int d = 0; d < 2; ++d) {
             const int64_t ns = (int64_t)wp.nx[l][d] * wp.ny[l][d];
-            total += ns * (1 + T * per_it);
+            int64_t searching = ns;            // seeds that run the random search
+            if (l == 0 && p->rs_grid > 0) {
+                const int g = p->rs_grid, c = p->seed_stride / 2;
+                int64_t gx = 0, gy = 0;
+                for (int i = 0; i < wp.nx[l][d]; ++i) gx += (c + p->seed_stride * i) % g == g / 2;
+                for (int j = 0; j < wp.ny[l][d]; ++j) gy += (c + p->seed_stride * j) % g == g / 2;
+                searching = gx * gy;
+            }
+            total += ns * (1 + 2 * T) + searching * T * (per_it - 2);
         }
     }
     return total;

@@ -303,7 +303,10 @@ __global__ void __launch_bounds__(256, 3) k_pm_x(const __grid_constant__ LvlBatc
     }
     const int ux0 = lo16(bu), uy0 = hi16(bu);
     uint4 r = make_uint4(0, 0, 0, 0);
-    for (int k = 0; k < mc.K; ++k) {          // Eq. 5
+    const int grid = mc.rs_grid;           // PGM-C3/G3: level-0 search on a grid only
+    const int Kl = (B.level == 0 && grid > 0 && !(px % grid == grid / 2 && py % grid == grid / 2))
+                       ? 0 : mc.K;
+    for (int k = 0; k < Kl; ++k) {          // Eq. 5
         if ((k & 1) == 0) {
             uint4 ctr = make_uint4((uint32_t)s,
                                    ((uint32_t)B.visit << 16) | ((uint32_t)dir << 15) | (uint32_t)mc.t,
@@ -478,7 +481,10 @@ __global__ void __launch_bounds__(256) k_pm(const __grid_constant__ LvlBatch B, 
     // Eq. 5: K candidates around the post-propagation match
     const int ux0 = lo16(bu), uy0 = hi16(bu);
     uint4 r = make_uint4(0, 0, 0, 0);
-    for (int k = 0; k < mc.K; ++k) {
+    const int grid = mc.rs_grid;           // PGM-C3/G3: level-0 search on a grid only
+    const int Kl = (B.level == 0 && grid > 0 && !(px % grid == grid / 2 && py % grid == grid / 2))
+                       ? 0 : mc.K;
+    for (int k = 0; k < Kl; ++k) {
         if ((k & 1) == 0) {
             uint4 ctr = make_uint4((uint32_t)s,
                                    ((uint32_t)B.visit << 16) | ((uint32_t)dir << 15) | (uint32_t)mc.t,

@@ -115,7 +115,7 @@ struct MatchConst {              // scalars common to one launch
     int32_t sigma, c;            // lattice stride and offset
     int32_t norm, rs_W, rs_mode, K;
     uint32_t key0, key1;
-    int32_t t, colour, tau2, pad;
+    int32_t t, colour, tau2, rs_grid;   // rs_grid > 0: level-0 search on that grid only
 };
 
 // Brackets the launches of one kernel class: counts them and, while

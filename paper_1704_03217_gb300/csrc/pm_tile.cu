@@ -275,8 +275,10 @@ __device__ __forceinline__ void seeds(const LvlBatch& B, const MatchConst& mc, c
         // around the match held after propagation
         int ux0 = 0, uy0 = 0;
         uint4 r = T.s_rnd[a];
+        const int g = mc.rs_grid;             // PGM-C3/G3: level-0 search on a grid only
+        const int K = (B.level == 0 && g > 0 && !(px % g == g / 2 && py % g == g / 2)) ? 0 : mc.K;
 #pragma unroll 1
-        for (int c = 0; c < 2 + mc.K; ++c) {
+        for (int c = 0; c < 2 + K; ++c) {
             int32_t cu;
             int qx, qy;
             if (c < 2) {

@@ -178,9 +178,17 @@ __global__ void k_sobel(const __grid_constant__ PyrBatch B, int dir_only) {
             gx += (S == 5 ? s5[j] : s3[j]) * sd;
             gy += (S == 5 ? d5[j] : d3[j]) * ss;
         }
-        if (dir_only) {
+        if (dir_only == 1) {                  // direction only: G ./ |G|
             gx = (gx > 0) - (gx < 0);
             gy = (gy > 0) - (gy < 0);
+        } else if (dir_only == 2) {           // 8-sector angle as an integer unit vector
+            const int ax = abs(gx), ay = abs(gy);
+            int cx, cy;
+            if (gx == 0 && gy == 0) { cx = 0; cy = 0; }
+            else if (408 * ay <= 169 * ax) { cx = gx > 0 ? 64 : -64; cy = 0; }
+            else if (408 * ax <= 169 * ay) { cx = 0; cy = gy > 0 ? 64 : -64; }
+            else { cx = gx > 0 ? 45 : -45; cy = gy > 0 ? 45 : -45; }
+            gx = cx; gy = cy;
         }
         g[ch] = gx;
         g[C + ch] = gy;
@@ -209,7 +217,7 @@ pgm_status launch_pyramid_batch(const pgm_params* p, int n, const PyrPlan* plans
     const int L = p0.L, C = p0.C, nsch = p0.nsch;
     dim3 blk(32, 8);
     auto grid = [&](int w, int h, int z) { return dim3((w + 31) / 32, (h + 7) / 8, z); };
-    const int dir_only = p->descriptor == PGM_DIR;
+    const int dir_only = p->descriptor;      // 0 full, 1 signs, 2 sectors
     for (int base = 0; base < n; base += PYR_MAXB) {
         const int m = n - base < PYR_MAXB ? n - base : PYR_MAXB;
         int nlaunch = L + nsch * L;

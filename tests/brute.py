@@ -123,7 +123,10 @@ def run_pipeline(prm, D1, D2, philox, schedule_kind=0, stream_id=0):
             cc = cost(l, d, px, py, px + cu[0], py + cu[1])
             if bc is None or cc < bc:
                 bc, bu, have = cc, cu, 1
-        if not have:
+        g = prm.get("rs_grid", 0)
+        if not have or (l == 0 and g > 0 and not (px % g == g // 2 and py % g == g // 2)):
+            if have:
+                F.ux[s], F.uy[s], F.valid[s], F.cost[s] = bu[0], bu[1], 1, bc
             return
         u0 = bu
         r = None

@@ -49,6 +49,8 @@ def _compare_fields(M, F, L):
     dict(ablation=2, refine_rounds=2),
     dict(ablation=4, tau2=2),
     dict(ablation=1, levels=3, seed_stride=1, iters_coarse=1, iters_fine=1),
+    dict(descriptor=2, color=1, seed_stride=1, patch_fwd=3, patch_bwd=3),
+    dict(rs_grid=3, seed_stride=1, iters_fine=2),
 ])
 @pytest.mark.parametrize("schedule", [O.SCHED_CHECKERBOARD, O.SCHED_SEQUENTIAL])
 def test_pipeline_brute(case, schedule):

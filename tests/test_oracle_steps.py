@@ -193,3 +193,37 @@ def test_transfer_hand_cases():
         assert got[2:] == want[2:], (r, got)
         if want[2]:
             assert got[:2] == want[:2], (r, got)
+
+
+# ---- uniform 8-sector angle descriptor (an extension) ---------------------
+def test_sector_rule_against_angles():
+    """The integer rule equals round(angle / 45 deg) mod 8 away from the sector
+    boundaries (22.5 deg + k 45 deg; its tan(22.5) ~ 169/408 is within 1e-6);
+    codes are 64 (cos, sin) of the sector centre, 45 on the diagonals."""
+    import math
+    code = {0: (64, 0), 1: (45, 45), 2: (0, 64), 3: (-45, 45), 4: (-64, 0), 5: (-45, -45),
+            6: (0, -64), 7: (45, -45)}
+    rng = np.random.default_rng(8)
+    for gx, gy in rng.integers(-12240, 12241, size=(3000, 2)):
+        gx, gy = int(gx), int(gy)
+        if gx == 0 and gy == 0:
+            continue
+        ang = math.degrees(math.atan2(gy, gx)) % 360.0
+        if abs(((ang - 22.5) % 45.0) - 22.5) > 22.49:          # within 0.01 deg of a boundary
+            continue
+        assert O.sector(gx, gy) == code[int(round(ang / 45.0)) % 8], (gx, gy)
+    assert O.sector(0, 0) == (0, 0)
+    assert O.sector(408, 169) == (64, 0) and O.sector(408, 170) == (45, 45)   # ties to the axis
+    assert O.sector(-169, 408) == (0, 64) and O.sector(-170, 408) == (-45, 45)
+
+
+def test_sector_pyramid_codes():
+    """The descriptor mode 2 writes sector codes of the Sobel gradients."""
+    rng = np.random.default_rng(9)
+    img = rng.integers(0, 256, size=(12, 17), dtype=np.uint8)
+    P0 = O.Pyramid(dict(levels=1, color=0, descriptor=0), img)
+    P2 = O.Pyramid(dict(levels=1, color=0, descriptor=2), img)
+    g, s = P0.desc(0, 0), P2.desc(0, 0)
+    for y in range(12):
+        for x in range(17):
+            assert (s[0, y, x], s[1, y, x]) == O.sector(int(g[0, y, x]), int(g[1, y, x]))

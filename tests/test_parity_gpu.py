@@ -74,6 +74,11 @@ def test_match_every_visit_c1(api):
     ("prop-all", dict(levels=4, color=0, ablation=2), (256, 140)),
     ("no-oprop", dict(levels=4, color=0, ablation=4, refine_rounds=3), (256, 140)),
     ("L1-level", dict(levels=1, color=0, patch_fwd=7, patch_bwd=5, iters_fine=3), (64, 48)),
+    ("sector", dict(levels=4, color=1, descriptor=2), (384, 164)),
+    ("sector-gray", dict(levels=4, color=0, descriptor=2), (301, 157)),
+    ("C3-dense", dict(levels=3, color=1, seed_stride=1, rs_grid=3, patch_fwd=7, patch_bwd=5),
+     (160, 96)),
+    ("G3", dict(levels=4, color=0, rs_grid=3), (301, 157)),
 ])
 def test_pipeline_parity(api, name, prm, size):
     if size is None:
