@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-pairs", type=int, default=0, help="oracle sample size (0: one per core)")
+    ap.add_argument("--serve", type=int, default=300,
+                    help="requests of the serving run (Poisson, 200/s); 0 skips it")
     return ap.parse_args()
 
 
@@ -330,6 +332,10 @@ def run_ours(a):
                               * B * max(3, a.steps // 4) / (tot * 1e-3) / 1e9}
             del mv
 
+    serving = None
+    if a.serve > 0 and rank == 0:
+        serving = run_serving(api, prm, a.serve, dev)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
@@ -361,6 +367,7 @@ def run_ours(a):
                                "init": sum(sum(e["init"]) for e in ev_counts),
                                "pm_global": sum(sum(e["pm_global"]) for e in ev_counts)},
             "variants": variants,
+            "serving": serving,
             "clocks": clk,
             "cpu_baseline": cpu,
         }
@@ -368,6 +375,32 @@ def run_ours(a):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_serving(api, prm, n, dev):
+    """Continuous batching of Poisson arrivals (mean 200 pairs/s) of pairs of
+    640x480, 1280x720, 1920x1080 and 1024x436 under a 40 GB budget, next to
+    the plain form (one pair per launch, one at a time) on the same requests."""
+    import torch
+    from paper_1704_03217_gb300 import serve
+    out = {"offered_pairs_per_s": 200.0, "budget_gb": 40, "requests": n,
+           "sizes": ["640x480", "1280x720", "1920x1080", "1024x436"]}
+    for name, max_batch, streams in (("continuous", 16, 3), ("plain", 1, 1)):
+        reqs = serve.poisson_requests(7, 200.0, n, pool=1)
+        ex = serve.GpuExecutor(prm, streams=streams, device=dev)
+        warm = serve.poisson_requests(8, 1e6, 4, pool=1)          # warm-up, not measured
+        serve.serve(warm, serve.Scheduler(40 << 30, max_batch, ex.bytes_of), ex)
+        torch.cuda.synchronize()
+        sch = serve.Scheduler(40 << 30, max_batch, ex.bytes_of)
+        t0 = time.perf_counter()
+        done = serve.serve(reqs, sch, ex)
+        wall = time.perf_counter() - t0
+        r = serve.summary(done, wall)
+        r["max_batch"], r["streams"] = max_batch, streams
+        r["peak_budget_gb"] = sch.peak / 2 ** 30
+        out[name] = r
+    out["p50_ms"], out["p99_ms"] = out["continuous"]["p50_ms"], out["continuous"]["p99_ms"]
+    return out
 
 
 def main():
