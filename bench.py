@@ -221,7 +221,10 @@ def run_ours(a):
     stream = torch.cuda.current_stream(dev)
     sids = [rank * B + k for k in range(B)]
 
-    # the whole step is captured once as a CUDA graph and replayed
+    # result-invariant launch knobs tuned on this workload, then the whole
+    # step is captured once as a CUDA graph and replayed
+    from paper_1704_03217_gb300 import tune
+    tuned, _ = tune.autotune(m, imgs1, imgs2, reps=2, slacks=(2, 4, 6), chunks=(16, 32))
     per_step_launches = m.capture(imgs1, imgs2, sids)
 
     def step():
@@ -345,6 +348,7 @@ def run_ours(a):
             "config": {"workload": WORKLOAD, "pairs_per_step": B, "image": "1024x436x3 uint8",
                        "l2": "flushed (256 MB write) before every timed step",
                        "launch": "whole step captured once as a CUDA graph, replayed",
+                       "tuning": {"window_slack": tuned[0], "pairs_per_launch": tuned[1]},
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "gcand_evals_per_s": nominal * value / 1e9,
             "nominal_evals_per_pair": nominal,

@@ -287,6 +287,22 @@ pgm_status pgm_profile_enable(int on);
  * pointer may be NULL).  Errors: PGM_ERR_CUDA. */
 pgm_status pgm_profile_read(double* ms, int64_t* launches);
 
+/* Result-invariant tuning knobs (no counterpart in the paper): they change
+ * only how work is laid out on the GPU, never a result.  Process-wide; set
+ * them between calls, not while other threads launch.
+ *   window_slack: margin (pixels, 0..32) of the shared-memory target window
+ *                 around a tile's median match (default 2); candidates
+ *                 outside it are scored from global memory.
+ *   pairs_per_launch: pairs sharing one launch in pgm_match_batch (1..32,
+ *                 default 32). */
+typedef struct {
+    int32_t window_slack;
+    int32_t pairs_per_launch;
+} pgm_tuning;
+/* NULL restores the defaults.  Errors: PGM_ERR_ARG (value out of range). */
+pgm_status pgm_set_tuning(const pgm_tuning* t);
+pgm_status pgm_get_tuning(pgm_tuning* t);
+
 /* Nominal candidate evaluations of one pair under params (2 propagation + K
  * random-search candidates per seed and iteration, one cost per seed and
  * visit, both directions; the exhaustive init is not counted). */

@@ -31,8 +31,13 @@ EXPORTS = [
     "pgm_pyramid_desc_layout", "pgm_pyramid_image_layout", "pgm_match_workspace_bytes",
     "pgm_match", "pgm_match_batch", "pgm_field_layout", "pgm_filter", "pgm_sync_status",
     "pgm_nominal_evals", "pgm_launch_count", "pgm_profile_enable", "pgm_profile_read",
-    "pgm_filter_noalloc", "pgm_build_pyramid_batch", "pgm_filter_batch",
+    "pgm_filter_noalloc", "pgm_build_pyramid_batch", "pgm_filter_batch", "pgm_set_tuning",
+    "pgm_get_tuning",
 ]
+
+
+class CTuning(C.Structure):
+    _fields_ = [("window_slack", C.c_int32), ("pairs_per_launch", C.c_int32)]
 NOALLOC_MAX_SEEDS = 1 << 20
 K_CLASSES = ["pyramid", "init", "cost", "pm", "consist", "transfer", "filter"]
 WS_EVALS_OFFSET, WS_EVALS_COUNT = 8, 8   # pm, cost, init, pm-from-global: fwd/bwd each
@@ -78,6 +83,8 @@ def load(path: str = LIB_PATH):
     L.pgm_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.pgm_profile_read.restype = C.c_int
     L.pgm_filter_noalloc.argtypes = [P, i32, i32, vp, vp, vp, i64, vp, vp]
+    L.pgm_set_tuning.argtypes = [C.POINTER(CTuning)]; L.pgm_set_tuning.restype = C.c_int
+    L.pgm_get_tuning.argtypes = [C.POINTER(CTuning)]; L.pgm_get_tuning.restype = C.c_int
     L.pgm_build_pyramid_batch.argtypes = [P, i32, C.POINTER(vp), C.POINTER(C.c_int32), psz,
                                           C.POINTER(vp), psz, vp]
     L.pgm_filter_batch.argtypes = [P, i32, C.POINTER(C.c_int32), C.POINTER(vp), psz,

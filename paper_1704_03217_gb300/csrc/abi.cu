@@ -12,6 +12,10 @@ namespace pgm {
 // ------------------------------------------------------ launch accounting
 static std::atomic<long long> g_launches{0};
 
+// ------------------------------------------------------------ tuning knobs
+static std::atomic<int> g_slack{2}, g_chunk{MAXB};
+Tuning tuning() { return Tuning{g_slack.load(), g_chunk.load()}; }
+
 namespace {
 struct ProfEvent { int cls; int n; cudaEvent_t a, b; };
 struct ProfState {
@@ -234,6 +238,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
     mc.key0 = (uint32_t)(p->philox_key & 0xffffffffu); mc.key1 = (uint32_t)(p->philox_key >> 32);
     mc.tau2 = p->tau2;
     mc.rs_grid = p->rs_grid;
+    mc.slack = tuning().slack;
     static thread_local LvlBatch B;       // ~8 KB: kept off the stack
     static thread_local XferBatch X;
     for (int k = 0; k < n; ++k)           // reset the evaluation counters
@@ -479,8 +484,9 @@ pgm_status pgm_match_batch(const pgm_params* p, int n, const void* const* d_pyr1
     if (n < 0 || (n > 0 && (!d_pyr1 || !d_pyr2 || !dims || !stream_ids || !d_ws || !ws_bytes)))
         return PGM_ERR_ARG;
     static thread_local PairCtx ctx[MAXB];
-    for (int base = 0; base < n; base += MAXB) {      // validate everything first
-        int m = n - base < MAXB ? n - base : MAXB;
+    const int chunk = tuning().chunk;
+    for (int base = 0; base < n; base += chunk) {     // validate everything first
+        int m = n - base < chunk ? n - base : chunk;
         for (int k = 0; k < m; ++k) {
             int i = base + k;
             r = prepare_pair(p, d_pyr1[i], d_pyr2[i], dims[4 * i], dims[4 * i + 1],
@@ -489,8 +495,8 @@ pgm_status pgm_match_batch(const pgm_params* p, int n, const void* const* d_pyr1
             if (r != PGM_OK) return r;
         }
     }
-    for (int base = 0; base < n; base += MAXB) {
-        int m = n - base < MAXB ? n - base : MAXB;
+    for (int base = 0; base < n; base += chunk) {
+        int m = n - base < chunk ? n - base : chunk;
         for (int k = 0; k < m; ++k) {
             int i = base + k;
             prepare_pair(p, d_pyr1[i], d_pyr2[i], dims[4 * i], dims[4 * i + 1], dims[4 * i + 2],
@@ -583,6 +589,22 @@ pgm_status pgm_sync_status(const pgm_params* p, int w1, int h1, int w2, int h2, 
             return PGM_ERR_CUDA;
         return (pgm_status)word;
     }
+    return PGM_OK;
+}
+
+pgm_status pgm_set_tuning(const pgm_tuning* t) {
+    if (!t) { g_slack = 2; g_chunk = MAXB; return PGM_OK; }
+    if (t->window_slack < 0 || t->window_slack > 32 || t->pairs_per_launch < 1 ||
+        t->pairs_per_launch > MAXB) return PGM_ERR_ARG;
+    g_slack = t->window_slack;
+    g_chunk = t->pairs_per_launch;
+    return PGM_OK;
+}
+
+pgm_status pgm_get_tuning(pgm_tuning* t) {
+    if (!t) return PGM_ERR_ARG;
+    t->window_slack = g_slack;
+    t->pairs_per_launch = g_chunk;
     return PGM_OK;
 }
 

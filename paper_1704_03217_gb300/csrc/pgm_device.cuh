@@ -116,7 +116,12 @@ struct MatchConst {              // scalars common to one launch
     int32_t norm, rs_W, rs_mode, K;
     uint32_t key0, key1;
     int32_t t, colour, tau2, rs_grid;   // rs_grid > 0: level-0 search on that grid only
+    int32_t slack, pad2;                // tuning: target-window margin of the tile kernels
 };
+
+// result-invariant tuning knobs (pgm_set_tuning)
+struct Tuning { int slack; int chunk; };
+Tuning tuning();
 
 // Brackets the launches of one kernel class: counts them and, while
 // pgm_profile_enable(1) is on for this thread, records an event pair.

@@ -29,7 +29,6 @@ namespace pgm {
 
 constexpr int PT_TW = 8, PT_TH = 8;            // lattice seeds per tile
 constexpr int PT_NACT = PT_TW * PT_TH / 2;     // seeds of one colour per tile
-constexpr int PT_SLACK = 6;                    // window margin around the median match (px)
 
 struct PtGeom {
     int wpp, wprp;         // words per pixel, words per patch row
@@ -40,7 +39,7 @@ struct PtGeom {
     int words;             // 32-bit shared words in all (descriptor rows, then uint64 sums)
 };
 
-__host__ __device__ inline PtGeom pt_geom(int nch, int P, int sigma, int rs_W) {
+__host__ __device__ inline PtGeom pt_geom(int nch, int P, int sigma, int rs_W, int slack) {
     PtGeom g;
     g.wpp = nch / 2;
     g.wprp = P * g.wpp;                               // words per patch row
@@ -49,8 +48,8 @@ __host__ __device__ inline PtGeom pt_geom(int nch, int P, int sigma, int rs_W) {
     const int rho = rs_W > 1 ? rs_W : 1;
     g.ref_w = span_x;
     g.ref_h = span_y;
-    g.win_w = span_x + 2 * (rho + PT_SLACK);
-    g.win_h = span_y + 2 * (rho + PT_SLACK);
+    g.win_w = span_x + 2 * (rho + slack);
+    g.win_h = span_y + 2 * (rho + slack);
     const int need = (g.ref_w > g.win_w ? g.ref_w : g.win_w) * g.wpp;
     g.sp = need + (((g.wprp - need) % 32) + 32) % 32;
     g.cw = g.win_w - P + 1;                           // centres whose patch fits
@@ -339,7 +338,7 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     const int i0 = ((int)blockIdx.x % tiles_x) * PT_TW, j0 = ((int)blockIdx.x / tiles_x) * PT_TH;
     const int P = D.P, h = P / 2;
     const int sig = mc.sigma;
-    const PtGeom G = pt_geom(NCH, P, sig, mc.rs_W);
+    const PtGeom G = pt_geom(NCH, P, sig, mc.rs_W, mc.slack);
     const int nw = P * G.wprp;
     uint32_t* s_ref = sm;
     uint32_t* s_tw = sm + G.ref_h * G.sp;
@@ -408,8 +407,8 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     // ---- B: window around the median match (unclamped pixel coordinates)
     const int rho = max(1, mc.rs_W);
     const bool use_win = s_med[0] != INT_MIN;
-    const int wx0 = use_win ? mc.c + sig * i0 - h + s_med[0] - rho - PT_SLACK : 0;
-    const int wy0 = use_win ? mc.c + sig * j0 - h + s_med[1] - rho - PT_SLACK : 0;
+    const int wx0 = use_win ? mc.c + sig * i0 - h + s_med[0] - rho - mc.slack : 0;
+    const int wy0 = use_win ? mc.c + sig * j0 - h + s_med[1] - rho - mc.slack : 0;
 
     // ---- C2: stage the window and its sums of |b|^2
     unsigned long long* s_sb = reinterpret_cast<unsigned long long*>(
@@ -524,7 +523,7 @@ k_cost_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     if ((int)blockIdx.x >= tiles_x * tiles_y) return;
     const int i0 = ((int)blockIdx.x % tiles_x) * PT_TW, j0 = ((int)blockIdx.x / tiles_x) * PT_TH;
     const int P = D.P, h = P / 2, sig = mc.sigma;
-    const PtGeom G = pt_geom(NCH, P, sig, mc.rs_W);
+    const PtGeom G = pt_geom(NCH, P, sig, mc.rs_W, mc.slack);
     uint32_t* s_ref = sm;
     uint32_t* s_tw = sm + G.ref_h * G.sp;
     unsigned long long* s_sb = reinterpret_cast<unsigned long long*>(
@@ -570,8 +569,8 @@ k_cost_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     __syncthreads();
     const int rho = max(1, mc.rs_W);
     const bool use_win = s_med[0] != INT_MIN;
-    const int wx0 = use_win ? mc.c + sig * i0 - h + s_med[0] - rho - PT_SLACK : 0;
-    const int wy0 = use_win ? mc.c + sig * j0 - h + s_med[1] - rho - PT_SLACK : 0;
+    const int wx0 = use_win ? mc.c + sig * i0 - h + s_med[0] - rho - mc.slack : 0;
+    const int wy0 = use_win ? mc.c + sig * j0 - h + s_med[1] - rho - mc.slack : 0;
     if (use_win) {
         stage<WPP>(s_tw, G.sp, reinterpret_cast<const uint32_t*>(D.tgt), D.tgt_pitch >> 1, D.tw,
                    D.th, wx0, wy0, G.win_w, G.win_h);
@@ -641,7 +640,7 @@ static bool pt_offsets_fit(const LvlBatch& B, int nch, const MatchConst& mc) {
     for (int k = 0; k < B.n; ++k)
         for (int d = 0; d < 2; ++d) {
             const int P = B.d[k][d].P;
-            const PtGeom g = pt_geom(nch, P, mc.sigma, mc.rs_W);
+            const PtGeom g = pt_geom(nch, P, mc.sigma, mc.rs_W, mc.slack);
             if (4L * ((long)(P - 1) * g.sp + g.wprp) >= 65536L) return false;
         }
     return true;
@@ -659,7 +658,7 @@ pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int 
             const DirLvl& D = B.d[k][d];
             const int t = ((D.nx + PT_TW - 1) / PT_TW) * ((D.ny + PT_TH - 1) / PT_TH);
             if (t > tiles) tiles = t;
-            const PtGeom g = pt_geom(nch, D.P, mc.sigma, mc.rs_W);
+            const PtGeom g = pt_geom(nch, D.P, mc.sigma, mc.rs_W, mc.slack);
             if (g.words > words) words = g.words;
             const int nwp = D.P * g.wprp;
             if (nwp > maxw) maxw = nwp;
@@ -682,7 +681,7 @@ pgm_status launch_cost_tile(const LvlBatch& B, const MatchConst& mc, int nch, bo
             const DirLvl& D = B.d[k][d];
             const int t = ((D.nx + PT_TW - 1) / PT_TW) * ((D.ny + PT_TH - 1) / PT_TH);
             if (t > tiles) tiles = t;
-            const PtGeom g = pt_geom(nch, D.P, mc.sigma, mc.rs_W);
+            const PtGeom g = pt_geom(nch, D.P, mc.sigma, mc.rs_W, mc.slack);
             if (g.words > words) words = g.words;
             if (D.P * g.wprp > maxw) maxw = D.P * g.wprp;
         }
