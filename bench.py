@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-pairs", type=int, default=0, help="oracle sample size (0: one per core)")
+    ap.add_argument("--tuning", default="",
+                    help="fixed launch knobs 'SLACK,PAIRS' instead of autotuning them")
     ap.add_argument("--serve", type=int, default=300,
                     help="requests of the serving run (Poisson, 200/s); 0 skips it")
     return ap.parse_args()
@@ -224,7 +226,11 @@ def run_ours(a):
     # result-invariant launch knobs tuned on this workload, then the whole
     # step is captured once as a CUDA graph and replayed
     from paper_1704_03217_gb300 import tune
-    tuned, _ = tune.autotune(m, imgs1, imgs2, reps=2, slacks=(2, 4, 6), chunks=(16, 32))
+    if a.tuning:
+        tuned = tuple(int(x) for x in a.tuning.split(","))
+        tune.set(*tuned)
+    else:
+        tuned, _ = tune.autotune(m, imgs1, imgs2, reps=2, slacks=(2, 4, 6), chunks=(16, 32))
     per_step_launches = m.capture(imgs1, imgs2, sids)
 
     def step():

@@ -280,6 +280,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
             }
             B.stream_id[k] = ctx[k].stream_id;
             B.evals[k] = reinterpret_cast<unsigned long long*>(ctx[k].ws + PGM_WS_EVALS_OFFSET);
+            B.err[k] = reinterpret_cast<uint32_t*>(ctx[k].ws + ctx[k].w.off_err);
         }
         pgm_status r;
         if (v == 0) {

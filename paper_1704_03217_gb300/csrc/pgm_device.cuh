@@ -99,6 +99,7 @@ struct LvlBatch {
     DirLvl d[MAXB][2];
     uint32_t stream_id[MAXB];
     unsigned long long* evals[MAXB];       // workspace header counters (include/pgm.h)
+    uint32_t* err[MAXB];                   // workspace status words (pgm_sync_status)
 };
 
 // One direction of one pair for the transfer between levels.

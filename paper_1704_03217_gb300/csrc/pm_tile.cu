@@ -1,23 +1,23 @@
 // pm_tile.cu -- one checkerboard colour phase of propagation (Eq. 4) and
-// limited random search (Eq. 5), squared-L2 cost, on seed tiles staged in
-// shared memory.
+// limited random search (Eq. 5), and the cost refresh at the start of a
+// visit, squared-L2 cost, on seed tiles staged in shared memory.
 //
-// A CTA owns an 8 x 8 tile of lattice seeds; the 32 seeds of the current
-// colour update, one warp per seed at a time.  Before any cost is computed the
-// CTA stages into shared memory
+// A tile is 8 x 8 lattice seeds; the 32 seeds of the current colour update,
+// one warp per seed at a time.  Before any cost is computed the tile's
+// shared-memory buffer receives
 //   - the reference region covering all patches of the tile, in the
 //     split-byte form (a = 128 a_h + a_l) that the dp2a cross products use;
 //   - a fixed-size target window around the tile's median displacement,
-//     wide enough for the random-search square plus a slack.
+//     wide enough for the random-search square plus a margin, and the sum
+//     |b|^2 of every patch centre inside it.
 // Both are staged in unclamped pixel coordinates with the image border
 // replicated, so the inner loop needs no border tests.
 //
-// Patch rows are padded to a multiple of 4 words (the padding words carry a
-// zero reference, so they add nothing), which makes every staged row 16-byte
-// aligned, and the shared row pitch is congruent to the padded row modulo 32:
-// the 32 consecutive words of a flattened patch that a warp reads fall in 32
-// different banks.  A candidate whose padded patch is not inside the window is
-// scored from global memory instead.  The cost of a candidate is
+// Lane l owns the words l, l + 32, ... of the flattened patch (P rows of P
+// pixels times the words per pixel, no padding), and the shared row pitch is
+// congruent to the patch row modulo 32: the 32 consecutive words that a warp
+// reads fall in 32 different banks.  A candidate whose patch is not inside
+// the window is scored from global memory instead.  The cost of a candidate is
 //   D = sum |a|^2 + sum |b|^2 - 2 sum <a, b>,
 // exact in integers, with sum |a|^2 per seed and sum |b|^2 per target pixel
 // computed by other kernels of the same visit.
@@ -65,10 +65,6 @@ namespace {
 // (x0 a multiple of 4) of an image (iw x ih px, row pitch pw words) to shared
 // memory (pitch sp), replicating the border.  Interior blocks move as 16-byte
 // vectors, others word by word.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
-                     (unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
-}
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
                      (unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
@@ -93,21 +89,22 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Start copying a rows x (w px) block of 32-bit words with top-left pixel
 // (x0, y0) of an image (iw x ih px, row pitch pw words) into shared memory
-// (pitch sp), replicating the border: asynchronous 4-byte copies, one warp
-// per row, lanes across it; completion by cp_async_wait_all.
+// (pitch sp), replicating the border: asynchronous 4-byte copies, warps w0,
+// w0 + nwarp, ... one row each, lanes across it; completion by
+// cp_async_wait_all.
 template <int WPP>
 __device__ __forceinline__ void stage(uint32_t* dst, int sp, const uint32_t* src, int pw, int iw,
-                                      int ih, int x0, int y0, int w, int rows) {
-    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+                                      int ih, int x0, int y0, int w, int rows, int w0, int nwarp) {
+    const int lane = threadIdx.x & 31;
     const int wwords = w * WPP;
     if (x0 >= 0 && y0 >= 0 && x0 + w <= iw && y0 + rows <= ih) {
-        for (int row = threadIdx.x >> 5; row < rows; row += nwarp) {
+        for (int row = w0; row < rows; row += nwarp) {
             const uint32_t* s = src + (size_t)(y0 + row) * pw + (size_t)x0 * WPP;
             uint32_t* d = dst + row * sp;
             for (int wd = lane; wd < wwords; wd += 32) cp_async4(d + wd, s + wd);
         }
     } else {
-        for (int row = threadIdx.x >> 5; row < rows; row += nwarp) {
+        for (int row = w0; row < rows; row += nwarp) {
             const uint32_t* srow = src + (size_t)clampi(y0 + row, 0, ih - 1) * pw;
             for (int wd = lane; wd < wwords; wd += 32) {
                 const int pix = wd / WPP, wi = wd - pix * WPP;      // WPP is 1 or 3
@@ -117,19 +114,16 @@ __device__ __forceinline__ void stage(uint32_t* dst, int sp, const uint32_t* src
     }
 }
 
-// Lane-owned words of the flattened (padded) patch: word k = lane + 32 m has
-// row k / wprp and column k % wprp; walked incrementally (no division).
-// byte offsets of the lane's words packed two per register (each < 2^16)
+// Byte offsets of the lane-owned words k = lane + 32 m of a flattened patch
+// (row k / wprp, column k % wprp of a staged block with row pitch sp).
 template <int M>
 struct Offs {
-    unsigned p[(M + 1) / 2];
-    __device__ __forceinline__ unsigned at(int m) const {
-        return (m & 1) ? (p[m >> 1] >> 16) : (p[m >> 1] & 0xffffu);
-    }
+    unsigned p[M];
+    __device__ __forceinline__ unsigned at(int m) const { return p[m]; }
 };
 
-// Lane-owned words of the flattened patch: word k = lane + 32 m has row
-// k / wpr and column k % wpr; walked incrementally (no division).
+// The same offsets walked incrementally (no division); bit m of vmask: word
+// lane + 32 m is a real patch word.
 template <int M>
 __device__ __forceinline__ void patch_walk(int lane, int wpr, int nw, int sp, Offs<M>& off,
                                            unsigned& vmask) {
@@ -137,12 +131,9 @@ __device__ __forceinline__ void patch_walk(int lane, int wpr, int nw, int sp, Of
     while (col >= wpr) { col -= wpr; ++row; }
     vmask = 0;
 #pragma unroll
-    for (int m = 0; m < (M + 1) / 2; ++m) off.p[m] = 0;
-#pragma unroll
     for (int m = 0; m < M; ++m) {
         const int k = lane + 32 * m;
-        const unsigned o = k < nw ? 4u * (unsigned)(row * sp + col) : 0u;   // byte offset
-        off.p[m >> 1] |= o << (16 * (m & 1));
+        off.p[m] = k < nw ? 4u * (unsigned)(row * sp + col) : 0u;
         if (k < nw) vmask |= 1u << m;
         col += 32;
         while (col >= wpr) { col -= wpr; ++row; }
@@ -207,188 +198,282 @@ __device__ __forceinline__ unsigned long long tile_cost(
     return xcost(sa, sb, cr);
 }
 
-struct TileCtx {
-    const uint32_t* s_ref; const uint32_t* s_tw; const unsigned long long* s_sb;
-    const int* s_seed; const int* s_u; const int (*s_nb)[2]; const unsigned char* s_f;
-    const unsigned long long* s_cost; const unsigned long long* s_sa; const uint4* s_rnd;
-    int i0, j0, rx0, wx0, wy0;
-    bool use_win;
-    int sig, h, P, nw, sx, sy, lane, warp;
+// ------------------------------------------------------------------
+// Search kernel, persistent form.  A CTA holds two tile buffers in shared
+// memory and walks its share of the launch's tiles (all pairs and both
+// directions, flattened).  While the consumer warps score the active seeds
+// of tile n from one buffer, the producer warps prepare tile n + 1 in the
+// other: they read its seeds, drop the propagated candidates that cannot
+// change the result (Eq. 4: an unusable neighbour, a centre outside the
+// target, a repeat of the current match or of the other candidate), draw the
+// first Philox block of every seed for the random search (Eq. 5), place the
+// target window at the median match, and stage the reference region, the
+// window and the window's sums |b|^2.  Rows move as bulk asynchronous copies
+// (one per row, 16-byte aligned, completing on the buffer's mbarrier); the
+// words outside the image (replicated border) and a ragged row end go by
+// 4-byte copies.  A barrier per tile hands the buffers over.
+//
+// Shared layout.  Every staged row is 16-byte aligned: shared word j of a
+// row holds image word x0 * wpp - sh + j, with sh = x0 * wpp mod 4.  The
+// words of a flattened patch are spread over 32-word groups of two kinds:
+//   A: words 32 j .. 32 j + 31 of patch row r (q = wprp / 32 per row; lane l
+//      takes word 32 j + l): 32 consecutive words, conflict-free at any pitch;
+//   B: the wl = wprp % 32 remaining words of g consecutive rows; lane l takes
+//      word 32 q + l % S of row g b + l / S, with S the power of two >= wl and
+//      g = 32 / S.  The window pitch is congruent to S modulo 32 (to 4 when
+//      S < 4), so the g row pieces fall in disjoint banks.
+// A lane without a word in a B group reads lane 0's word (a broadcast) and
+// carries a zero reference.  The reference region has its own, narrower
+// pitch; its lane offsets are read from a table when a seed's reference
+// words are loaded, the window's stay in registers.
+constexpr int PP_CONS = 8, PP_PROD = 2;          // consumer / producer warps
+constexpr int PP_THREADS = 32 * (PP_CONS + PP_PROD);
+constexpr int PP_MMAX = 24;                      // 32-word groups of the largest patch
+constexpr long long PP_WAIT_CYCLES = 1ll << 31;  // bounded mbarrier wait (about 1 s)
+
+struct PpGeom {
+    int wpp, wprp, q, wl, S, g, nA, nB, M;
+    int ref_w, ref_h, win_w, win_h;   // staged regions (px)
+    int spr, spw;                     // words per shared row: reference region, window
+    int cw, ch, cwp;                  // window centres (cw x ch), sums row pitch (even)
+    int off_win, off_sb;              // word offsets in a buffer
+    int words;                        // one buffer (multiple of 4)
 };
+
+__host__ __device__ inline int pp_pitch(int need, int res) {
+    need = (need + 3) & ~3;
+    return need + (((res - need) % 32) + 32) % 32;
+}
+
+__host__ __device__ inline PpGeom pp_geom(int nch, int P, int sigma, int rs_W, int slack) {
+    PpGeom g;
+    g.wpp = nch / 2;
+    g.wprp = P * g.wpp;
+    g.q = g.wprp / 32;
+    g.wl = g.wprp % 32;
+    g.S = 0;
+    g.g = 0;
+    if (g.wl > 0) {
+        g.S = 1;
+        while (g.S < g.wl) g.S <<= 1;
+        g.g = 32 / g.S;
+    }
+    g.nA = P * g.q;
+    g.nB = g.wl > 0 ? (P + g.g - 1) / g.g : 0;
+    g.M = g.nA + g.nB;
+    const int rho = rs_W > 1 ? rs_W : 1;
+    g.ref_w = sigma * (PT_TW - 1) + P;
+    g.ref_h = sigma * (PT_TH - 1) + P;
+    g.win_w = g.ref_w + 2 * (rho + slack);
+    g.win_h = g.ref_h + 2 * (rho + slack);
+    const int res = g.S >= 4 ? (g.S & 31) : 4;
+    g.spr = pp_pitch(3 + g.ref_w * g.wpp, res);       // + up to 3 words of alignment shift
+    g.spw = pp_pitch(3 + g.win_w * g.wpp, res);
+    g.cw = g.win_w - P + 1;
+    g.ch = g.win_h - P + 1;
+    g.cwp = (g.cw + 2) & ~1;                           // + 1 centre of alignment shift
+    g.off_win = g.spr * g.ref_h;
+    g.off_sb = g.off_win + g.spw * g.win_h;            // a multiple of 4 words
+    g.words = (g.off_sb + 2 * g.cwp * g.ch + 3) & ~3;
+    return g;
+}
+
+// Patch row and word of lane l in group m (A or B); *valid = false for a
+// lane without a word (it then names lane 0's word of the group).
+__host__ __device__ inline void pp_word(const PpGeom& g, int P, int m, int l, int* row, int* col,
+                                        bool* valid) {
+    if (m >= g.M) { *row = 0; *col = 0; *valid = false; return; }
+    if (m < g.nA) {
+        *row = m / g.q;
+        *col = 32 * (m % g.q) + l;
+        *valid = true;
+        return;
+    }
+    const int b = m - g.nA;
+    *row = b * g.g + l / g.S;
+    *col = 32 * g.q + l % g.S;
+    *valid = l % g.S < g.wl && *row < P;
+    if (!*valid) { *row = b * g.g; *col = 32 * g.q; }
+}
+
+struct __align__(16) SeedRec {      // one active seed of a staged tile
+    int s, px, py, f;               // seed index (-1: none), centre, flags
+    int u, nb0, nb1, K;             // current match; propagated candidates to score; search count
+    int r0, r1, pad0, pad1;         // random-search offsets k = 0, 1 (packed like u)
+    unsigned long long cost, sa;    // current cost, sum |a|^2 of the reference patch
+};
+
+struct TileHdr { int pair, dir, i0, j0, rx0, wx0, wy0, use_win, shr, shw, shs, pad; };
+
+// The flattened tiles of one launch: (pair, dir) slot k = 2 pair + dir owns
+// tiles [cum[k], cum[k + 1]).
+struct PtSched { int nk, total; int cum[2 * MAXB + 1]; };
 
 constexpr int NO_CAND = INT_MIN;            // no propagated candidate
 
-// The seeds of one tile and colour, one warp each.  M = number of 32-word
-// groups of the flattened patch: no per-group test is needed, the words of
-// the last group that lie past the patch read a valid shared word and
-// multiply it by a zero reference.
-template <int NCH, int M, bool EXACT>
-__device__ __forceinline__ void seeds(const LvlBatch& B, const MatchConst& mc, const DirLvl& D,
-                                      const PtGeom& G, const TileCtx& T) {
-    constexpr int WPP = NCH / 2;
-    const int lane = T.lane, P = T.P, h = T.h, sig = T.sig;
-    const int pair = blockIdx.z, dir = blockIdx.y;
-    const unsigned a_ref = (unsigned)__cvta_generic_to_shared(T.s_ref);
-    const unsigned a_tw = (unsigned)__cvta_generic_to_shared(T.s_tw);
-    const unsigned a_sb = (unsigned)__cvta_generic_to_shared(T.s_sb);
-    Offs<M> off;                            // byte offsets of the lane's patch words
-    unsigned vmask;                         // bit m: word lane + 32 m is a real patch word
-    patch_walk<M>(lane, G.wprp, T.nw, G.sp, off, vmask);
+__device__ __forceinline__ void pp_bar_producers() {
+    asm volatile("bar.sync 1, %0;\n" ::"n"(32 * PP_PROD) : "memory");
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+// wait for phase `parity` of an mbarrier, giving up after PP_WAIT_CYCLES
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > PP_WAIT_CYCLES) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ int floor_div(int a, int b) {
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
 
-    for (int a = T.warp; a < PT_NACT; a += 8) {
-        const int s = T.s_seed[a];
-        if (s < 0) continue;
-        const int j = T.j0 + a / (PT_TW / 2);
-        const int i = T.i0 + 2 * (a % (PT_TW / 2)) + ((j + mc.colour) & 1);
-        const int px = mc.c + sig * i, py = mc.c + sig * j;
-        const uint8_t f0 = T.s_f[a];
-        bool have = f0 & F_VALID;
-        int32_t bu = T.s_u[a];
-        unsigned long long bc = have ? T.s_cost[a] : INF;
-        const int32_t u_in = bu;
-        const bool have_in = have;
-        const unsigned long long sa = T.s_sa[a];
+// Column span of a staged region: shared words [0, nwords) of every row; the
+// in-image, 16-byte aligned part [jb, je) goes by one bulk copy per row.
+struct Span { int gw0, nwords, jb, je; };
+__device__ __forceinline__ Span pp_span(int x0w, int sh, int wwords, int iw_words) {
+    Span s;
+    s.gw0 = x0w - sh;                                   // a multiple of 4
+    s.nwords = (sh + wwords + 3) & ~3;
+    const int lo = max(0, -s.gw0), hi = min(s.nwords, iw_words - s.gw0);
+    s.jb = min(lo, s.nwords);
+    s.je = hi > s.jb ? s.jb + ((hi - s.jb) & ~3) : s.jb;
+    return s;
+}
 
-        int b[M];
-        bool loaded = false;
-        unsigned n_eval = 0, n_glob = 0;
-        auto score = [&](int qx, int qy) -> unsigned long long {
-            if (!loaded) {
-                const unsigned rbase =
-                    a_ref + 4u * (unsigned)(sig * (j - T.j0) * G.sp + (mc.c + sig * i - h - T.rx0) * WPP);
-#pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    b[m] = lds32(rbase + off.at(m));
-                    // words past the patch read a valid shared word; zero their weight
-                    if (!EXACT || m == M - 1) b[m] &= (int)(0u - ((vmask >> m) & 1u));
-                }
-                loaded = true;
-            }
-            ++n_eval;
-            return tile_cost<NCH, M>(b, off, D, G, a_tw, a_sb, T.use_win, T.wx0, T.wy0, sa, qx, qy,
-                                     lane, n_glob);
-        };
-
-        // one loop over the candidate sequence (a single inlined cost site):
-        // c = 0, 1: propagated matches (Eq. 4); c >= 2: random search (Eq. 5)
-        // around the match held after propagation
-        int ux0 = 0, uy0 = 0;
-        uint4 r = T.s_rnd[a];
-        const int g = mc.rs_grid;             // PGM-C3/G3: level-0 search on a grid only
-        const int K = (B.level == 0 && g > 0 && !(px % g == g / 2 && py % g == g / 2)) ? 0 : mc.K;
-#pragma unroll 1
-        for (int c = 0; c < 2 + K; ++c) {
-            int32_t cu;
-            int qx, qy;
-            if (c < 2) {
-                cu = T.s_nb[a][c];
-                if (cu == NO_CAND || (have && cu == bu)) continue;
-                qx = px + lo16((uint32_t)cu);
-                qy = py + hi16((uint32_t)cu);
-            } else {
-                if (!have) break;
-                const int k = c - 2;
-                if (k == 0) { ux0 = lo16((uint32_t)bu); uy0 = hi16((uint32_t)bu); }
-                if (k > 0 && (k & 1) == 0)
-                    r = philox(make_uint4((uint32_t)s,
-                                          ((uint32_t)B.visit << 16) | ((uint32_t)dir << 15) | (uint32_t)mc.t,
-                                          ((uint32_t)B.level << 16) | (uint32_t)(k >> 1),
-                                          B.stream_id[pair]),
-                               mc.key0, mc.key1);
-                const uint32_t rx = (k & 1) ? r.z : r.x, ry = (k & 1) ? r.w : r.y;
-                const int dx = rs_off(rx, k, mc.rs_W, mc.rs_mode), dy = rs_off(ry, k, mc.rs_W, mc.rs_mode);
-                if (dx == 0 && dy == 0) continue;
-                qx = px + ux0 + dx;                 // tested before packing into 16 bits
-                qy = py + uy0 + dy;
-                cu = pack_u(ux0 + dx, uy0 + dy);
-            }
-            if (!inside(D, qx, qy)) continue;
-            const unsigned long long cst = score(qx, qy);
-            if (cst < bc) { bc = cst; bu = cu; have = true; }
-        }
-        if (lane == 0) {
-            if (n_eval) atomicAdd(B.evals[pair] + dir, (unsigned long long)n_eval);
-            if (n_glob) atomicAdd(B.evals[pair] + 6 + dir, (unsigned long long)n_glob);
-            if (have && (bu != u_in || !have_in)) {
-                D.u[s] = bu;
-                D.cost[s] = bc;
-                D.flags[s] = f0 | F_VALID;
+// Lane `lane` of one warp stages rows lane, lane + 32, ... of a region
+// (row r from image row clamp(y0 + r)); the warp's bulk bytes were announced
+// on `bar` by the caller.  Words outside the bulk span: 4-byte copies with the
+// pixel clamped (the border replicated).
+template <int WPP>
+__device__ __forceinline__ void pp_stage_rows(unsigned dst, int sp, const uint32_t* src, int pw,
+                                              int iw, int ih, int y0, int rows, const Span& s,
+                                              unsigned bar, int lane) {
+    const unsigned bulk = (unsigned)(s.je - s.jb) * 4u;
+    for (int r = lane; r < rows; r += 32) {
+        const uint32_t* srow = src + (size_t)clampi(y0 + r, 0, ih - 1) * pw;
+        const unsigned drow = dst + 4u * (unsigned)(r * sp);
+        if (bulk) bulk_g2s(drow + 4u * (unsigned)s.jb, srow + s.gw0 + s.jb, bulk, bar);
+        for (int half = 0; half < 2; ++half) {          // the words left and right of it
+            const int j1 = half ? s.nwords : s.jb;
+            for (int j = half ? s.je : 0; j < j1; ++j) {
+                const int gw = s.gw0 + j, p = floor_div(gw, WPP), wi = gw - p * WPP;
+                const uint32_t* s4 = srow + (size_t)clampi(p, 0, iw - 1) * WPP + wi;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n"
+                             ::"r"(drow + 4u * (unsigned)j), "l"(s4) : "memory");
             }
         }
     }
 }
 
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+// Producer warps pw = 0, 1: prepare flattened tile t in the buffer at shared
+// address `buf`; its bulk copies complete on `bar` (two arrivals: pw 0 after
+// announcing the window rows, pw 1 after announcing the reference rows and
+// the window sums).
 template <int NCH>
-__global__ void __launch_bounds__(256, 3)
-k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
+__device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& mc,
+                                           const PtSched& S, int t, unsigned buf, SeedRec* rec,
+                                           TileHdr* hdr, int* next, const PpGeom* geom,
+                                           unsigned bar, int pw, int lane) {
     constexpr int WPP = NCH / 2;
-    extern __shared__ __align__(16) uint32_t sm[];
-    __shared__ int s_seed[PT_NACT];         // seed index, -1 if none
-    __shared__ int s_u[PT_NACT];            // current displacement
-    __shared__ int s_nb[PT_NACT][2];        // propagated displacement, or the sentinel
-    __shared__ unsigned char s_f[PT_NACT];  // flags
-    __shared__ unsigned long long s_cost[PT_NACT], s_sa[PT_NACT];
-    __shared__ uint4 s_rnd[PT_NACT];        // Philox block 0 of the seed (random search)
-    __shared__ int s_med[2];
-
-    const int pair = blockIdx.z, dir = blockIdx.y;
+    int lo = 0, hi = S.nk - 1;                   // (pair, dir) slot holding tile t:
+    while (lo < hi) {                            // the last k with cum[k] <= t
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.cum[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int k = lo, pair = k >> 1, dir = k & 1;
     const DirLvl& D = B.d[pair][dir];
-    const int tiles_x = (D.nx + PT_TW - 1) / PT_TW, tiles_y = (D.ny + PT_TH - 1) / PT_TH;
-    if ((int)blockIdx.x >= tiles_x * tiles_y) return;
-    const int i0 = ((int)blockIdx.x % tiles_x) * PT_TW, j0 = ((int)blockIdx.x / tiles_x) * PT_TH;
-    const int P = D.P, h = P / 2;
-    const int sig = mc.sigma;
-    const PtGeom G = pt_geom(NCH, P, sig, mc.rs_W, mc.slack);
-    const int nw = P * G.wprp;
-    uint32_t* s_ref = sm;
-    uint32_t* s_tw = sm + G.ref_h * G.sp;
-    const int t4 = mc.t & 3;
-    const int sx = (t4 == 0 || t4 == 3) ? 1 : -1, sy = (t4 == 0 || t4 == 2) ? 1 : -1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    // ---- C1: start staging the reference region (independent of the seeds)
+    const int tiles_x = (D.nx + PT_TW - 1) / PT_TW, tt = t - S.cum[k];
+    const int i0 = (tt % tiles_x) * PT_TW, j0 = (tt / tiles_x) * PT_TH;
+    const PpGeom G = geom[dir];
+    const int P = D.P, h = P / 2, sig = mc.sigma;
     const int rx0 = mc.c + sig * i0 - h, ry0 = mc.c + sig * j0 - h;
-    stage<WPP>(s_ref, G.sp, D.ref_split, D.ref_pitch >> 1, D.rw, D.rh, rx0, ry0, G.ref_w, G.ref_h);
+    const int shr = ((rx0 * WPP) % 4 + 4) % 4;
+    fence_proxy_async();                         // earlier reads of this buffer come first
 
-    // ---- A: the active seeds (warp 0, one lane per seed); their first
-    // Philox block is drawn by warp 1 meanwhile
-    if (warp == 1 && mc.K > 0) {
+    if (pw == 1) {
+        // the reference region does not depend on the seeds
+        const Span sr = pp_span(rx0 * WPP, shr, G.ref_w * WPP, D.rw * WPP);
+        if (lane == 0 && sr.je > sr.jb)
+            mbar_expect_tx(bar, (unsigned)(sr.je - sr.jb) * 4u * (unsigned)G.ref_h);
+        __syncwarp();
+        pp_stage_rows<WPP>(buf, G.spr, D.ref_split, D.ref_pitch >> 1, D.rw, D.rh, ry0, G.ref_h, sr,
+                           bar, lane);
+    } else {
+        const int t4 = mc.t & 3;
+        const int sx = (t4 == 0 || t4 == 3) ? 1 : -1, sy = (t4 == 0 || t4 == 2) ? 1 : -1;
         const int a = lane, j = j0 + a / (PT_TW / 2);
         const int i = i0 + 2 * (a % (PT_TW / 2)) + ((j + mc.colour) & 1);
-        if (i < D.nx && j < D.ny)
-            s_rnd[a] = philox(make_uint4((uint32_t)(j * D.nx + i),
-                                         ((uint32_t)B.visit << 16) | ((uint32_t)dir << 15) | (uint32_t)mc.t,
-                                         ((uint32_t)B.level << 16), B.stream_id[pair]),
-                              mc.key0, mc.key1);
-    }
-    if (warp == 0) {
-        const int a = lane, r = a / (PT_TW / 2), k = a % (PT_TW / 2);
-        const int j = j0 + r, i = i0 + 2 * k + ((j + mc.colour) & 1);
-        int s = -1, u = 0, f = 0;
+        SeedRec R;
+        R.s = -1; R.px = 0; R.py = 0; R.f = 0; R.u = 0; R.nb0 = NO_CAND; R.nb1 = NO_CAND; R.K = 0;
+        R.r0 = 0; R.r1 = 0; R.pad0 = 0; R.pad1 = 0; R.cost = INF; R.sa = 0;
         if (i < D.nx && j < D.ny) {
-            s = j * D.nx + i;
+            const int s = j * D.nx + i;
             const int ni = i - sx, nj = j - sy;
             const bool okx = ni >= 0 && ni < D.nx, oky = nj >= 0 && nj < D.ny;
             const int sn0 = okx ? j * D.nx + ni : s, sn1 = oky ? nj * D.nx + i : s;
-            // independent loads, issued together
-            f = D.flags[s];
-            u = D.u[s];
-            const unsigned long long cst = D.cost[s], sa2 = D.sa2[s];
-            const int f0 = D.flags[sn0], f1 = D.flags[sn1];
-            const int u0 = D.u[sn0], u1 = D.u[sn1];
-            s_cost[a] = cst;
-            s_sa[a] = sa2;
-            s_nb[a][0] = (okx && (f0 & F_VALID)) ? u0 : NO_CAND;
-            s_nb[a][1] = (oky && (f1 & F_VALID)) ? u1 : NO_CAND;
+            const int f = D.flags[s], u = D.u[s];
+            const unsigned long long cst = D.cost[s], sa = D.sa2[s];
+            const int f0 = D.flags[sn0], f1 = D.flags[sn1], u0 = D.u[sn0], u1 = D.u[sn1];
+            const int px = mc.c + sig * i, py = mc.c + sig * j;
+            const bool have = f & F_VALID;
+            const int c0 = (okx && (f0 & F_VALID)) ? u0 : NO_CAND;
+            const int c1 = (oky && (f1 & F_VALID)) ? u1 : NO_CAND;
+            const bool ok0 = c0 != NO_CAND && !(have && c0 == u) &&
+                             inside(D, px + lo16((uint32_t)c0), py + hi16((uint32_t)c0));
+            // a repeat of c0 scores the same and cannot be strictly better
+            const bool ok1 = c1 != NO_CAND && c1 != c0 && !(have && c1 == u) &&
+                             inside(D, px + lo16((uint32_t)c1), py + hi16((uint32_t)c1));
+            R.s = s; R.px = px; R.py = py; R.f = f; R.u = u;
+            R.nb0 = ok0 ? c0 : NO_CAND;
+            R.nb1 = ok1 ? c1 : NO_CAND;
+            R.cost = cst; R.sa = sa;
+            const int g = mc.rs_grid;             // PGM-C3/G3: level-0 search on a grid only
+            R.K = (B.level == 0 && g > 0 && !(px % g == g / 2 && py % g == g / 2)) ? 0 : mc.K;
+            if (R.K > 0) {
+                const uint4 r = philox(
+                    make_uint4((uint32_t)s,
+                               ((uint32_t)B.visit << 16) | ((uint32_t)dir << 15) | (uint32_t)mc.t,
+                               (uint32_t)B.level << 16, B.stream_id[pair]),
+                    mc.key0, mc.key1);
+                R.r0 = pack_u(rs_off(r.x, 0, mc.rs_W, mc.rs_mode), rs_off(r.y, 0, mc.rs_W, mc.rs_mode));
+                R.r1 = pack_u(rs_off(r.z, 1, mc.rs_W, mc.rs_mode), rs_off(r.w, 1, mc.rs_W, mc.rs_mode));
+            }
         }
-        s_seed[a] = s;
-        s_u[a] = u;
-        s_f[a] = (unsigned char)f;
-        // median of the valid current displacements: rank by (value, lane)
-        const bool v = s >= 0 && (f & F_VALID);
+        rec[a] = R;
+        // window centre: median of the valid current matches, ranked by (value, lane)
+        const bool v = R.s >= 0 && (R.f & F_VALID);
         const unsigned vm = __ballot_sync(FULL, v);
         const int nv = __popc(vm);
-        const int ux = lo16((uint32_t)u), uy = hi16((uint32_t)u);
+        const int ux = lo16((uint32_t)R.u), uy = hi16((uint32_t)R.u);
         int rx = 0, ry = 0;
         for (int o = 0; o < 32; ++o) {
             const int ox = __shfl_sync(FULL, ux, o), oy = __shfl_sync(FULL, uy, o);
@@ -397,63 +482,311 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
                 ry += oy < uy || (oy == uy && o < lane);
             }
         }
-        if (lane == 0) { s_med[0] = INT_MIN; s_med[1] = INT_MIN; }
-        __syncwarp();
-        if (v && rx == nv / 2) s_med[0] = ux;
-        if (v && ry == nv / 2) s_med[1] = uy;
+        const int rho = max(1, mc.rs_W);
+        const unsigned mx = __ballot_sync(FULL, v && rx == nv / 2);
+        const unsigned my = __ballot_sync(FULL, v && ry == nv / 2);
+        const int medx = __shfl_sync(FULL, ux, mx ? __ffs(mx) - 1 : 0);
+        const int medy = __shfl_sync(FULL, uy, my ? __ffs(my) - 1 : 0);
+        if (lane == 0) {
+            TileHdr H;
+            H.pair = pair; H.dir = dir; H.i0 = i0; H.j0 = j0; H.rx0 = rx0;
+            H.use_win = nv > 0;
+            H.wx0 = nv > 0 ? mc.c + sig * i0 - h + medx - rho - mc.slack : 0;
+            H.wy0 = nv > 0 ? mc.c + sig * j0 - h + medy - rho - mc.slack : 0;
+            H.shr = shr;
+            H.shw = ((H.wx0 * WPP) % 4 + 4) % 4;
+            H.shs = (H.wx0 + h) & 1;
+            H.pad = 0;
+            *hdr = H;
+            *next = 0;
+        }
     }
-    __syncthreads();
-
-    // ---- B: window around the median match (unclamped pixel coordinates)
-    const int rho = max(1, mc.rs_W);
-    const bool use_win = s_med[0] != INT_MIN;
-    const int wx0 = use_win ? mc.c + sig * i0 - h + s_med[0] - rho - mc.slack : 0;
-    const int wy0 = use_win ? mc.c + sig * j0 - h + s_med[1] - rho - mc.slack : 0;
-
-    // ---- C2: stage the window and its sums of |b|^2
-    unsigned long long* s_sb = reinterpret_cast<unsigned long long*>(
-        sm + ((G.sp * (G.ref_h + G.win_h) + 1) & ~1));
-    if (use_win) {
-        stage<WPP>(s_tw, G.sp, reinterpret_cast<const uint32_t*>(D.tgt), D.tgt_pitch >> 1, D.tw,
-                   D.th, wx0, wy0, G.win_w, G.win_h);
-        // sum |b|^2 of every centre whose patch lies in the window (centres
-        // outside the image are never scored; their entries are don't-care)
-        const int cx0 = wx0 + h, cy0 = wy0 + h;
-        for (int row = warp; row < G.ch; row += 8) {
-            const unsigned long long* srow = D.sb2 + (size_t)clampi(cy0 + row, 0, D.th - 1) * D.tw;
-            for (int col = lane; col < G.cw; col += 32)
-                cp_async8(s_sb + row * G.cw + col, srow + clampi(cx0 + col, 0, D.tw - 1));
+    pp_bar_producers();                           // the window position is known
+    const TileHdr H = *hdr;
+    const unsigned win = buf + 4u * (unsigned)G.off_win, sbb = buf + 4u * (unsigned)G.off_sb;
+    if (pw == 0) {
+        if (H.use_win) {
+            const Span sw = pp_span(H.wx0 * WPP, H.shw, G.win_w * WPP, D.tw * WPP);
+            if (lane == 0) {
+                if (sw.je > sw.jb) mbar_arrive_tx(bar, (unsigned)(sw.je - sw.jb) * 4u * (unsigned)G.win_h);
+                else mbar_arrive(bar);
+            }
+            __syncwarp();
+            pp_stage_rows<WPP>(win, G.spw, reinterpret_cast<const uint32_t*>(D.tgt),
+                               D.tgt_pitch >> 1, D.tw, D.th, H.wy0, G.win_h, sw, bar, lane);
+        } else if (lane == 0) {
+            mbar_arrive(bar);
+        }
+    } else {
+        // sums |b|^2 of the centres whose patch lies in the window; centres
+        // outside the image are never scored, their entries are don't-care
+        const int cx0 = H.wx0 + h, cy0 = H.wy0 + h;
+        const bool bulk = H.use_win && (D.tw & 1) == 0;
+        unsigned bytes = 0;
+        int c_lo = 0;
+        if (bulk) {
+            const int a0 = cx0 - H.shs;                       // even
+            c_lo = max(a0, 0);
+            const int c_hi = min(a0 + G.cwp, D.tw);
+            bytes = c_hi > c_lo ? (unsigned)(c_hi - c_lo) * 8u : 0u;
+            if (lane == 0) {
+                if (bytes) mbar_arrive_tx(bar, bytes * (unsigned)G.ch);
+                else mbar_arrive(bar);
+            }
+            __syncwarp();
+            if (bytes)
+                for (int r = lane; r < G.ch; r += 32) {
+                    const unsigned long long* srow =
+                        D.sb2 + (size_t)clampi(cy0 + r, 0, D.th - 1) * D.tw;
+                    bulk_g2s(sbb + 8u * (unsigned)(r * G.cwp + (c_lo - a0)), srow + c_lo, bytes, bar);
+                }
+        } else {
+            if (lane == 0) mbar_arrive(bar);
+            if (H.use_win)
+                for (int r = 0; r < G.ch; ++r) {
+                    const unsigned long long* srow =
+                        D.sb2 + (size_t)clampi(cy0 + r, 0, D.th - 1) * D.tw;
+                    for (int col = lane; col < G.cw; col += 32)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n"
+                                     ::"r"(sbb + 8u * (unsigned)(r * G.cwp + H.shs + col)),
+                                     "l"(srow + clampi(cx0 + col, 0, D.tw - 1)) : "memory");
+                }
         }
     }
     cp_async_wait_all();
-    __syncthreads();
+}
 
-    // ---- D: one warp per active seed, specialised on the exact number of
-    // 32-word groups of this direction's patch
-    TileCtx T{s_ref, s_tw, s_sb, s_seed, s_u, s_nb, s_f, s_cost, s_sa, s_rnd,
-              i0, j0, rx0, wx0, wy0, use_win, sig, h, P, nw, sx, sy, lane, warp};
-    const int groups = (nw + 31) / 32;
-    // exact group counts of the common patch sides (6 ch: P 8, 11, 15, 16;
-    // 2 ch: P 8, 11, 15/16) need only the last group masked
-#define PGM_SEEDS(MM, EX) seeds<NCH, MM, EX>(B, mc, D, G, T)
-    if (NCH == 6) {
-        if (groups == 6) PGM_SEEDS(6, true);
-        else if (groups == 12) PGM_SEEDS(12, true);
-        else if (groups == 22) PGM_SEEDS(22, true);
-        else if (groups == 24) PGM_SEEDS(24, true);
-        else if (groups <= 4) PGM_SEEDS(4, false);
-        else if (groups <= 8) PGM_SEEDS(8, false);
-        else if (groups <= 16) PGM_SEEDS(16, false);
-        else PGM_SEEDS(24, false);
+// Cost of target centre (qx, qy) for the reference words b (lane offsets
+// `off` into the window): from the staged window when the patch lies inside
+// it, else from global memory with the border replicated.
+template <int NCH, int M>
+__device__ __forceinline__ unsigned long long pp_cost(const int (&b)[M], const Offs<M>& off,
+                                                      const DirLvl& D, const PpGeom& G,
+                                                      const TileHdr& H, unsigned a_tw,
+                                                      unsigned a_sb, unsigned long long sa, int qx,
+                                                      int qy, int lane, unsigned& n_glob) {
+    constexpr int WPP = NCH / 2;
+    const int P = D.P, h = P / 2;
+    const int x0 = qx - h - H.wx0, y0 = qy - h - H.wy0;
+    unsigned long long sb;
+    int sl, sh;
+    if (H.use_win && x0 >= 0 && y0 >= 0 && x0 + P <= G.win_w && y0 + P <= G.win_h) {
+        sb = lds64(a_sb + 8u * (unsigned)(y0 * G.cwp + H.shs + x0));
+        const unsigned base = a_tw + 4u * (unsigned)(y0 * G.spw + H.shw + x0 * WPP);
+        int l0 = 0, l1 = 0, l2 = 0, l3 = 0, h0 = 0, h1 = 0, h2 = 0, h3 = 0;   // four chains each
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int v = lds32(base + off.at(m));
+            switch (m & 3) {
+                case 0: l0 = __dp2a_lo(v, b[m], l0); h0 = __dp2a_hi(v, b[m], h0); break;
+                case 1: l1 = __dp2a_lo(v, b[m], l1); h1 = __dp2a_hi(v, b[m], h1); break;
+                case 2: l2 = __dp2a_lo(v, b[m], l2); h2 = __dp2a_hi(v, b[m], h2); break;
+                default: l3 = __dp2a_lo(v, b[m], l3); h3 = __dp2a_hi(v, b[m], h3); break;
+            }
+        }
+        sl = (l0 + l1) + (l2 + l3);
+        sh = (h0 + h1) + (h2 + h3);
     } else {
-        if (groups == 2) PGM_SEEDS(2, true);
-        else if (groups == 4) PGM_SEEDS(4, true);
-        else if (groups == 8) PGM_SEEDS(8, true);
-        else if (groups <= 2) PGM_SEEDS(2, false);
-        else if (groups <= 4) PGM_SEEDS(4, false);
-        else PGM_SEEDS(8, false);
+        sb = D.sb2[(size_t)qy * D.tw + qx];
+        const int pitchw = D.tgt_pitch >> 1;
+        const uint32_t* t32 = reinterpret_cast<const uint32_t*>(D.tgt);
+        sl = 0;
+        sh = 0;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int o = (int)(off.at(m) >> 2), row = o / G.spw, col = o - row * G.spw;
+            const int pix = col / WPP, wi = col - pix * WPP;
+            const int x = clampi(qx - h + pix, 0, D.tw - 1), y = clampi(qy - h + row, 0, D.th - 1);
+            const int v = (int)__ldg(t32 + (size_t)y * pitchw + (size_t)x * WPP + wi);
+            sl = __dp2a_lo(v, b[m], sl);
+            sh = __dp2a_hi(v, b[m], sh);
+        }
+        ++n_glob;
     }
-#undef PGM_SEEDS
+    sl = __reduce_add_sync(FULL, sl);
+    sh = __reduce_add_sync(FULL, sh);
+    return xcost(sa, sb, (long long)sh * 128 + (long long)sl);
+}
+
+// Consumer warps: the active seeds of the tile in the buffer at `buf`, taken
+// one at a time from a shared counter.  M = 32-word groups of the patch; NA >=
+// 0: the layout has exactly NA A groups followed by M - NA B groups; NA < 0:
+// M is an upper bound and the masks come from the geometry at run time.
+template <int NCH, int M, int NA>
+__device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& mc,
+                                           const TileHdr& H, const PpGeom& G, const SeedRec* rec,
+                                           unsigned buf, const unsigned short* offr,
+                                           const unsigned short* offw, int* next, int lane) {
+    constexpr int WPP = NCH / 2;
+    const DirLvl& D = B.d[H.pair][H.dir];
+    const int P = D.P, h = P / 2, sig = mc.sigma;
+    const unsigned a_ref = buf, a_tw = buf + 4u * (unsigned)G.off_win;
+    const unsigned a_sb = buf + 4u * (unsigned)G.off_sb;
+    Offs<M> off;                            // byte offsets of the lane's patch words in the window
+#pragma unroll
+    for (int m = 0; m < M; ++m) off.p[m] = offw[m * 32 + lane];
+    // zero references: B-group lanes without a word, and past the last row
+    const bool has_b = G.S == 0 || lane % G.S < G.wl;
+    const int mask_b = has_b ? -1 : 0;
+    const int mask_last = (has_b && (G.nB == 0 || (G.nB - 1) * G.g + lane / G.S < P)) ? -1 : 0;
+    unsigned n_eval = 0, n_glob = 0;
+    for (;;) {
+        int a = 0;
+        if (lane == 0) a = atomicAdd(next, 1);
+        a = __shfl_sync(FULL, a, 0);
+        if (a >= PT_NACT) break;
+        const SeedRec R = rec[a];
+        if (R.s < 0) continue;
+        bool have = R.f & F_VALID;
+        if (!have && R.nb0 == NO_CAND && R.nb1 == NO_CAND) continue;   // nothing to score
+        int32_t bu = R.u;
+        unsigned long long bc = have ? R.cost : INF;
+        int b[M];
+        const unsigned rbase = a_ref + 4u * (unsigned)((a / (PT_TW / 2)) * sig * G.spr + H.shr +
+                                                       (R.px - h - H.rx0) * WPP);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            b[m] = lds32(rbase + offr[m * 32 + lane]);
+            if (NA >= 0) {
+                if (m >= NA) b[m] &= (m == M - 1) ? mask_last : mask_b;
+            } else {
+                b[m] &= m < G.nA ? -1 : (m < G.M - 1 ? mask_b : (m == G.M - 1 ? mask_last : 0));
+            }
+        }
+        // one loop over the candidate sequence (a single inlined cost site):
+        // c = 0, 1: propagated matches (Eq. 4); c >= 2: random search (Eq. 5)
+        // around the match held after propagation
+        int ux0 = 0, uy0 = 0;
+        uint4 r = make_uint4(0, 0, 0, 0);
+#pragma unroll 1
+        for (int c = 0; c < 2 + R.K; ++c) {
+            int32_t cu;
+            int qx, qy;
+            if (c < 2) {
+                cu = c ? R.nb1 : R.nb0;
+                if (cu == NO_CAND) continue;
+                qx = R.px + lo16((uint32_t)cu);
+                qy = R.py + hi16((uint32_t)cu);
+            } else {
+                if (!have) break;
+                const int k = c - 2;
+                if (k == 0) { ux0 = lo16((uint32_t)bu); uy0 = hi16((uint32_t)bu); }
+                int dx, dy;
+                if (k < 2) {
+                    const uint32_t o = (uint32_t)(k ? R.r1 : R.r0);
+                    dx = lo16(o);
+                    dy = hi16(o);
+                } else {
+                    if ((k & 1) == 0)
+                        r = philox(make_uint4((uint32_t)R.s,
+                                              ((uint32_t)B.visit << 16) | ((uint32_t)H.dir << 15) |
+                                                  (uint32_t)mc.t,
+                                              ((uint32_t)B.level << 16) | (uint32_t)(k >> 1),
+                                              B.stream_id[H.pair]),
+                                   mc.key0, mc.key1);
+                    dx = rs_off((k & 1) ? r.z : r.x, k, mc.rs_W, mc.rs_mode);
+                    dy = rs_off((k & 1) ? r.w : r.y, k, mc.rs_W, mc.rs_mode);
+                }
+                if (dx == 0 && dy == 0) continue;
+                qx = R.px + ux0 + dx;               // tested before packing into 16 bits
+                qy = R.py + uy0 + dy;
+                if (!inside(D, qx, qy)) continue;
+                cu = pack_u(ux0 + dx, uy0 + dy);
+            }
+            ++n_eval;
+            const unsigned long long cst =
+                pp_cost<NCH, M>(b, off, D, G, H, a_tw, a_sb, R.sa, qx, qy, lane, n_glob);
+            if (cst < bc) { bc = cst; bu = cu; have = true; }
+        }
+        if (lane == 0 && have && (bu != R.u || !(R.f & F_VALID))) {
+            D.u[R.s] = bu;
+            D.cost[R.s] = bc;
+            D.flags[R.s] = (uint8_t)(R.f | F_VALID);
+        }
+    }
+    if (lane == 0) {
+        if (n_eval) atomicAdd(B.evals[H.pair] + H.dir, (unsigned long long)n_eval);
+        if (n_glob) atomicAdd(B.evals[H.pair] + 6 + H.dir, (unsigned long long)n_glob);
+    }
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(PP_THREADS, 2)
+k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_constant__ PtSched S,
+       const int buf_words) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ SeedRec s_rec[2][PT_NACT];
+    __shared__ TileHdr s_hdr[2];
+    __shared__ PpGeom s_geom[2];
+    __shared__ unsigned short s_offr[2][PP_MMAX * 32], s_offw[2][PP_MMAX * 32];
+    __shared__ __align__(8) unsigned long long s_bar[2];
+    __shared__ int s_next[2], s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned a_sm = (unsigned)__cvta_generic_to_shared(sm);
+    const unsigned bar0 = (unsigned)__cvta_generic_to_shared(&s_bar[0]);
+    if (threadIdx.x < 2)
+        s_geom[threadIdx.x] = pp_geom(NCH, B.d[0][threadIdx.x].P, mc.sigma, mc.rs_W, mc.slack);
+    if (threadIdx.x == 0) {
+        mbar_init(bar0, 2);
+        mbar_init(bar0 + 8, 2);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * PP_MMAX * 32; e += PP_THREADS) {
+        const int d = e / (PP_MMAX * 32), m = (e >> 5) % PP_MMAX, l = e & 31;
+        const PpGeom& G = s_geom[d];
+        int row, col;
+        bool valid;
+        pp_word(G, B.d[0][d].P, m, l, &row, &col, &valid);
+        s_offr[d][m * 32 + l] = (unsigned short)(4 * (row * G.spr + col));
+        s_offw[d][m * 32 + l] = (unsigned short)(4 * (row * G.spw + col));
+    }
+    int t = blockIdx.x;                          // the host launches at most S.total CTAs
+    if (warp >= PP_CONS)
+        pp_produce<NCH>(B, mc, S, t, a_sm, s_rec[0], &s_hdr[0], &s_next[0], s_geom, bar0,
+                        warp - PP_CONS, lane);
+    __syncthreads();
+    unsigned pend_bar = 0, pend_par = 0;         // producers: copies not yet waited for
+    for (int n = 0; t < S.total; ++n, t += gridDim.x) {
+        const int cur = n & 1;
+        if (warp >= PP_CONS) {
+            pend_bar = 0;
+            if (t + (int)gridDim.x < S.total) {
+                pend_bar = bar0 + 8u * (unsigned)(cur ^ 1);
+                pend_par = (unsigned)((n + 1) >> 1) & 1u;
+                pp_produce<NCH>(B, mc, S, t + gridDim.x, a_sm + 4u * (unsigned)((cur ^ 1) * buf_words),
+                                s_rec[cur ^ 1], &s_hdr[cur ^ 1], &s_next[cur ^ 1], s_geom, pend_bar,
+                                warp - PP_CONS, lane);
+            }
+        } else {
+            const TileHdr H = s_hdr[cur];
+            if (!__all_sync(FULL, mbar_wait(bar0 + 8u * (unsigned)cur, (unsigned)(n >> 1) & 1u))) {
+                if (lane == 0) {
+                    atomicOr(B.err[H.pair], (unsigned)PGM_ERR_TIMEOUT);
+                    s_abort = 1;
+                }
+            } else {
+                const PpGeom G = s_geom[H.dir];
+                const unsigned buf = a_sm + 4u * (unsigned)(cur * buf_words);
+#define PGM_CONSUME(MM, NA) \
+    pp_consume<NCH, MM, NA>(B, mc, H, G, s_rec[cur], buf, s_offr[H.dir], s_offw[H.dir], &s_next[cur], lane)
+                // exact layouts of the common patch sides (6 ch: P 15, 11, 16);
+                // other sides take an upper bound with run-time masks
+                if (NCH == 6 && G.M == 23 && G.nA == 15) PGM_CONSUME(23, 15);
+                else if (NCH == 6 && G.M == 12 && G.nA == 11) PGM_CONSUME(12, 11);
+                else if (NCH == 6 && G.M == 24 && G.nA == 16) PGM_CONSUME(24, 16);
+                else if (G.M <= 8) PGM_CONSUME(8, -1);
+                else if (G.M <= 16) PGM_CONSUME(16, -1);
+                else PGM_CONSUME(24, -1);
+#undef PGM_CONSUME
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+    }
+    // after a timed-out wait: let this thread's bulk copies land before leaving
+    if (pend_bar && s_abort) (void)mbar_wait(pend_bar, pend_par);
 }
 
 // ------------------------------------------------------------------
@@ -529,7 +862,8 @@ k_cost_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     unsigned long long* s_sb = reinterpret_cast<unsigned long long*>(
         sm + ((G.sp * (G.ref_h + G.win_h) + 1) & ~1));
     const int rx0 = mc.c + sig * i0 - h, ry0 = mc.c + sig * j0 - h;
-    stage<WPP>(s_ref, G.sp, D.ref_split, D.ref_pitch >> 1, D.rw, D.rh, rx0, ry0, G.ref_w, G.ref_h);
+    stage<WPP>(s_ref, G.sp, D.ref_split, D.ref_pitch >> 1, D.rw, D.rh, rx0, ry0, G.ref_w, G.ref_h,
+               threadIdx.x >> 5, 8);
 
     bool valid = false;
     if (threadIdx.x < PC_N) {
@@ -573,7 +907,7 @@ k_cost_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     const int wy0 = use_win ? mc.c + sig * j0 - h + s_med[1] - rho - mc.slack : 0;
     if (use_win) {
         stage<WPP>(s_tw, G.sp, reinterpret_cast<const uint32_t*>(D.tgt), D.tgt_pitch >> 1, D.tw,
-                   D.th, wx0, wy0, G.win_w, G.win_h);
+                   D.th, wx0, wy0, G.win_w, G.win_h, threadIdx.x >> 5, 8);
         const int cx0 = wx0 + h, cy0 = wy0 + h, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         for (int row = warp; row < G.ch; row += 8) {
             const unsigned long long* srow = D.sb2 + (size_t)clampi(cy0 + row, 0, D.th - 1) * D.tw;
@@ -620,16 +954,34 @@ pgm_status launch_c(const LvlBatch& B, const MatchConst& mc, int tiles, int smem
     return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
 }
 
+// Grid of the persistent search kernel: as many CTAs as fit on the device at
+// once (the occupancy query is cached per device and shared-memory size),
+// never more than there are tiles.
 template <int NCH>
-pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, int tiles, int smem_bytes,
+pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, const PtSched& S, int buf_words,
                     cudaStream_t st) {
+    const int smem = 2 * buf_words * 4;
     static int configured = 0;                 // opt-in above 48 KB once per instantiation
-    if (configured < smem_bytes) {
-        if (cudaFuncSetAttribute(k_pm_t<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem_bytes) != cudaSuccess) return PGM_ERR_CUDA;
-        configured = smem_bytes;
+    static int cache_dev = -1, cache_smem = -1, cache_cap = 0;
+    if (configured < smem) {
+        if (cudaFuncSetAttribute(k_pm_t<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess) return PGM_ERR_CUDA;
+        configured = smem;
     }
-    k_pm_t<NCH><<<dim3(tiles, 2, B.n), 256, smem_bytes, st>>>(B, mc);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PGM_ERR_CUDA;
+    if (dev != cache_dev || smem != cache_smem) {
+        int sms = 0, per = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pm_t<NCH>, PP_THREADS, smem) !=
+                cudaSuccess || per < 1)
+            return PGM_ERR_CUDA;
+        cache_cap = sms * per;
+        cache_dev = dev;
+        cache_smem = smem;
+    }
+    const int grid = S.total < cache_cap ? S.total : cache_cap;
+    k_pm_t<NCH><<<grid, PP_THREADS, smem, st>>>(B, mc, S, buf_words);
     return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
 }
 
@@ -646,30 +998,34 @@ static bool pt_offsets_fit(const LvlBatch& B, int nch, const MatchConst& mc) {
     return true;
 }
 
-// *handled = false when the staged tile would not fit in shared memory; the
-// caller then uses the per-seed kernel.
+// *handled = false when two tile buffers would not fit in shared memory or a
+// staged row could not move by 16-byte bulk copies; the caller then uses the
+// per-seed kernel.
 pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
                           bool* handled, cudaStream_t st) {
     (void)maxP;
     *handled = false;
-    int tiles = 0, words = 0, maxw = 0;
-    for (int k = 0; k < B.n; ++k)
-        for (int d = 0; d < 2; ++d) {
-            const DirLvl& D = B.d[k][d];
-            const int t = ((D.nx + PT_TW - 1) / PT_TW) * ((D.ny + PT_TH - 1) / PT_TH);
-            if (t > tiles) tiles = t;
-            const PtGeom g = pt_geom(nch, D.P, mc.sigma, mc.rs_W, mc.slack);
-            if (g.words > words) words = g.words;
-            const int nwp = D.P * g.wprp;
-            if (nwp > maxw) maxw = nwp;
-        }
-    const int smem_bytes = words * 4;
-    if (smem_bytes > 160 * 1024 || !pt_offsets_fit(B, nch, mc)) return PGM_OK;
+    PtSched S;
+    S.nk = 2 * B.n;
+    S.total = 0;
+    int words = 0;
+    bool ok = true;
+    for (int k = 0; k < S.nk; ++k) {
+        const DirLvl& D = B.d[k >> 1][k & 1];
+        S.cum[k] = S.total;
+        S.total += ((D.nx + PT_TW - 1) / PT_TW) * ((D.ny + PT_TH - 1) / PT_TH);
+        const PpGeom g = pp_geom(nch, D.P, mc.sigma, mc.rs_W, mc.slack);
+        if (g.words > words) words = g.words;
+        if (g.M > PP_MMAX || 4L * ((long)(D.P - 1) * g.spw + g.wprp) >= 65536L) ok = false;
+        if ((((uintptr_t)D.ref_split | (uintptr_t)D.tgt | (uintptr_t)D.sb2) & 15) != 0 ||
+            (D.ref_pitch * 2) % 16 != 0 || (D.tgt_pitch * 2) % 16 != 0)
+            ok = false;
+    }
+    S.cum[S.nk] = S.total;
+    if (!ok || 2L * words * 4 > 200L * 1024) return PGM_OK;
     *handled = true;
-    if (tiles == 0) return PGM_OK;
-    if ((maxw + 31) / 32 > 24) return PGM_ERR_UNSUPPORTED;
-    return nch == 2 ? launch_t<2>(B, mc, tiles, smem_bytes, st)
-                    : launch_t<6>(B, mc, tiles, smem_bytes, st);
+    if (S.total == 0) return PGM_OK;
+    return nch == 2 ? launch_t<2>(B, mc, S, words, st) : launch_t<6>(B, mc, S, words, st);
 }
 
 pgm_status launch_cost_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
