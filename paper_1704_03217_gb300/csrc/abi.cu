@@ -50,7 +50,10 @@ KScope::KScope(int c, cudaStream_t s, int nl) : cls(c), st(s), n(nl), slot(-1) {
 
 KScope::~KScope() {
     g_launches.fetch_add(n, std::memory_order_relaxed);
-    if (slot >= 0 && slot < (int)g_prof.open.size()) cudaEventRecord(g_prof.open[slot].b, st);
+    if (slot >= 0 && slot < (int)g_prof.open.size()) {
+        g_prof.open[slot].n = n;              // the launcher may have changed the count
+        cudaEventRecord(g_prof.open[slot].b, st);
+    }
 }
 
 pgm_status check_params(const pgm_params* p) {

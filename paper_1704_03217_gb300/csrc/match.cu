@@ -701,7 +701,9 @@ pgm_status launch_pm_phase(const LvlBatch& B, const MatchConst& mc, int nch, int
     dim3 g((max_seeds + 7) / 8, 2, B.n);   // max_seeds: half-row width x rows
     if (mc.norm == PGM_L2SQ) {
         bool handled = false;
-        pgm_status r = launch_pm_tile(B, mc, nch, maxP, &handled, st);
+        int nl = 0;
+        pgm_status r = launch_pm_tile(B, mc, nch, maxP, &nl, &handled, st);
+        if (handled) ks.n = nl;
         if (r != PGM_OK || handled) return r;
         PGM_DISPATCH_X(k_pm_x, g, B, mc);
     }

@@ -162,7 +162,7 @@ pgm_status launch_consist(const LvlBatch& B, const MatchConst& mc, int max_seeds
 pgm_status launch_transfer(const XferBatch& X, int max_seeds, cudaStream_t st);
 pgm_status launch_box(const LvlBatch& B, int nch, int max_pixels, cudaStream_t st);
 // pm_tile.cu: *handled = false when the staged tile would not fit in shared memory
-pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
+pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP, int* nlaunch,
                           bool* handled, cudaStream_t st);
 pgm_status launch_cost_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
                             cudaStream_t st);

@@ -305,9 +305,9 @@ struct __align__(16) SeedRec {      // one active seed of a staged tile
 
 struct TileHdr { int pair, dir, i0, j0, rx0, wx0, wy0, use_win, shr, shw, shs, pad; };
 
-// The flattened tiles of one launch: (pair, dir) slot k = 2 pair + dir owns
-// tiles [cum[k], cum[k + 1]).
-struct PtSched { int nk, total; int cum[2 * MAXB + 1]; };
+// The flattened tiles of one launch (one direction): pair k owns tiles
+// [cum[k], cum[k + 1]).
+struct PtSched { int nk, total, dir, pad; int cum[MAXB + 1]; };
 
 constexpr int NO_CAND = INT_MIN;            // no propagated candidate
 
@@ -401,19 +401,18 @@ __device__ __forceinline__ void mbar_arrive(unsigned bar) {
 template <int NCH>
 __device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& mc,
                                            const PtSched& S, int t, unsigned buf, SeedRec* rec,
-                                           TileHdr* hdr, int* next, const PpGeom* geom,
+                                           TileHdr* hdr, int* next, const PpGeom& G,
                                            unsigned bar, int pw, int lane) {
     constexpr int WPP = NCH / 2;
-    int lo = 0, hi = S.nk - 1;                   // (pair, dir) slot holding tile t:
+    int lo = 0, hi = S.nk - 1;                   // pair holding tile t:
     while (lo < hi) {                            // the last k with cum[k] <= t
         const int mid = (lo + hi + 1) >> 1;
         if (S.cum[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    const int k = lo, pair = k >> 1, dir = k & 1;
+    const int k = lo, pair = k, dir = S.dir;
     const DirLvl& D = B.d[pair][dir];
     const int tiles_x = (D.nx + PT_TW - 1) / PT_TW, tt = t - S.cum[k];
     const int i0 = (tt % tiles_x) * PT_TW, j0 = (tt / tiles_x) * PT_TH;
-    const PpGeom G = geom[dir];
     const int P = D.P, h = P / 2, sig = mc.sigma;
     const int rx0 = mc.c + sig * i0 - h, ry0 = mc.c + sig * j0 - h;
     const int shr = ((rx0 * WPP) % 4 + 4) % 4;
@@ -556,27 +555,40 @@ __device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& 
     cp_async_wait_all();
 }
 
-// Cost of target centre (qx, qy) for the reference words b (lane offsets
-// `off` into the window): from the staged window when the patch lies inside
-// it, else from global memory with the border replicated.
-template <int NCH, int M>
-__device__ __forceinline__ unsigned long long pp_cost(const int (&b)[M], const Offs<M>& off,
+// Group addressing of the consumer.  NA >= 0: groups [0, NA) are A groups
+// of a layout with q = 1 (lane l reads word l of patch row m, at byte offset
+// 4 (m sp + l) from the patch origin), groups [NA, M) take per-lane offsets
+// from the tables; NA < 0: every group takes table offsets.
+template <int M, int NA>
+struct PpLay {
+    static constexpr int A0 = NA >= 0 ? NA : 0;
+    static constexpr int NB = M - A0 > 0 ? M - A0 : 1;
+};
+
+// Cost of target centre (qx, qy) for the reference words b: from the staged
+// window when the patch lies inside it, else from global memory with the
+// border replicated.  SPW > 0: the window pitch as a constant.
+template <int NCH, int M, int NA, int SPW>
+__device__ __forceinline__ unsigned long long pp_cost(const int (&b)[M],
+                                                      const Offs<PpLay<M, NA>::NB>& off,
                                                       const DirLvl& D, const PpGeom& G,
                                                       const TileHdr& H, unsigned a_tw,
                                                       unsigned a_sb, unsigned long long sa, int qx,
                                                       int qy, int lane, unsigned& n_glob) {
-    constexpr int WPP = NCH / 2;
-    const int P = D.P, h = P / 2;
+    constexpr int WPP = NCH / 2, A0 = PpLay<M, NA>::A0;
+    const int P = D.P, h = P / 2, spw = SPW > 0 ? SPW : G.spw;
     const int x0 = qx - h - H.wx0, y0 = qy - h - H.wy0;
     unsigned long long sb;
     int sl, sh;
     if (H.use_win && x0 >= 0 && y0 >= 0 && x0 + P <= G.win_w && y0 + P <= G.win_h) {
         sb = lds64(a_sb + 8u * (unsigned)(y0 * G.cwp + H.shs + x0));
-        const unsigned base = a_tw + 4u * (unsigned)(y0 * G.spw + H.shw + x0 * WPP);
+        const unsigned base = a_tw + 4u * (unsigned)(y0 * spw + H.shw + x0 * WPP);
+        const unsigned basel = base + 4u * (unsigned)lane;
         int l0 = 0, l1 = 0, l2 = 0, l3 = 0, h0 = 0, h1 = 0, h2 = 0, h3 = 0;   // four chains each
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-            const int v = lds32(base + off.at(m));
+            const unsigned addr = m < A0 ? basel + 4u * (unsigned)(m * spw) : base + off.at(m - A0);
+            const int v = lds32(addr);
             switch (m & 3) {
                 case 0: l0 = __dp2a_lo(v, b[m], l0); h0 = __dp2a_hi(v, b[m], h0); break;
                 case 1: l1 = __dp2a_lo(v, b[m], l1); h1 = __dp2a_hi(v, b[m], h1); break;
@@ -594,7 +606,12 @@ __device__ __forceinline__ unsigned long long pp_cost(const int (&b)[M], const O
         sh = 0;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-            const int o = (int)(off.at(m) >> 2), row = o / G.spw, col = o - row * G.spw;
+            int row = m, col = lane;
+            if (m >= A0) {
+                const int o = (int)(off.at(m - A0) >> 2);
+                row = o / spw;
+                col = o - row * spw;
+            }
             const int pix = col / WPP, wi = col - pix * WPP;
             const int x = clampi(qx - h + pix, 0, D.tw - 1), y = clampi(qy - h + row, 0, D.th - 1);
             const int v = (int)__ldg(t32 + (size_t)y * pitchw + (size_t)x * WPP + wi);
@@ -609,22 +626,23 @@ __device__ __forceinline__ unsigned long long pp_cost(const int (&b)[M], const O
 }
 
 // Consumer warps: the active seeds of the tile in the buffer at `buf`, taken
-// one at a time from a shared counter.  M = 32-word groups of the patch; NA >=
-// 0: the layout has exactly NA A groups followed by M - NA B groups; NA < 0:
-// M is an upper bound and the masks come from the geometry at run time.
-template <int NCH, int M, int NA>
+// one at a time from a shared counter.  M = 32-word groups of the patch;
+// NA as for PpLay (NA < 0: M is an upper bound and the masks come from the
+// geometry at run time); SPW, SPR > 0: window / reference pitches as
+// constants.
+template <int NCH, int M, int NA, int SPW, int SPR>
 __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& mc,
                                            const TileHdr& H, const PpGeom& G, const SeedRec* rec,
                                            unsigned buf, const unsigned short* offr,
                                            const unsigned short* offw, int* next, int lane) {
-    constexpr int WPP = NCH / 2;
+    constexpr int WPP = NCH / 2, A0 = PpLay<M, NA>::A0, NB = PpLay<M, NA>::NB;
     const DirLvl& D = B.d[H.pair][H.dir];
-    const int P = D.P, h = P / 2, sig = mc.sigma;
+    const int P = D.P, h = P / 2, sig = mc.sigma, spr = SPR > 0 ? SPR : G.spr;
     const unsigned a_ref = buf, a_tw = buf + 4u * (unsigned)G.off_win;
     const unsigned a_sb = buf + 4u * (unsigned)G.off_sb;
-    Offs<M> off;                            // byte offsets of the lane's patch words in the window
+    Offs<NB> off;                           // byte offsets of the lane's table-addressed words
 #pragma unroll
-    for (int m = 0; m < M; ++m) off.p[m] = offw[m * 32 + lane];
+    for (int m = 0; m < NB; ++m) off.p[m] = A0 + m < M ? offw[(A0 + m) * 32 + lane] : 0u;
     // zero references: B-group lanes without a word, and past the last row
     const bool has_b = G.S == 0 || lane % G.S < G.wl;
     const int mask_b = has_b ? -1 : 0;
@@ -642,11 +660,12 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
         int32_t bu = R.u;
         unsigned long long bc = have ? R.cost : INF;
         int b[M];
-        const unsigned rbase = a_ref + 4u * (unsigned)((a / (PT_TW / 2)) * sig * G.spr + H.shr +
+        const unsigned rbase = a_ref + 4u * (unsigned)((a / (PT_TW / 2)) * sig * spr + H.shr +
                                                        (R.px - h - H.rx0) * WPP);
+        const unsigned rbasel = rbase + 4u * (unsigned)lane;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-            b[m] = lds32(rbase + offr[m * 32 + lane]);
+            b[m] = lds32(m < A0 ? rbasel + 4u * (unsigned)(m * spr) : rbase + offr[m * 32 + lane]);
             if (NA >= 0) {
                 if (m >= NA) b[m] &= (m == M - 1) ? mask_last : mask_b;
             } else {
@@ -694,8 +713,8 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
                 cu = pack_u(ux0 + dx, uy0 + dy);
             }
             ++n_eval;
-            const unsigned long long cst =
-                pp_cost<NCH, M>(b, off, D, G, H, a_tw, a_sb, R.sa, qx, qy, lane, n_glob);
+            const unsigned long long cst = pp_cost<NCH, M, NA, SPW>(b, off, D, G, H, a_tw, a_sb,
+                                                                    R.sa, qx, qy, lane, n_glob);
             if (cst < bc) { bc = cst; bu = cu; have = true; }
         }
         if (lane == 0 && have && (bu != R.u || !(R.f & F_VALID))) {
@@ -710,37 +729,40 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
     }
 }
 
-template <int NCH>
+// One colour phase of one direction for all pairs of the launch; the
+// consumer is specialised at compile time (M, NA, SPW, SPR as for
+// pp_consume), so each specialisation is its own kernel with its own register
+// allocation.
+template <int NCH, int M, int NA, int SPW, int SPR>
 __global__ void __launch_bounds__(PP_THREADS, 2)
 k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_constant__ PtSched S,
        const int buf_words) {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ SeedRec s_rec[2][PT_NACT];
     __shared__ TileHdr s_hdr[2];
-    __shared__ PpGeom s_geom[2];
-    __shared__ unsigned short s_offr[2][PP_MMAX * 32], s_offw[2][PP_MMAX * 32];
+    __shared__ PpGeom s_geom;
+    __shared__ unsigned short s_offr[PP_MMAX * 32], s_offw[PP_MMAX * 32];
     __shared__ __align__(8) unsigned long long s_bar[2];
     __shared__ int s_next[2], s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned a_sm = (unsigned)__cvta_generic_to_shared(sm);
     const unsigned bar0 = (unsigned)__cvta_generic_to_shared(&s_bar[0]);
-    if (threadIdx.x < 2)
-        s_geom[threadIdx.x] = pp_geom(NCH, B.d[0][threadIdx.x].P, mc.sigma, mc.rs_W, mc.slack);
+    const int P = B.d[0][S.dir].P;
     if (threadIdx.x == 0) {
+        s_geom = pp_geom(NCH, P, mc.sigma, mc.rs_W, mc.slack);
         mbar_init(bar0, 2);
         mbar_init(bar0 + 8, 2);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 2 * PP_MMAX * 32; e += PP_THREADS) {
-        const int d = e / (PP_MMAX * 32), m = (e >> 5) % PP_MMAX, l = e & 31;
-        const PpGeom& G = s_geom[d];
+    for (int e = threadIdx.x; e < PP_MMAX * 32; e += PP_THREADS) {
+        const int m = e >> 5, l = e & 31;
         int row, col;
         bool valid;
-        pp_word(G, B.d[0][d].P, m, l, &row, &col, &valid);
-        s_offr[d][m * 32 + l] = (unsigned short)(4 * (row * G.spr + col));
-        s_offw[d][m * 32 + l] = (unsigned short)(4 * (row * G.spw + col));
+        pp_word(s_geom, P, m, l, &row, &col, &valid);
+        s_offr[e] = (unsigned short)(4 * (row * s_geom.spr + col));
+        s_offw[e] = (unsigned short)(4 * (row * s_geom.spw + col));
     }
     int t = blockIdx.x;                          // the host launches at most S.total CTAs
     if (warp >= PP_CONS)
@@ -767,19 +789,9 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
                     s_abort = 1;
                 }
             } else {
-                const PpGeom G = s_geom[H.dir];
-                const unsigned buf = a_sm + 4u * (unsigned)(cur * buf_words);
-#define PGM_CONSUME(MM, NA) \
-    pp_consume<NCH, MM, NA>(B, mc, H, G, s_rec[cur], buf, s_offr[H.dir], s_offw[H.dir], &s_next[cur], lane)
-                // exact layouts of the common patch sides (6 ch: P 15, 11, 16);
-                // other sides take an upper bound with run-time masks
-                if (NCH == 6 && G.M == 23 && G.nA == 15) PGM_CONSUME(23, 15);
-                else if (NCH == 6 && G.M == 12 && G.nA == 11) PGM_CONSUME(12, 11);
-                else if (NCH == 6 && G.M == 24 && G.nA == 16) PGM_CONSUME(24, 16);
-                else if (G.M <= 8) PGM_CONSUME(8, -1);
-                else if (G.M <= 16) PGM_CONSUME(16, -1);
-                else PGM_CONSUME(24, -1);
-#undef PGM_CONSUME
+                pp_consume<NCH, M, NA, SPW, SPR>(B, mc, H, s_geom, s_rec[cur],
+                                                 a_sm + 4u * (unsigned)(cur * buf_words), s_offr,
+                                                 s_offw, &s_next[cur], lane);
             }
         }
         __syncthreads();
@@ -955,16 +967,17 @@ pgm_status launch_c(const LvlBatch& B, const MatchConst& mc, int tiles, int smem
 }
 
 // Grid of the persistent search kernel: as many CTAs as fit on the device at
-// once (the occupancy query is cached per device and shared-memory size),
-// never more than there are tiles.
-template <int NCH>
+// once (the occupancy query is cached per specialisation, device and
+// shared-memory size), never more than there are tiles.
+template <int NCH, int M, int NA, int SPW, int SPR>
 pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, const PtSched& S, int buf_words,
                     cudaStream_t st) {
     const int smem = 2 * buf_words * 4;
-    static int configured = 0;                 // opt-in above 48 KB once per instantiation
+    static int configured = 0;                 // opt-in above 48 KB once per specialisation
     static int cache_dev = -1, cache_smem = -1, cache_cap = 0;
+    auto kern = k_pm_t<NCH, M, NA, SPW, SPR>;
     if (configured < smem) {
-        if (cudaFuncSetAttribute(k_pm_t<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
             cudaSuccess) return PGM_ERR_CUDA;
         configured = smem;
     }
@@ -973,7 +986,7 @@ pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, const PtSched& S, i
     if (dev != cache_dev || smem != cache_smem) {
         int sms = 0, per = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pm_t<NCH>, PP_THREADS, smem) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, PP_THREADS, smem) !=
                 cudaSuccess || per < 1)
             return PGM_ERR_CUDA;
         cache_cap = sms * per;
@@ -981,10 +994,32 @@ pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, const PtSched& S, i
         cache_smem = smem;
     }
     const int grid = S.total < cache_cap ? S.total : cache_cap;
-    k_pm_t<NCH><<<grid, PP_THREADS, smem, st>>>(B, mc, S, buf_words);
+    kern<<<grid, PP_THREADS, smem, st>>>(B, mc, S, buf_words);
     return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
 }
 
+// The consumer specialisation for a direction's layout: exact layouts of the
+// common patch sides (6 channels: P 15, 11, 16), with constant pitches for
+// the default geometry (seed stride 3, W = 2, margin 2); other layouts take
+// an upper bound of the group count with run-time masks.
+template <int NCH>
+pgm_status launch_dir(const LvlBatch& B, const MatchConst& mc, const PtSched& S, const PpGeom& G,
+                      int buf_words, cudaStream_t st) {
+    if constexpr (NCH == 6) {
+        if (G.q == 1 && G.M == 23 && G.nA == 15)
+            return (G.spw == 144 && G.spr == 112) ? launch_t<6, 23, 15, 144, 112>(B, mc, S, buf_words, st)
+                                                  : launch_t<6, 23, 15, 0, 0>(B, mc, S, buf_words, st);
+        if (G.q == 1 && G.M == 12 && G.nA == 11)
+            return (G.spw == 132 && G.spr == 100) ? launch_t<6, 12, 11, 132, 100>(B, mc, S, buf_words, st)
+                                                  : launch_t<6, 12, 11, 0, 0>(B, mc, S, buf_words, st);
+        if (G.q == 1 && G.M == 24 && G.nA == 16) return launch_t<6, 24, 16, 0, 0>(B, mc, S, buf_words, st);
+        if (G.M <= 8) return launch_t<6, 8, -1, 0, 0>(B, mc, S, buf_words, st);
+        if (G.M <= 16) return launch_t<6, 16, -1, 0, 0>(B, mc, S, buf_words, st);
+        return launch_t<6, 24, -1, 0, 0>(B, mc, S, buf_words, st);
+    } else {
+        return launch_t<NCH, 8, -1, 0, 0>(B, mc, S, buf_words, st);   // 2 channels: M <= 8
+    }
+}
 }  // namespace
 
 // the packed 16-bit byte offsets of a patch must fit
@@ -1001,31 +1036,45 @@ static bool pt_offsets_fit(const LvlBatch& B, int nch, const MatchConst& mc) {
 // *handled = false when two tile buffers would not fit in shared memory or a
 // staged row could not move by 16-byte bulk copies; the caller then uses the
 // per-seed kernel.
-pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
+pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP, int* nlaunch,
                           bool* handled, cudaStream_t st) {
     (void)maxP;
     *handled = false;
-    PtSched S;
-    S.nk = 2 * B.n;
-    S.total = 0;
+    *nlaunch = 0;
+    PtSched S[2];
+    PpGeom G[2];
     int words = 0;
     bool ok = true;
-    for (int k = 0; k < S.nk; ++k) {
-        const DirLvl& D = B.d[k >> 1][k & 1];
-        S.cum[k] = S.total;
-        S.total += ((D.nx + PT_TW - 1) / PT_TW) * ((D.ny + PT_TH - 1) / PT_TH);
-        const PpGeom g = pp_geom(nch, D.P, mc.sigma, mc.rs_W, mc.slack);
-        if (g.words > words) words = g.words;
-        if (g.M > PP_MMAX || 4L * ((long)(D.P - 1) * g.spw + g.wprp) >= 65536L) ok = false;
-        if ((((uintptr_t)D.ref_split | (uintptr_t)D.tgt | (uintptr_t)D.sb2) & 15) != 0 ||
-            (D.ref_pitch * 2) % 16 != 0 || (D.tgt_pitch * 2) % 16 != 0)
+    for (int d = 0; d < 2; ++d) {
+        S[d].nk = B.n;
+        S[d].total = 0;
+        S[d].dir = d;
+        S[d].pad = 0;
+        G[d] = pp_geom(nch, B.d[0][d].P, mc.sigma, mc.rs_W, mc.slack);
+        if (G[d].words > words) words = G[d].words;
+        if (G[d].M > PP_MMAX || 4L * ((long)(B.d[0][d].P - 1) * G[d].spw + G[d].wprp) >= 65536L)
             ok = false;
+        for (int k = 0; k < B.n; ++k) {
+            const DirLvl& D = B.d[k][d];
+            S[d].cum[k] = S[d].total;
+            S[d].total += ((D.nx + PT_TW - 1) / PT_TW) * ((D.ny + PT_TH - 1) / PT_TH);
+            if (D.P != B.d[0][d].P) ok = false;
+            if ((((uintptr_t)D.ref_split | (uintptr_t)D.tgt | (uintptr_t)D.sb2) & 15) != 0 ||
+                (D.ref_pitch * 2) % 16 != 0 || (D.tgt_pitch * 2) % 16 != 0)
+                ok = false;
+        }
+        S[d].cum[B.n] = S[d].total;
     }
-    S.cum[S.nk] = S.total;
     if (!ok || 2L * words * 4 > 200L * 1024) return PGM_OK;
     *handled = true;
-    if (S.total == 0) return PGM_OK;
-    return nch == 2 ? launch_t<2>(B, mc, S, words, st) : launch_t<6>(B, mc, S, words, st);
+    for (int d = 0; d < 2; ++d) {
+        if (S[d].total == 0) continue;
+        const pgm_status r = nch == 2 ? launch_dir<2>(B, mc, S[d], G[d], G[d].words, st)
+                                      : launch_dir<6>(B, mc, S[d], G[d], G[d].words, st);
+        if (r != PGM_OK) return r;
+        ++*nlaunch;
+    }
+    return PGM_OK;
 }
 
 pgm_status launch_cost_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
