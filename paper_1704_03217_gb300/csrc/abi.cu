@@ -308,16 +308,21 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
             r = launch_transfer(X, max_seeds, st);
         }
         if (r != PGM_OK) return r;
-        r = launch_cost_fill(B, mc, nch, maxP, max_seeds, st);
-        if (r != PGM_OK) return r;
+        // the cost refresh of the visit: by the search kernel's first
+        // iteration when the tile kernel takes the batch, else on its own
         const int T = l == 0 ? p->iters_fine : p->iters_coarse;
+        const bool fused = T > 0 && pm_tile_fits(B, mc, nch);
+        if (!fused) {
+            r = launch_cost_fill(B, mc, nch, maxP, max_seeds, st);
+            if (r != PGM_OK) return r;
+        }
         for (int t = 0; t < T; ++t)
             for (int col = 0; col < 2; ++col) {
-                mc.t = t; mc.colour = col;
+                mc.t = t; mc.colour = col; mc.refresh = fused && t == 0;
                 r = launch_pm_phase(B, mc, nch, maxP, max_half, st);
                 if (r != PGM_OK) return r;
             }
-        mc.t = 0; mc.colour = 0;
+        mc.t = 0; mc.colour = 0; mc.refresh = 0;
         r = launch_consist(B, mc, max_seeds, st);
         if (r != PGM_OK) return r;
     }

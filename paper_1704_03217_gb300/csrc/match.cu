@@ -705,6 +705,7 @@ pgm_status launch_pm_phase(const LvlBatch& B, const MatchConst& mc, int nch, int
         pgm_status r = launch_pm_tile(B, mc, nch, maxP, &nl, &handled, st);
         if (handled) ks.n = nl;
         if (r != PGM_OK || handled) return r;
+        if (mc.refresh) return PGM_ERR_UNSUPPORTED;     // the per-seed kernel does no refresh
         PGM_DISPATCH_X(k_pm_x, g, B, mc);
     }
     else PGM_DISPATCH_NCH_PPL_NORM(k_pm, g, B, mc);

@@ -117,7 +117,8 @@ struct MatchConst {              // scalars common to one launch
     int32_t norm, rs_W, rs_mode, K;
     uint32_t key0, key1;
     int32_t t, colour, tau2, rs_grid;   // rs_grid > 0: level-0 search on that grid only
-    int32_t slack, pad2;                // tuning: target-window margin of the tile kernels
+    int32_t slack;                      // tuning: target-window margin of the tile kernels
+    int32_t refresh;                    // search phase also scores the current matches first
 };
 
 // result-invariant tuning knobs (pgm_set_tuning)
@@ -162,6 +163,9 @@ pgm_status launch_consist(const LvlBatch& B, const MatchConst& mc, int max_seeds
 pgm_status launch_transfer(const XferBatch& X, int max_seeds, cudaStream_t st);
 pgm_status launch_box(const LvlBatch& B, int nch, int max_pixels, cudaStream_t st);
 // pm_tile.cu: *handled = false when the staged tile would not fit in shared memory
+// true when the tile search kernel takes this batch (it then also does the
+// cost refresh of a visit's first iteration, MatchConst::refresh)
+bool pm_tile_fits(const LvlBatch& B, const MatchConst& mc, int nch);
 pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP, int* nlaunch,
                           bool* handled, cudaStream_t st);
 pgm_status launch_cost_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,

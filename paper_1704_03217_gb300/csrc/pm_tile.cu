@@ -440,21 +440,31 @@ __device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& 
             const bool okx = ni >= 0 && ni < D.nx, oky = nj >= 0 && nj < D.ny;
             const int sn0 = okx ? j * D.nx + ni : s, sn1 = oky ? nj * D.nx + i : s;
             const int f = D.flags[s], u = D.u[s];
-            const unsigned long long cst = D.cost[s], sa = D.sa2[s];
-            const int f0 = D.flags[sn0], f1 = D.flags[sn1], u0 = D.u[sn0], u1 = D.u[sn1];
             const int px = mc.c + sig * i, py = mc.c + sig * j;
-            const bool have = f & F_VALID;
-            const int c0 = (okx && (f0 & F_VALID)) ? u0 : NO_CAND;
-            const int c1 = (oky && (f1 & F_VALID)) ? u1 : NO_CAND;
+            const unsigned long long cst = D.cost[s], sa = D.sa2img[(size_t)py * D.rw + px];
+            const int f0 = D.flags[sn0], f1 = D.flags[sn1], u0 = D.u[sn0], u1 = D.u[sn1];
+            // cost refresh (first iteration of a visit): a match whose centre
+            // lies outside the target leaves the seed uninitialised
+            bool have = f & F_VALID, ok_n0 = okx && (f0 & F_VALID), ok_n1 = oky && (f1 & F_VALID);
+            if (mc.refresh) {
+                have = have && inside(D, px + lo16((uint32_t)u), py + hi16((uint32_t)u));
+                ok_n0 = ok_n0 && inside(D, px - sx * sig + lo16((uint32_t)u0), py + hi16((uint32_t)u0));
+                ok_n1 = ok_n1 && inside(D, px + lo16((uint32_t)u1), py - sy * sig + hi16((uint32_t)u1));
+            }
+            const int c0 = ok_n0 ? u0 : NO_CAND;
+            const int c1 = ok_n1 ? u1 : NO_CAND;
             const bool ok0 = c0 != NO_CAND && !(have && c0 == u) &&
                              inside(D, px + lo16((uint32_t)c0), py + hi16((uint32_t)c0));
             // a repeat of c0 scores the same and cannot be strictly better
             const bool ok1 = c1 != NO_CAND && c1 != c0 && !(have && c1 == u) &&
                              inside(D, px + lo16((uint32_t)c1), py + hi16((uint32_t)c1));
-            R.s = s; R.px = px; R.py = py; R.f = f; R.u = u;
+            R.s = s; R.px = px; R.py = py; R.u = u;
+            R.f = have ? f : (f & ~F_VALID);
+            R.pad0 = f;                           // flags as read
             R.nb0 = ok0 ? c0 : NO_CAND;
             R.nb1 = ok1 ? c1 : NO_CAND;
-            R.cost = cst; R.sa = sa;
+            R.cost = mc.refresh ? INF : cst;
+            R.sa = sa;
             const int g = mc.rs_grid;             // PGM-C3/G3: level-0 search on a grid only
             R.K = (B.level == 0 && g > 0 && !(px % g == g / 2 && py % g == g / 2)) ? 0 : mc.K;
             if (R.K > 0) {
@@ -647,7 +657,7 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
     const bool has_b = G.S == 0 || lane % G.S < G.wl;
     const int mask_b = has_b ? -1 : 0;
     const int mask_last = (has_b && (G.nB == 0 || (G.nB - 1) * G.g + lane / G.S < P)) ? -1 : 0;
-    unsigned n_eval = 0, n_glob = 0;
+    unsigned n_eval = 0, n_cost = 0, n_glob = 0;
     for (;;) {
         int a = 0;
         if (lane == 0) a = atomicAdd(next, 1);
@@ -656,7 +666,10 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
         const SeedRec R = rec[a];
         if (R.s < 0) continue;
         bool have = R.f & F_VALID;
-        if (!have && R.nb0 == NO_CAND && R.nb1 == NO_CAND) continue;   // nothing to score
+        if (!have && R.nb0 == NO_CAND && R.nb1 == NO_CAND) {          // nothing to score
+            if (lane == 0 && R.f != R.pad0) D.flags[R.s] = (uint8_t)R.f;   // refresh dropped it
+            continue;
+        }
         int32_t bu = R.u;
         unsigned long long bc = have ? R.cost : INF;
         int b[M];
@@ -673,15 +686,22 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
             }
         }
         // one loop over the candidate sequence (a single inlined cost site):
-        // c = 0, 1: propagated matches (Eq. 4); c >= 2: random search (Eq. 5)
-        // around the match held after propagation
+        // c = -1: the current match (cost refresh); c = 0, 1: propagated
+        // matches (Eq. 4); c >= 2: random search (Eq. 5) around the match held
+        // after propagation
         int ux0 = 0, uy0 = 0;
         uint4 r = make_uint4(0, 0, 0, 0);
 #pragma unroll 1
-        for (int c = 0; c < 2 + R.K; ++c) {
+        for (int c = (mc.refresh && have) ? -1 : 0; c < 2 + R.K; ++c) {
             int32_t cu;
             int qx, qy;
-            if (c < 2) {
+            if (c < 0) {
+                cu = R.u;
+                qx = R.px + lo16((uint32_t)cu);
+                qy = R.py + hi16((uint32_t)cu);
+                --n_eval;                           // counted as a refresh, not a search
+                ++n_cost;
+            } else if (c < 2) {
                 cu = c ? R.nb1 : R.nb0;
                 if (cu == NO_CAND) continue;
                 qx = R.px + lo16((uint32_t)cu);
@@ -717,14 +737,19 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
                                                                     R.sa, qx, qy, lane, n_glob);
             if (cst < bc) { bc = cst; bu = cu; have = true; }
         }
-        if (lane == 0 && have && (bu != R.u || !(R.f & F_VALID))) {
-            D.u[R.s] = bu;
-            D.cost[R.s] = bc;
-            D.flags[R.s] = (uint8_t)(R.f | F_VALID);
+        if (lane == 0) {
+            if (have && (mc.refresh || bu != R.u || !(R.f & F_VALID))) {
+                D.u[R.s] = bu;
+                D.cost[R.s] = bc;
+                D.flags[R.s] = (uint8_t)(R.f | F_VALID);
+            } else if (!have && R.f != R.pad0) {
+                D.flags[R.s] = (uint8_t)R.f;
+            }
         }
     }
     if (lane == 0) {
         if (n_eval) atomicAdd(B.evals[H.pair] + H.dir, (unsigned long long)n_eval);
+        if (n_cost) atomicAdd(B.evals[H.pair] + 2 + H.dir, (unsigned long long)n_cost);
         if (n_glob) atomicAdd(B.evals[H.pair] + 6 + H.dir, (unsigned long long)n_glob);
     }
 }
@@ -1036,14 +1061,10 @@ static bool pt_offsets_fit(const LvlBatch& B, int nch, const MatchConst& mc) {
 // *handled = false when two tile buffers would not fit in shared memory or a
 // staged row could not move by 16-byte bulk copies; the caller then uses the
 // per-seed kernel.
-pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP, int* nlaunch,
-                          bool* handled, cudaStream_t st) {
-    (void)maxP;
-    *handled = false;
-    *nlaunch = 0;
-    PtSched S[2];
-    PpGeom G[2];
-    int words = 0;
+// Per-direction schedule and layout of a search launch; false when two tile
+// buffers would not fit in shared memory, a lane offset would not fit in 16
+// bits or a staged row could not move by 16-byte bulk copies.
+static bool pp_plan(const LvlBatch& B, const MatchConst& mc, int nch, PtSched* S, PpGeom* G) {
     bool ok = true;
     for (int d = 0; d < 2; ++d) {
         S[d].nk = B.n;
@@ -1051,8 +1072,8 @@ pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int 
         S[d].dir = d;
         S[d].pad = 0;
         G[d] = pp_geom(nch, B.d[0][d].P, mc.sigma, mc.rs_W, mc.slack);
-        if (G[d].words > words) words = G[d].words;
-        if (G[d].M > PP_MMAX || 4L * ((long)(B.d[0][d].P - 1) * G[d].spw + G[d].wprp) >= 65536L)
+        if (G[d].M > PP_MMAX || 4L * ((long)(B.d[0][d].P - 1) * G[d].spw + G[d].wprp) >= 65536L ||
+            2L * G[d].words * 4 > 200L * 1024)
             ok = false;
         for (int k = 0; k < B.n; ++k) {
             const DirLvl& D = B.d[k][d];
@@ -1065,7 +1086,25 @@ pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int 
         }
         S[d].cum[B.n] = S[d].total;
     }
-    if (!ok || 2L * words * 4 > 200L * 1024) return PGM_OK;
+    return ok;
+}
+
+bool pm_tile_fits(const LvlBatch& B, const MatchConst& mc, int nch) {
+    PtSched S[2];
+    PpGeom G[2];
+    return mc.norm == PGM_L2SQ && pp_plan(B, mc, nch, S, G);
+}
+
+// *handled = false when pp_plan refuses the batch; the caller then uses the
+// per-seed kernel.  *nlaunch: kernels launched (one per direction with tiles).
+pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP, int* nlaunch,
+                          bool* handled, cudaStream_t st) {
+    (void)maxP;
+    *handled = false;
+    *nlaunch = 0;
+    PtSched S[2];
+    PpGeom G[2];
+    if (!pp_plan(B, mc, nch, S, G)) return PGM_OK;
     *handled = true;
     for (int d = 0; d < 2; ++d) {
         if (S[d].total == 0) continue;
