@@ -226,7 +226,7 @@ __device__ __forceinline__ unsigned long long tile_cost(
 // carries a zero reference.  The reference region has its own, narrower
 // pitch; its lane offsets are read from a table when a seed's reference
 // words are loaded, the window's stay in registers.
-constexpr int PP_CONS = 8, PP_PROD = 2;          // consumer / producer warps
+constexpr int PP_CONS = 10, PP_PROD = 2;          // consumer / producer warps
 constexpr int PP_THREADS = 32 * (PP_CONS + PP_PROD);
 constexpr int PP_MMAX = 24;                      // 32-word groups of the largest patch
 constexpr long long PP_WAIT_CYCLES = 1ll << 31;  // bounded mbarrier wait (about 1 s)
