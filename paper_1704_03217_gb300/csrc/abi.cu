@@ -154,14 +154,6 @@ bool make_ws_plan(const pgm_params* p, int w1, int h1, int w2, int h2, WsPlan* w
             wp->off_sa2img[l][d] = off;
             off = align_up(off + 8 * (size_t)r.W[l] * r.H[l], 256);
         }
-    for (int d = 0; d < 2; ++d) {
-        const PyrPlan& t = d == 0 ? b : a;
-        wp->off_boxtmp[d] = off;
-        off = align_up(off + 8 * (size_t)t.W[0] * t.H[0], 256);
-        const PyrPlan& r = d == 0 ? a : b;
-        wp->off_boxtmp_ref[d] = off;
-        off = align_up(off + 8 * (size_t)r.W[0] * r.H[0], 256);
-    }
     size_t n0 = (size_t)wp->nx[0][0] * wp->ny[0][0];
     wp->nblk0 = (int)((n0 + 255) / 256);
     wp->off_label = off; off = align_up(off + 4 * n0, 256);
@@ -224,9 +216,7 @@ void fill_dir(const pgm_params* p, const PairCtx& c, int l, int d, DirLvl* D) {
     D->oflags = c.ws + c.w.off_flags[l][1 - d];
     D->sa2 = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sa2[l][d]);
     D->sb2 = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sb2[l][d]);
-    D->boxtmp = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_boxtmp[d]);
     D->sa2img = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sa2img[l][d]);
-    D->boxtmp_ref = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_boxtmp_ref[d]);
 }
 
 pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) {

@@ -89,45 +89,56 @@ __device__ __forceinline__ unsigned long long warp_cost(const Ref<NCH, PPL>& R, 
 //   |sum b a_l| <= 1536 * 12240 * 64 < 1.3e9,  |sum b a_h| <= 1536 * 12240 * 96 < 1.9e9.
 
 // Box filter of N(x, y) = sum_c G_c(x, y)^2 over the P x P patch with
-// replicated borders, separable: row sums, then column sums (exact, uint64).
-// blockIdx.y = 2 * direction + (0: target image -> sb2, 1: reference -> sa2img)
+// replicated borders (the sums |a|^2 and |b|^2 of Eq. 3 expanded), exact in
+// uint64 (N itself fits 32 bits: 6 values of at most 24480^2).  A CTA makes a
+// BOX_TW x BOX_TH block of one map: N over the block and a halo of P / 2
+// (clamped coordinates) into shared memory, then row sums, then column sums.
+// blockIdx.y = 2 * direction + (0: target image -> sb2, 1: reference ->
+// sa2img); blockIdx.x = block of that map (the grid covers the largest map).
+constexpr int BOX_TW = 32, BOX_TH = 16, BOX_H = MAXP / 2;
 template <int NCH>
-__global__ void k_box_h(const __grid_constant__ LvlBatch B) {
+__global__ void __launch_bounds__(256) k_box(const __grid_constant__ LvlBatch B) {
+    __shared__ uint32_t sN[BOX_TH + 2 * BOX_H][BOX_TW + 2 * BOX_H];
+    __shared__ unsigned long long sR[BOX_TH + 2 * BOX_H][BOX_TW];
     const DirLvl& D = B.d[blockIdx.z][blockIdx.y >> 1];
     const bool ref = blockIdx.y & 1;
-    const int w = ref ? D.rw : D.tw, hh = ref ? D.rh : D.th;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= w * hh) return;
-    const int x = idx % w, y = idx / w, h = D.P / 2;
+    const int w = ref ? D.rw : D.tw, hh = ref ? D.rh : D.th, P = D.P, h = P / 2;
+    const int tx = (w + BOX_TW - 1) / BOX_TW, ty = (hh + BOX_TH - 1) / BOX_TH;
+    if ((int)blockIdx.x >= tx * ty) return;
+    const int x0 = ((int)blockIdx.x % tx) * BOX_TW, y0 = ((int)blockIdx.x / tx) * BOX_TH;
     const int16_t* img = ref ? D.ref : D.tgt;
     const int pitch = ref ? D.ref_pitch : D.tgt_pitch;
-    const uint32_t* row = reinterpret_cast<const uint32_t*>(img + (size_t)y * pitch);
-    unsigned long long s = 0;
-    for (int o = 0; o < D.P; ++o) {
-        const int xx = clampi(x + o - h, 0, w - 1);
+    const int iw = BOX_TW + P - 1, ih = BOX_TH + P - 1;
+    for (int e = threadIdx.x; e < iw * ih; e += blockDim.x) {
+        const int r = e / iw, c = e - r * iw;
+        const int x = clampi(x0 - h + c, 0, w - 1), y = clampi(y0 - h + r, 0, hh - 1);
+        const uint32_t* px =
+            reinterpret_cast<const uint32_t*>(img + (size_t)y * pitch) + (size_t)x * (NCH / 2);
         uint32_t n = 0;
 #pragma unroll
-        for (int c = 0; c < NCH / 2; ++c) {
-            const uint32_t v = __ldg(row + (size_t)xx * (NCH / 2) + c);
+        for (int c2 = 0; c2 < NCH / 2; ++c2) {
+            const uint32_t v = __ldg(px + c2);
             const int a = lo16(v), b = hi16(v);
             n += (uint32_t)(a * a) + (uint32_t)(b * b);
         }
-        s += n;
+        sN[r][c] = n;
     }
-    (ref ? D.boxtmp_ref : D.boxtmp)[idx] = s;
-}
-
-__global__ void k_box_v(const __grid_constant__ LvlBatch B) {
-    const DirLvl& D = B.d[blockIdx.z][blockIdx.y >> 1];
-    const bool ref = blockIdx.y & 1;
-    const int w = ref ? D.rw : D.tw, hh = ref ? D.rh : D.th;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= w * hh) return;
-    const int x = idx % w, y = idx / w, h = D.P / 2;
-    const unsigned long long* tmp = ref ? D.boxtmp_ref : D.boxtmp;
-    unsigned long long s = 0;
-    for (int o = 0; o < D.P; ++o) s += tmp[(size_t)clampi(y + o - h, 0, hh - 1) * w + x];
-    (ref ? D.sa2img : D.sb2)[idx] = s;
+    __syncthreads();
+    for (int e = threadIdx.x; e < ih * BOX_TW; e += blockDim.x) {
+        const int r = e / BOX_TW, c = e - r * BOX_TW;
+        unsigned long long s = 0;
+        for (int o = 0; o < P; ++o) s += sN[r][c + o];
+        sR[r][c] = s;
+    }
+    __syncthreads();
+    unsigned long long* out = ref ? D.sa2img : D.sb2;
+    for (int e = threadIdx.x; e < BOX_TH * BOX_TW; e += blockDim.x) {
+        const int r = e / BOX_TW, c = e - r * BOX_TW, x = x0 + c, y = y0 + r;
+        if (x >= w || y >= hh) continue;
+        unsigned long long s = 0;
+        for (int o = 0; o < P; ++o) s += sR[r + o][c];
+        out[(size_t)y * w + x] = s;
+    }
 }
 
 // Lane l owns words l, l + 32, ... of the P x P x NCH patch, flattened row by
@@ -713,12 +724,21 @@ pgm_status launch_pm_phase(const LvlBatch& B, const MatchConst& mc, int nch, int
 }
 
 pgm_status launch_box(const LvlBatch& B, int nch, int max_pixels, cudaStream_t st) {
-    if (max_pixels <= 0) return PGM_OK;
-    KScope ks(PGM_K_COST, st, 2);
-    dim3 g((max_pixels + 255) / 256, 4, B.n);
-    if (nch == 2) k_box_h<2><<<g, 256, 0, st>>>(B);
-    else k_box_h<6><<<g, 256, 0, st>>>(B);
-    k_box_v<<<g, 256, 0, st>>>(B);
+    (void)max_pixels;
+    int tiles = 0;
+    for (int k = 0; k < B.n; ++k)
+        for (int d = 0; d < 2; ++d) {
+            const DirLvl& D = B.d[k][d];
+            const int t1 = ((D.tw + BOX_TW - 1) / BOX_TW) * ((D.th + BOX_TH - 1) / BOX_TH);
+            const int t2 = ((D.rw + BOX_TW - 1) / BOX_TW) * ((D.rh + BOX_TH - 1) / BOX_TH);
+            tiles = t1 > tiles ? t1 : tiles;
+            tiles = t2 > tiles ? t2 : tiles;
+        }
+    if (tiles <= 0) return PGM_OK;
+    KScope ks(PGM_K_COST, st);
+    dim3 g(tiles, 4, B.n);
+    if (nch == 2) k_box<2><<<g, 256, 0, st>>>(B);
+    else k_box<6><<<g, 256, 0, st>>>(B);
     return last_status();
 }
 

@@ -44,9 +44,7 @@ struct WsPlan {
     size_t off_u[MAXL][2], off_cost[MAXL][2], off_flags[MAXL][2];
     size_t off_sa2[MAXL][2];     // per seed: sum of |G|^2 over its reference patch
     size_t off_sb2[MAXL][2];     // per target pixel: sum of |G|^2 over the patch there
-    size_t off_boxtmp[2];        // per direction: row sums of the box filter (level-0 size)
     size_t off_sa2img[MAXL][2];  // per reference pixel: sum of |G|^2 over the patch there
-    size_t off_boxtmp_ref[2];    // per direction: row sums for the reference box filter
     size_t off_err;              // uint32 device status word
     size_t off_label, off_size, off_bsum;   // filter scratch (level-0 forward lattice)
     int nblk0;                   // blocks of the level-0 forward lattice scan
@@ -88,9 +86,7 @@ struct DirLvl {
     const uint8_t* oflags;       //                  flags
     unsigned long long* sa2;     // per seed: sum over the reference patch of |G|^2
     unsigned long long* sb2;     // per target pixel (row pitch tw): same over the target patch
-    unsigned long long* boxtmp;  // scratch of the box filter (row pitch tw)
     unsigned long long* sa2img;  // per reference pixel (row pitch rw): sum over its patch
-    unsigned long long* boxtmp_ref;  // scratch of the reference box filter (row pitch rw)
 };
 
 struct LvlBatch {

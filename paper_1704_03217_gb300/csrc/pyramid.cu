@@ -142,41 +142,60 @@ __global__ void k_convert(const __grid_constant__ PyrBatch B) {
 
 // ----------------------------------------------------------------- Sobel
 // Gx = sum_j s_j sum_i d_i I(x+i, y+j); Gy with the roles of the axes swapped.
+// A CTA makes a 32 x 8 block of one image: the (32 + S - 1) x (8 + S - 1)
+// input pixels of every channel (border replicated) go to shared memory, the
+// horizontal passes (d and s along x) are kept per input row, and the
+// vertical passes finish Gx and Gy (separable and exact in integers).
+constexpr int SB_TW = 32, SB_TH = 8;
 template <int S, int C>
-__global__ void k_sobel(const __grid_constant__ PyrBatch B, int dir_only) {
+__global__ void __launch_bounds__(SB_TW * SB_TH) k_sobel(const __grid_constant__ PyrBatch B,
+                                                         int dir_only) {
+    constexpr int R = S / 2, IW = SB_TW + S - 1, IH = SB_TH + S - 1;
+    __shared__ uint8_t sI[C][IH][IW];
+    __shared__ int sD[C][IH][SB_TW], sS[C][IH][SB_TW];
     const PyrItem& it = B.it[blockIdx.z];
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int w = it.sw, h = it.sh, row = it.srow;
+    const int x0 = blockIdx.x * SB_TW, y0 = blockIdx.y * SB_TH;
+    if (x0 >= w || y0 >= h) return;                     // the whole block (uniform)
     const size_t plane = it.splane;
     const uint8_t* in = it.src;
-    if (x >= w || y >= h) return;
-    constexpr int R = S / 2;
-    const int d5[5] = {-1, -2, 0, 2, 1}, s5[5] = {1, 4, 6, 4, 1};
-    const int d3[3] = {-1, 0, 1}, s3[3] = {1, 2, 1};
-    int xs[S], ys[S];
-#pragma unroll
-    for (int i = 0; i < S; ++i) {
-        xs[i] = clampi(x + i - R, 0, w - 1);
-        ys[i] = clampi(y + i - R, 0, h - 1);
+    const int tid = threadIdx.y * SB_TW + threadIdx.x;
+    for (int e = tid; e < C * IH * IW; e += SB_TW * SB_TH) {
+        const int ch = e / (IH * IW), rc = e - ch * (IH * IW), r = rc / IW, c = rc - r * IW;
+        const int x = clampi(x0 - R + c, 0, w - 1), y = clampi(y0 - R + r, 0, h - 1);
+        sI[ch][r][c] = in[ch * plane + (size_t)y * row + x];
     }
+    __syncthreads();
+    for (int e = tid; e < C * IH * SB_TW; e += SB_TW * SB_TH) {
+        const int ch = e / (IH * SB_TW), rc = e - ch * (IH * SB_TW), r = rc / SB_TW,
+                  c = rc - r * SB_TW;
+        int sd = 0, ss = 0;
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            const int v = sI[ch][r][c + i];
+            sd += (S == 5 ? (i == 0 ? -1 : i == 1 ? -2 : i == 2 ? 0 : i == 3 ? 2 : 1)
+                          : (i - 1)) * v;
+            ss += (S == 5 ? (i == 0 ? 1 : i == 1 ? 4 : i == 2 ? 6 : i == 3 ? 4 : 1)
+                          : (i == 1 ? 2 : 1)) * v;
+        }
+        sD[ch][r][c] = sd;
+        sS[ch][r][c] = ss;
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= w || y >= h) return;
     int g[2 * C];
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) {
-        const uint8_t* src = in + ch * plane;
         int gx = 0, gy = 0;
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-            const uint8_t* r = src + (size_t)ys[j] * row;
-            int sd = 0, ss = 0;
-#pragma unroll
-            for (int i = 0; i < S; ++i) {
-                int v = r[xs[i]];
-                sd += (S == 5 ? d5[i] : d3[i]) * v;
-                ss += (S == 5 ? s5[i] : s3[i]) * v;
-            }
-            gx += (S == 5 ? s5[j] : s3[j]) * sd;
-            gy += (S == 5 ? d5[j] : d3[j]) * ss;
+            const int sj = S == 5 ? (j == 0 ? 1 : j == 1 ? 4 : j == 2 ? 6 : j == 3 ? 4 : 1)
+                                  : (j == 1 ? 2 : 1);
+            const int dj = S == 5 ? (j == 0 ? -1 : j == 1 ? -2 : j == 2 ? 0 : j == 3 ? 2 : 1)
+                                  : (j - 1);
+            gx += sj * sD[ch][threadIdx.y + j][threadIdx.x];
+            gy += dj * sS[ch][threadIdx.y + j][threadIdx.x];
         }
         if (dir_only == 1) {                  // direction only: G ./ |G|
             gx = (gx > 0) - (gx < 0);
