@@ -305,9 +305,10 @@ struct __align__(16) SeedRec {      // one active seed of a staged tile
 
 struct TileHdr { int pair, dir, i0, j0, rx0, wx0, wy0, use_win, shr, shw, shs, pad; };
 
-// The flattened tiles of one launch (one direction): pair k owns tiles
-// [cum[k], cum[k + 1]).
-struct PtSched { int nk, total, dir, pad; int cum[MAXB + 1]; };
+// The flattened tiles of one launch: slot k owns tiles [cum[k], cum[k + 1]);
+// ndir = 1: slot k is pair k in direction dir; ndir = 2: slot k is pair k / 2
+// in direction k % 2.
+struct PtSched { int nk, total, dir, ndir; int cum[2 * MAXB + 1]; };
 
 constexpr int NO_CAND = INT_MIN;            // no propagated candidate
 
@@ -401,15 +402,16 @@ __device__ __forceinline__ void mbar_arrive(unsigned bar) {
 template <int NCH>
 __device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& mc,
                                            const PtSched& S, int t, unsigned buf, SeedRec* rec,
-                                           TileHdr* hdr, int* next, const PpGeom& G,
+                                           TileHdr* hdr, int* next, const PpGeom* geom,
                                            unsigned bar, int pw, int lane) {
     constexpr int WPP = NCH / 2;
-    int lo = 0, hi = S.nk - 1;                   // pair holding tile t:
+    int lo = 0, hi = S.nk - 1;                   // slot holding tile t:
     while (lo < hi) {                            // the last k with cum[k] <= t
         const int mid = (lo + hi + 1) >> 1;
         if (S.cum[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    const int k = lo, pair = k, dir = S.dir;
+    const int k = lo, pair = S.ndir == 2 ? k >> 1 : k, dir = S.ndir == 2 ? (k & 1) : S.dir;
+    const PpGeom& G = geom[dir];
     const DirLvl& D = B.d[pair][dir];
     const int tiles_x = (D.nx + PT_TW - 1) / PT_TW, tt = t - S.cum[k];
     const int i0 = (tt % tiles_x) * PT_TW, j0 = (tt / tiles_x) * PT_TH;
@@ -765,29 +767,30 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ SeedRec s_rec[2][PT_NACT];
     __shared__ TileHdr s_hdr[2];
-    __shared__ PpGeom s_geom;
-    __shared__ unsigned short s_offr[PP_MMAX * 32], s_offw[PP_MMAX * 32];
+    __shared__ PpGeom s_geom[2];
+    __shared__ unsigned short s_offr[2][PP_MMAX * 32], s_offw[2][PP_MMAX * 32];
     __shared__ __align__(8) unsigned long long s_bar[2];
     __shared__ int s_next[2], s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned a_sm = (unsigned)__cvta_generic_to_shared(sm);
     const unsigned bar0 = (unsigned)__cvta_generic_to_shared(&s_bar[0]);
-    const int P = B.d[0][S.dir].P;
+    if (threadIdx.x < 2)
+        s_geom[threadIdx.x] = pp_geom(NCH, B.d[0][threadIdx.x].P, mc.sigma, mc.rs_W, mc.slack);
     if (threadIdx.x == 0) {
-        s_geom = pp_geom(NCH, P, mc.sigma, mc.rs_W, mc.slack);
         mbar_init(bar0, 2);
         mbar_init(bar0 + 8, 2);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < PP_MMAX * 32; e += PP_THREADS) {
-        const int m = e >> 5, l = e & 31;
+    for (int e = threadIdx.x; e < 2 * PP_MMAX * 32; e += PP_THREADS) {
+        const int d = e / (PP_MMAX * 32), i = e - d * (PP_MMAX * 32), m = i >> 5, l = i & 31;
+        const PpGeom& G = s_geom[d];
         int row, col;
         bool valid;
-        pp_word(s_geom, P, m, l, &row, &col, &valid);
-        s_offr[e] = (unsigned short)(4 * (row * s_geom.spr + col));
-        s_offw[e] = (unsigned short)(4 * (row * s_geom.spw + col));
+        pp_word(G, B.d[0][d].P, m, l, &row, &col, &valid);
+        s_offr[d][i] = (unsigned short)(4 * (row * G.spr + col));
+        s_offw[d][i] = (unsigned short)(4 * (row * G.spw + col));
     }
     int t = blockIdx.x;                          // the host launches at most S.total CTAs
     if (warp >= PP_CONS)
@@ -814,9 +817,9 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
                     s_abort = 1;
                 }
             } else {
-                pp_consume<NCH, M, NA, SPW, SPR>(B, mc, H, s_geom, s_rec[cur],
-                                                 a_sm + 4u * (unsigned)(cur * buf_words), s_offr,
-                                                 s_offw, &s_next[cur], lane);
+                pp_consume<NCH, M, NA, SPW, SPR>(B, mc, H, s_geom[H.dir], s_rec[cur],
+                                                 a_sm + 4u * (unsigned)(cur * buf_words),
+                                                 s_offr[H.dir], s_offw[H.dir], &s_next[cur], lane);
             }
         }
         __syncthreads();
@@ -1058,54 +1061,86 @@ static bool pt_offsets_fit(const LvlBatch& B, int nch, const MatchConst& mc) {
     return true;
 }
 
-// *handled = false when two tile buffers would not fit in shared memory or a
-// staged row could not move by 16-byte bulk copies; the caller then uses the
-// per-seed kernel.
-// Per-direction schedule and layout of a search launch; false when two tile
-// buffers would not fit in shared memory, a lane offset would not fit in 16
-// bits or a staged row could not move by 16-byte bulk copies.
+// Per-direction schedules S[0], S[1], the schedule of both directions
+// together S[2], and the layouts; false when two tile buffers would not fit
+// in shared memory, a lane offset would not fit in 16 bits or a staged row
+// could not move by 16-byte bulk copies.
 static bool pp_plan(const LvlBatch& B, const MatchConst& mc, int nch, PtSched* S, PpGeom* G) {
     bool ok = true;
+    S[2].nk = 2 * B.n;
+    S[2].total = 0;
+    S[2].dir = 0;
+    S[2].ndir = 2;
     for (int d = 0; d < 2; ++d) {
         S[d].nk = B.n;
         S[d].total = 0;
         S[d].dir = d;
-        S[d].pad = 0;
+        S[d].ndir = 1;
         G[d] = pp_geom(nch, B.d[0][d].P, mc.sigma, mc.rs_W, mc.slack);
         if (G[d].M > PP_MMAX || 4L * ((long)(B.d[0][d].P - 1) * G[d].spw + G[d].wprp) >= 65536L ||
             2L * G[d].words * 4 > 200L * 1024)
             ok = false;
-        for (int k = 0; k < B.n; ++k) {
+    }
+    for (int k = 0; k < B.n; ++k)
+        for (int d = 0; d < 2; ++d) {
             const DirLvl& D = B.d[k][d];
+            const int tiles = ((D.nx + PT_TW - 1) / PT_TW) * ((D.ny + PT_TH - 1) / PT_TH);
             S[d].cum[k] = S[d].total;
-            S[d].total += ((D.nx + PT_TW - 1) / PT_TW) * ((D.ny + PT_TH - 1) / PT_TH);
+            S[d].total += tiles;
+            S[2].cum[2 * k + d] = S[2].total;
+            S[2].total += tiles;
             if (D.P != B.d[0][d].P) ok = false;
             if ((((uintptr_t)D.ref_split | (uintptr_t)D.tgt | (uintptr_t)D.sb2) & 15) != 0 ||
                 (D.ref_pitch * 2) % 16 != 0 || (D.tgt_pitch * 2) % 16 != 0)
                 ok = false;
         }
-        S[d].cum[B.n] = S[d].total;
-    }
+    S[0].cum[B.n] = S[0].total;
+    S[1].cum[B.n] = S[1].total;
+    S[2].cum[2 * B.n] = S[2].total;
     return ok;
 }
 
 bool pm_tile_fits(const LvlBatch& B, const MatchConst& mc, int nch) {
-    PtSched S[2];
+    PtSched S[3];
     PpGeom G[2];
     return mc.norm == PGM_L2SQ && pp_plan(B, mc, nch, S, G);
 }
 
+static int device_sms() {
+    static int dev_cached = -1, sms = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev != dev_cached) {
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        dev_cached = dev;
+    }
+    return sms;
+}
+
 // *handled = false when pp_plan refuses the batch; the caller then uses the
-// per-seed kernel.  *nlaunch: kernels launched (one per direction with tiles).
+// per-seed kernel.  A small phase (at most one tile per resident CTA, the
+// coarse levels) runs both directions in one launch of the general
+// consumer; a larger one runs each direction in its own launch of the
+// consumer specialised for its layout.  *nlaunch: kernels launched.
 pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP, int* nlaunch,
                           bool* handled, cudaStream_t st) {
     (void)maxP;
     *handled = false;
     *nlaunch = 0;
-    PtSched S[2];
+    PtSched S[3];
     PpGeom G[2];
     if (!pp_plan(B, mc, nch, S, G)) return PGM_OK;
     *handled = true;
+    if (S[2].total == 0) return PGM_OK;
+    const int words = G[0].words > G[1].words ? G[0].words : G[1].words;
+    if (S[2].total <= 2 * device_sms()) {
+        const int m = G[0].M > G[1].M ? G[0].M : G[1].M;
+        *nlaunch = 1;
+        if (nch == 2) return launch_t<2, 8, -1, 0, 0>(B, mc, S[2], words, st);
+        if (m <= 8) return launch_t<6, 8, -1, 0, 0>(B, mc, S[2], words, st);
+        if (m <= 16) return launch_t<6, 16, -1, 0, 0>(B, mc, S[2], words, st);
+        return launch_t<6, 24, -1, 0, 0>(B, mc, S[2], words, st);
+    }
     for (int d = 0; d < 2; ++d) {
         if (S[d].total == 0) continue;
         const pgm_status r = nch == 2 ? launch_dir<2>(B, mc, S[d], G[d], G[d].words, st)
