@@ -1,0 +1,195 @@
+// init_tile.cu -- exhaustive nearest-neighbour initialisation at the
+// coarsest level for the squared-L2 cost: every seed starts from the target
+// centre of least patch distance (Eq. 3) over the whole target image, ties to
+// the smaller raster index (y, then x).
+//
+// D(s, q) = sum |a|^2 + sum |b|^2 - 2 <a, b>: the two sums come from the box
+// filters of the same visit, the cross terms from dp2a products of the target
+// words (two int16 values) with the seed's reference words in split-byte form
+// (a = 128 a_h + a_l).  A CTA takes IN_SB seeds of one direction of one pair
+// and every target centre.  The whole target image, with a border of P / 2
+// replicated, and the seeds' reference patches sit in shared memory; a thread
+// scores IN_PB centres against the IN_SB seeds at once, each target word
+// loaded once for all seeds and each reference word (a broadcast) once for
+// all centres.  A patch row is summed in 32 bits (at most 48 words: below
+// 2^31 for any descriptor value), the rows in 64 bits.
+#include "match_common.cuh"
+
+namespace pgm {
+namespace {
+
+constexpr int IN_SB = 4, IN_PB = 2, IN_THREADS = 256;
+
+// shared words: target image with border, then IN_SB reference patches
+__host__ __device__ inline int in_words(int nch, int P, int tw, int th) {
+    const int wpp = nch / 2;
+    return (tw + P - 1) * (th + P - 1) * wpp + IN_SB * P * P * wpp;
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(IN_THREADS) k_init_t(const __grid_constant__ LvlBatch B,
+                                                       const MatchConst mc) {
+    constexpr int WPP = NCH / 2;
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ unsigned long long s_cost[IN_THREADS / 32][IN_SB];
+    __shared__ int s_q[IN_THREADS / 32][IN_SB];
+    const int pair = blockIdx.z, dir = blockIdx.y;
+    const DirLvl& D = B.d[pair][dir];
+    const int ns = D.nx * D.ny, s0 = blockIdx.x * IN_SB;
+    if (s0 >= ns) return;
+    const int P = D.P, h = P / 2, sig = mc.sigma;
+    const int tpw = D.tw + P - 1, tph = D.th + P - 1, tp = tpw * WPP, prw = P * WPP;
+    const int rw = P * prw;                                // words of one reference patch
+    uint32_t* sT = sm;
+    uint32_t* sR = sm + tph * tp;
+
+    const uint32_t* t32 = reinterpret_cast<const uint32_t*>(D.tgt);
+    const int tpitch = D.tgt_pitch >> 1;
+    for (int e = threadIdx.x; e < tph * tp; e += IN_THREADS) {
+        const int r = e / tp, c = e - r * tp, px = c / WPP, wi = c - px * WPP;
+        const int x = clampi(px - h, 0, D.tw - 1), y = clampi(r - h, 0, D.th - 1);
+        sT[e] = __ldg(t32 + (size_t)y * tpitch + (size_t)x * WPP + wi);
+    }
+    const int rpitch = D.ref_pitch >> 1;
+    for (int e = threadIdx.x; e < IN_SB * rw; e += IN_THREADS) {
+        const int k = e / rw, i = e - k * rw, row = i / prw, c = i - row * prw;
+        const int px = c / WPP, wi = c - px * WPP;
+        const int s = min(s0 + k, ns - 1);                 // a missing seed repeats the last
+        const int si = s % D.nx, sj = s / D.nx;
+        const int x = clampi(mc.c + sig * si + px - h, 0, D.rw - 1);
+        const int y = clampi(mc.c + sig * sj + row - h, 0, D.rh - 1);
+        sR[e] = __ldg(D.ref_split + (size_t)y * rpitch + (size_t)x * WPP + wi);
+    }
+    __syncthreads();
+
+    unsigned long long sa[IN_SB], bc[IN_SB];
+    int bq[IN_SB];
+#pragma unroll
+    for (int k = 0; k < IN_SB; ++k) {
+        const int s = min(s0 + k, ns - 1), si = s % D.nx, sj = s / D.nx;
+        sa[k] = D.sa2img[(size_t)(mc.c + sig * sj) * D.rw + (mc.c + sig * si)];
+        bc[k] = INF;
+        bq[k] = 0;
+    }
+    const int nq = D.tw * D.th;
+    for (int q0 = threadIdx.x; q0 < nq; q0 += IN_THREADS * IN_PB) {
+        int base[IN_PB];
+#pragma unroll
+        for (int p = 0; p < IN_PB; ++p) {
+            const int q = min(q0 + p * IN_THREADS, nq - 1);
+            const int qx = q % D.tw, qy = q / D.tw;
+            base[p] = qy * tp + qx * WPP;                  // patch corner in the staged image
+        }
+        long long acc[IN_PB][IN_SB];
+#pragma unroll
+        for (int p = 0; p < IN_PB; ++p)
+#pragma unroll
+            for (int k = 0; k < IN_SB; ++k) acc[p][k] = 0;
+        for (int r = 0; r < P; ++r) {
+            int lo[IN_PB][IN_SB], hi[IN_PB][IN_SB];
+#pragma unroll
+            for (int p = 0; p < IN_PB; ++p)
+#pragma unroll
+                for (int k = 0; k < IN_SB; ++k) { lo[p][k] = 0; hi[p][k] = 0; }
+            const uint32_t* rrow = sR + r * prw;
+#pragma unroll 3
+            for (int c = 0; c < prw; ++c) {
+                int tv[IN_PB];
+#pragma unroll
+                for (int p = 0; p < IN_PB; ++p) tv[p] = (int)sT[base[p] + r * tp + c];
+#pragma unroll
+                for (int k = 0; k < IN_SB; ++k) {
+                    const int a = (int)rrow[k * rw + c];
+#pragma unroll
+                    for (int p = 0; p < IN_PB; ++p) {
+                        lo[p][k] = __dp2a_lo(tv[p], a, lo[p][k]);
+                        hi[p][k] = __dp2a_hi(tv[p], a, hi[p][k]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < IN_PB; ++p)
+#pragma unroll
+                for (int k = 0; k < IN_SB; ++k)
+                    acc[p][k] += (long long)hi[p][k] * 128 + (long long)lo[p][k];
+        }
+#pragma unroll
+        for (int p = 0; p < IN_PB; ++p) {
+            const int q = q0 + p * IN_THREADS;
+            if (q >= nq) continue;
+            const unsigned long long sb = D.sb2[q];
+#pragma unroll
+            for (int k = 0; k < IN_SB; ++k) {
+                const unsigned long long c = xcost(sa[k], sb, acc[p][k]);
+                if (c < bc[k] || (c == bc[k] && q < bq[k])) { bc[k] = c; bq[k] = q; }
+            }
+        }
+    }
+    // least (cost, raster index) per seed over the CTA
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < IN_SB; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long c = __shfl_xor_sync(FULL, bc[k], o);
+            const int q = __shfl_xor_sync(FULL, bq[k], o);
+            if (c < bc[k] || (c == bc[k] && q < bq[k])) { bc[k] = c; bq[k] = q; }
+        }
+        if (lane == 0) { s_cost[warp][k] = bc[k]; s_q[warp][k] = bq[k]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < IN_SB && s0 + (int)threadIdx.x < ns) {
+        const int k = threadIdx.x, s = s0 + k;
+        unsigned long long c = s_cost[0][k];
+        int q = s_q[0][k];
+        for (int w = 1; w < IN_THREADS / 32; ++w)
+            if (s_cost[w][k] < c || (s_cost[w][k] == c && s_q[w][k] < q)) { c = s_cost[w][k]; q = s_q[w][k]; }
+        const int si = s % D.nx, sj = s / D.nx;
+        D.u[s] = pack_u(q % D.tw - (mc.c + sig * si), q / D.tw - (mc.c + sig * sj));
+        D.cost[s] = c;
+        D.flags[s] = F_VALID;
+    }
+    if (threadIdx.x == 0) {
+        const int nk = min(IN_SB, ns - s0);
+        atomicAdd(B.evals[pair] + 4 + dir, (unsigned long long)nk * (unsigned long long)nq);
+    }
+}
+
+template <int NCH>
+pgm_status launch_in(const LvlBatch& B, const MatchConst& mc, int groups, int smem,
+                     cudaStream_t st) {
+    static int configured = 0;
+    if (configured < smem) {
+        if (cudaFuncSetAttribute(k_init_t<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess) return PGM_ERR_CUDA;
+        configured = smem;
+    }
+    k_init_t<NCH><<<dim3(groups, 2, B.n), IN_THREADS, smem, st>>>(B, mc);
+    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+}
+
+}  // namespace
+
+// *handled = false (nothing launched) when the cost is not squared L2 or a
+// target image with its border does not fit in shared memory.
+pgm_status launch_init_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
+                            cudaStream_t st) {
+    *handled = false;
+    if (mc.norm != PGM_L2SQ) return PGM_OK;
+    int words = 0, seeds = 0;
+    for (int k = 0; k < B.n; ++k)
+        for (int d = 0; d < 2; ++d) {
+            const DirLvl& D = B.d[k][d];
+            const int w = in_words(nch, D.P, D.tw, D.th);
+            if (w > words) words = w;
+            if (D.nx * D.ny > seeds) seeds = D.nx * D.ny;
+        }
+    if (4L * words > 200L * 1024) return PGM_OK;
+    *handled = true;
+    if (seeds == 0) return PGM_OK;
+    const int groups = (seeds + IN_SB - 1) / IN_SB;
+    return nch == 2 ? launch_in<2>(B, mc, groups, 4 * words, st)
+                    : launch_in<6>(B, mc, groups, 4 * words, st);
+}
+
+}  // namespace pgm

@@ -653,6 +653,9 @@ pgm_status launch_init(const LvlBatch& B, const MatchConst& mc, int nch, int max
     (void)maxP;
     if (max_seeds <= 0) return PGM_OK;
     KScope ks(PGM_K_INIT, st);
+    bool handled = false;
+    const pgm_status r = launch_init_tile(B, mc, nch, &handled, st);
+    if (r != PGM_OK || handled) return r;
     dim3 g(max_seeds, 2, B.n);
     if (nch == 2) {
         if (mc.norm == 0) k_init<2, 0><<<g, 256, 0, st>>>(B, mc);

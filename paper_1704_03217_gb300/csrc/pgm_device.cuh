@@ -159,6 +159,10 @@ pgm_status launch_consist(const LvlBatch& B, const MatchConst& mc, int max_seeds
 pgm_status launch_transfer(const XferBatch& X, int max_seeds, cudaStream_t st);
 pgm_status launch_box(const LvlBatch& B, int nch, int max_pixels, cudaStream_t st);
 // pm_tile.cu: *handled = false when the staged tile would not fit in shared memory
+// exhaustive init, squared L2, target image staged in shared memory;
+// *handled = false when it does not apply (the caller uses the direct kernel)
+pgm_status launch_init_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
+                            cudaStream_t st);
 // true when the tile search kernel takes this batch (it then also does the
 // cost refresh of a visit's first iteration, MatchConst::refresh)
 bool pm_tile_fits(const LvlBatch& B, const MatchConst& mc, int nch);
