@@ -299,7 +299,8 @@ __host__ __device__ inline void pp_word(const PpGeom& g, int P, int m, int l, in
 struct __align__(16) SeedRec {      // one active seed of a staged tile
     int s, px, py, f;               // seed index (-1: none), centre, flags
     int u, nb0, nb1, K;             // current match; propagated candidates to score; search count
-    int r0, r1, pad0, pad1;         // random-search offsets k = 0, 1 (packed like u)
+    int r0, r1, pad0, pad1;         // random-search offsets k = 0, 1 (packed like u); flags as read
+    int wu, w0, w1, pad2;           // window slots (pp_slot) of u, nb0, nb1
     unsigned long long cost, sa;    // current cost, sum |a|^2 of the reference patch
 };
 
@@ -436,6 +437,7 @@ __device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& 
         SeedRec R;
         R.s = -1; R.px = 0; R.py = 0; R.f = 0; R.u = 0; R.nb0 = NO_CAND; R.nb1 = NO_CAND; R.K = 0;
         R.r0 = 0; R.r1 = 0; R.pad0 = 0; R.pad1 = 0; R.cost = INF; R.sa = 0;
+        R.wu = -1; R.w0 = -1; R.w1 = -1; R.pad2 = 0;
         if (i < D.nx && j < D.ny) {
             const int s = j * D.nx + i;
             const int ni = i - sx, nj = j - sy;
@@ -479,7 +481,6 @@ __device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& 
                 R.r1 = pack_u(rs_off(r.z, 1, mc.rs_W, mc.rs_mode), rs_off(r.w, 1, mc.rs_W, mc.rs_mode));
             }
         }
-        rec[a] = R;
         // window centre: median of the valid current matches, ranked by (value, lane)
         const bool v = R.s >= 0 && (R.f & F_VALID);
         const unsigned vm = __ballot_sync(FULL, v);
@@ -498,15 +499,33 @@ __device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& 
         const unsigned my = __ballot_sync(FULL, v && ry == nv / 2);
         const int medx = __shfl_sync(FULL, ux, mx ? __ffs(mx) - 1 : 0);
         const int medy = __shfl_sync(FULL, uy, my ? __ffs(my) - 1 : 0);
+        // the window slots of the candidates known now (the current match
+        // and the propagated ones)
+        const int wx0 = nv > 0 ? mc.c + sig * i0 - h + medx - rho - mc.slack : 0;
+        const int wy0 = nv > 0 ? mc.c + sig * j0 - h + medy - rho - mc.slack : 0;
+        const int shw = ((wx0 * WPP) % 4 + 4) % 4, shs = (wx0 + h) & 1;
+        auto slot = [&](int32_t cu) {
+            const int x0 = R.px + lo16((uint32_t)cu) - h - wx0;
+            const int y0 = R.py + hi16((uint32_t)cu) - h - wy0;
+            if (nv == 0 || cu == NO_CAND || x0 < 0 || y0 < 0 || x0 + P > G.win_w || y0 + P > G.win_h)
+                return -1;
+            return (int)(4u * (unsigned)(y0 * G.spw + shw + x0 * WPP)) |
+                   ((y0 * G.cwp + shs + x0) << 16);
+        };
+        R.wu = slot(R.u);
+        R.w0 = slot(R.nb0);
+        R.w1 = slot(R.nb1);
+        R.pad2 = 0;
+        rec[a] = R;
         if (lane == 0) {
             TileHdr H;
             H.pair = pair; H.dir = dir; H.i0 = i0; H.j0 = j0; H.rx0 = rx0;
             H.use_win = nv > 0;
-            H.wx0 = nv > 0 ? mc.c + sig * i0 - h + medx - rho - mc.slack : 0;
-            H.wy0 = nv > 0 ? mc.c + sig * j0 - h + medy - rho - mc.slack : 0;
+            H.wx0 = wx0;
+            H.wy0 = wy0;
             H.shr = shr;
-            H.shw = ((H.wx0 * WPP) % 4 + 4) % 4;
-            H.shs = (H.wx0 + h) & 1;
+            H.shw = shw;
+            H.shs = shs;
             H.pad = 0;
             *hdr = H;
             *next = 0;
@@ -577,64 +596,67 @@ struct PpLay {
     static constexpr int NB = M - A0 > 0 ? M - A0 : 1;
 };
 
-// Cost of target centre (qx, qy) for the reference words b: from the staged
-// window when the patch lies inside it, else from global memory with the
-// border replicated.  SPW > 0: the window pitch as a constant.
+// Window slot of target centre (qx, qy): the byte offset of its patch
+// corner from the window start in the low 16 bits and the index of its sum
+// |b|^2 above, or -1 when the patch is not inside the staged window.
+__device__ __forceinline__ int pp_slot(const PpGeom& G, const TileHdr& H, int P, int wpp, int qx,
+                                       int qy) {
+    const int x0 = qx - P / 2 - H.wx0, y0 = qy - P / 2 - H.wy0;
+    if (!H.use_win || x0 < 0 || y0 < 0 || x0 + P > G.win_w || y0 + P > G.win_h) return -1;
+    return (int)(4u * (unsigned)(y0 * G.spw + H.shw + x0 * wpp)) | ((y0 * G.cwp + H.shs + x0) << 16);
+}
+
+// Cross term <a, b> of the reference words b with the target patch whose
+// corner is at shared byte address `base` (window pitch SPW > 0 as a
+// constant, else G.spw).
+template <int M, int NA, int SPW>
+__device__ __forceinline__ long long pp_dot_win(const int (&b)[M],
+                                                const Offs<PpLay<M, NA>::NB>& off,
+                                                const PpGeom& G, unsigned base, int lane) {
+    constexpr int A0 = PpLay<M, NA>::A0;
+    const int spw = SPW > 0 ? SPW : G.spw;
+    const unsigned basel = base + 4u * (unsigned)lane;
+    int l0 = 0, l1 = 0, h0 = 0, h1 = 0;                 // two chains each
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const unsigned addr = m < A0 ? basel + 4u * (unsigned)(m * spw) : base + off.at(m - A0);
+        const int v = lds32(addr);
+        if (m & 1) { l1 = __dp2a_lo(v, b[m], l1); h1 = __dp2a_hi(v, b[m], h1); }
+        else { l0 = __dp2a_lo(v, b[m], l0); h0 = __dp2a_hi(v, b[m], h0); }
+    }
+    const int sl = __reduce_add_sync(FULL, l0 + l1), sh = __reduce_add_sync(FULL, h0 + h1);
+    return (long long)sh * 128 + (long long)sl;
+}
+
+// The same from global memory with the border replicated (a patch outside
+// the staged window).
 template <int NCH, int M, int NA, int SPW>
-__device__ __forceinline__ unsigned long long pp_cost(const int (&b)[M],
-                                                      const Offs<PpLay<M, NA>::NB>& off,
-                                                      const DirLvl& D, const PpGeom& G,
-                                                      const TileHdr& H, unsigned a_tw,
-                                                      unsigned a_sb, unsigned long long sa, int qx,
-                                                      int qy, int lane, unsigned& n_glob) {
+__device__ __forceinline__ long long pp_dot_glob(const int (&b)[M],
+                                                 const Offs<PpLay<M, NA>::NB>& off,
+                                                 const DirLvl& D, const PpGeom& G, int qx, int qy,
+                                                 int lane) {
     constexpr int WPP = NCH / 2, A0 = PpLay<M, NA>::A0;
-    const int P = D.P, h = P / 2, spw = SPW > 0 ? SPW : G.spw;
-    const int x0 = qx - h - H.wx0, y0 = qy - h - H.wy0;
-    unsigned long long sb;
-    int sl, sh;
-    if (H.use_win && x0 >= 0 && y0 >= 0 && x0 + P <= G.win_w && y0 + P <= G.win_h) {
-        sb = lds64(a_sb + 8u * (unsigned)(y0 * G.cwp + H.shs + x0));
-        const unsigned base = a_tw + 4u * (unsigned)(y0 * spw + H.shw + x0 * WPP);
-        const unsigned basel = base + 4u * (unsigned)lane;
-        int l0 = 0, l1 = 0, l2 = 0, l3 = 0, h0 = 0, h1 = 0, h2 = 0, h3 = 0;   // four chains each
+    const int h = D.P / 2, spw = SPW > 0 ? SPW : G.spw;
+    const int pitchw = D.tgt_pitch >> 1;
+    const uint32_t* t32 = reinterpret_cast<const uint32_t*>(D.tgt);
+    int sl = 0, sh = 0;
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const unsigned addr = m < A0 ? basel + 4u * (unsigned)(m * spw) : base + off.at(m - A0);
-            const int v = lds32(addr);
-            switch (m & 3) {
-                case 0: l0 = __dp2a_lo(v, b[m], l0); h0 = __dp2a_hi(v, b[m], h0); break;
-                case 1: l1 = __dp2a_lo(v, b[m], l1); h1 = __dp2a_hi(v, b[m], h1); break;
-                case 2: l2 = __dp2a_lo(v, b[m], l2); h2 = __dp2a_hi(v, b[m], h2); break;
-                default: l3 = __dp2a_lo(v, b[m], l3); h3 = __dp2a_hi(v, b[m], h3); break;
-            }
+    for (int m = 0; m < M; ++m) {
+        int row = m, col = lane;
+        if (m >= A0) {
+            const int o = (int)(off.at(m - A0) >> 2);
+            row = o / spw;
+            col = o - row * spw;
         }
-        sl = (l0 + l1) + (l2 + l3);
-        sh = (h0 + h1) + (h2 + h3);
-    } else {
-        sb = D.sb2[(size_t)qy * D.tw + qx];
-        const int pitchw = D.tgt_pitch >> 1;
-        const uint32_t* t32 = reinterpret_cast<const uint32_t*>(D.tgt);
-        sl = 0;
-        sh = 0;
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            int row = m, col = lane;
-            if (m >= A0) {
-                const int o = (int)(off.at(m - A0) >> 2);
-                row = o / spw;
-                col = o - row * spw;
-            }
-            const int pix = col / WPP, wi = col - pix * WPP;
-            const int x = clampi(qx - h + pix, 0, D.tw - 1), y = clampi(qy - h + row, 0, D.th - 1);
-            const int v = (int)__ldg(t32 + (size_t)y * pitchw + (size_t)x * WPP + wi);
-            sl = __dp2a_lo(v, b[m], sl);
-            sh = __dp2a_hi(v, b[m], sh);
-        }
-        ++n_glob;
+        const int pix = col / WPP, wi = col - pix * WPP;
+        const int x = clampi(qx - h + pix, 0, D.tw - 1), y = clampi(qy - h + row, 0, D.th - 1);
+        const int v = (int)__ldg(t32 + (size_t)y * pitchw + (size_t)x * WPP + wi);
+        sl = __dp2a_lo(v, b[m], sl);
+        sh = __dp2a_hi(v, b[m], sh);
     }
     sl = __reduce_add_sync(FULL, sl);
     sh = __reduce_add_sync(FULL, sh);
-    return xcost(sa, sb, (long long)sh * 128 + (long long)sl);
+    return (long long)sh * 128 + (long long)sl;
 }
 
 // Consumer warps: the active seeds of the tile in the buffer at `buf`, taken
@@ -687,25 +709,21 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
                 b[m] &= m < G.nA ? -1 : (m < G.M - 1 ? mask_b : (m == G.M - 1 ? mask_last : 0));
             }
         }
-        // one loop over the candidate sequence (a single inlined cost site):
-        // c = -1: the current match (cost refresh); c = 0, 1: propagated
-        // matches (Eq. 4); c >= 2: random search (Eq. 5) around the match held
-        // after propagation
+        // one loop over the candidate sequence (one inlined cost site each for
+        // the window and for global memory): c = -1: the current match (cost
+        // refresh); c = 0, 1: propagated matches (Eq. 4); c >= 2: random
+        // search (Eq. 5) around the match held after propagation.  The first
+        // three come with their window slots.
         int ux0 = 0, uy0 = 0;
         uint4 r = make_uint4(0, 0, 0, 0);
 #pragma unroll 1
         for (int c = (mc.refresh && have) ? -1 : 0; c < 2 + R.K; ++c) {
             int32_t cu;
-            int qx, qy;
-            if (c < 0) {
-                cu = R.u;
-                qx = R.px + lo16((uint32_t)cu);
-                qy = R.py + hi16((uint32_t)cu);
-                --n_eval;                           // counted as a refresh, not a search
-                ++n_cost;
-            } else if (c < 2) {
-                cu = c ? R.nb1 : R.nb0;
+            int qx, qy, slot;
+            if (c < 2) {
+                cu = c < 0 ? R.u : (c ? R.nb1 : R.nb0);
                 if (cu == NO_CAND) continue;
+                slot = c < 0 ? R.wu : (c ? R.w1 : R.w0);
                 qx = R.px + lo16((uint32_t)cu);
                 qy = R.py + hi16((uint32_t)cu);
             } else {
@@ -733,10 +751,20 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
                 qy = R.py + uy0 + dy;
                 if (!inside(D, qx, qy)) continue;
                 cu = pack_u(ux0 + dx, uy0 + dy);
+                slot = pp_slot(G, H, P, WPP, qx, qy);
             }
-            ++n_eval;
-            const unsigned long long cst = pp_cost<NCH, M, NA, SPW>(b, off, D, G, H, a_tw, a_sb,
-                                                                    R.sa, qx, qy, lane, n_glob);
+            if (c < 0) ++n_cost; else ++n_eval;
+            unsigned long long sb;
+            long long cr;
+            if (slot >= 0) {
+                sb = lds64(a_sb + 8u * (unsigned)(slot >> 16));
+                cr = pp_dot_win<M, NA, SPW>(b, off, G, a_tw + (unsigned)(slot & 0xffff), lane);
+            } else {
+                sb = D.sb2[(size_t)qy * D.tw + qx];
+                cr = pp_dot_glob<NCH, M, NA, SPW>(b, off, D, G, qx, qy, lane);
+                ++n_glob;
+            }
+            const unsigned long long cst = xcost(R.sa, sb, cr);
             if (cst < bc) { bc = cst; bu = cu; have = true; }
         }
         if (lane == 0) {
@@ -1078,7 +1106,8 @@ static bool pp_plan(const LvlBatch& B, const MatchConst& mc, int nch, PtSched* S
         S[d].ndir = 1;
         G[d] = pp_geom(nch, B.d[0][d].P, mc.sigma, mc.rs_W, mc.slack);
         if (G[d].M > PP_MMAX || 4L * ((long)(B.d[0][d].P - 1) * G[d].spw + G[d].wprp) >= 65536L ||
-            2L * G[d].words * 4 > 200L * 1024)
+            2L * G[d].words * 4 > 200L * 1024 || 4L * G[d].spw * G[d].win_h >= 65536L ||
+            (long)G[d].cwp * G[d].ch >= 32768L)
             ok = false;
     }
     for (int k = 0; k < B.n; ++k)
