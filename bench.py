@@ -107,9 +107,11 @@ def run_reference(a):
 
 
 # ------------------------------------------------------- ncu traffic record
-def pm_traffic_per_launch(pairs):
-    """DRAM bytes per k_pm_t launch from the committed ncu record, scaled to
-    `pairs` per step; None when the kernel source changed since the capture."""
+def pm_traffic_per_launch(pairs, launches):
+    """DRAM bytes per k_pm_t launch: the committed ncu record's bytes over all
+    search launches of one step, scaled to `pairs` per step and divided by
+    this step's `launches`; None when the kernel source changed since the
+    capture."""
     import hashlib
     rec = os.path.join(ROOT, "profiles", "k_pm_t_traffic.json")
     src = os.path.join(ROOT, "paper_1704_03217_gb300", "csrc", "pm_tile.cu")
@@ -118,9 +120,9 @@ def pm_traffic_per_launch(pairs):
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except (OSError, ValueError):
         return None
-    if r.get("pm_tile_sha256") != h:
+    if r.get("pm_tile_sha256") != h or "dram_bytes_per_step" not in r or launches <= 0:
         return None
-    return r["dram_bytes_per_launch"] * pairs / r["pairs"]
+    return r["dram_bytes_per_step"] * pairs / r["pairs"] / launches
 
 
 # ------------------------------------------------------------- multi-rank
@@ -316,7 +318,7 @@ def run_ours(a):
     achieved_tmac = el_per_launch / (pm_launch_ms * 1e-3) / 1e12
     l1_gbs = 2 * el_per_launch / (pm_launch_ms * 1e-3) / 1e9
     l1_peak = sms * 128 * sm_mhz * 1e6 / 1e9
-    traffic = pm_traffic_per_launch(B)
+    traffic = pm_traffic_per_launch(B, kernel_launches["pm"])
 
     variants = {}
     if not a.no_variants:
