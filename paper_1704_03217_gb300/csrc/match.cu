@@ -92,10 +92,11 @@ __device__ __forceinline__ unsigned long long warp_cost(const Ref<NCH, PPL>& R, 
 // replicated borders (the sums |a|^2 and |b|^2 of Eq. 3 expanded), exact in
 // uint64 (N itself fits 32 bits: 6 values of at most 24480^2).  A CTA makes a
 // BOX_TW x BOX_TH block of one map: N over the block and a halo of P / 2
-// (clamped coordinates) into shared memory, then row sums, then column sums.
+// (clamped coordinates) into shared memory, then running row sums over runs
+// of BOX_RUN outputs, then running column sums the same way.
 // blockIdx.y = 2 * direction + (0: target image -> sb2, 1: reference ->
 // sa2img); blockIdx.x = block of that map (the grid covers the largest map).
-constexpr int BOX_TW = 32, BOX_TH = 16, BOX_H = MAXP / 2;
+constexpr int BOX_TW = 64, BOX_TH = 32, BOX_H = MAXP / 2, BOX_RUN = 8;
 template <int NCH>
 __global__ void __launch_bounds__(256) k_box(const __grid_constant__ LvlBatch B) {
     __shared__ uint32_t sN[BOX_TH + 2 * BOX_H][BOX_TW + 2 * BOX_H];
@@ -124,20 +125,35 @@ __global__ void __launch_bounds__(256) k_box(const __grid_constant__ LvlBatch B)
         sN[r][c] = n;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < ih * BOX_TW; e += blockDim.x) {
-        const int r = e / BOX_TW, c = e - r * BOX_TW;
+    // row sums: thread -> (row, run of BOX_RUN outputs); consecutive threads
+    // take consecutive runs of one row
+    constexpr int RUNS_X = BOX_TW / BOX_RUN;
+    for (int e = threadIdx.x; e < ih * RUNS_X; e += blockDim.x) {
+        const int r = e / RUNS_X, c0 = (e - r * RUNS_X) * BOX_RUN;
         unsigned long long s = 0;
-        for (int o = 0; o < P; ++o) s += sN[r][c + o];
-        sR[r][c] = s;
+        for (int o = 0; o < P; ++o) s += sN[r][c0 + o];
+        sR[r][c0] = s;
+#pragma unroll
+        for (int k = 1; k < BOX_RUN; ++k) {
+            s += (unsigned long long)sN[r][c0 + k + P - 1] - sN[r][c0 + k - 1];
+            sR[r][c0 + k] = s;
+        }
     }
     __syncthreads();
+    // column sums: thread -> (column, run of BOX_RUN rows); a warp covers 32
+    // consecutive columns, so the stores of one row are coalesced
     unsigned long long* out = ref ? D.sa2img : D.sb2;
-    for (int e = threadIdx.x; e < BOX_TH * BOX_TW; e += blockDim.x) {
-        const int r = e / BOX_TW, c = e - r * BOX_TW, x = x0 + c, y = y0 + r;
-        if (x >= w || y >= hh) continue;
+    constexpr int RUNS_Y = BOX_TH / BOX_RUN;
+    for (int e = threadIdx.x; e < BOX_TW * RUNS_Y; e += blockDim.x) {
+        const int c = e % BOX_TW, r0 = (e / BOX_TW) * BOX_RUN, x = x0 + c;
         unsigned long long s = 0;
-        for (int o = 0; o < P; ++o) s += sR[r + o][c];
-        out[(size_t)y * w + x] = s;
+        for (int o = 0; o < P; ++o) s += sR[r0 + o][c];
+#pragma unroll
+        for (int k = 0; k < BOX_RUN; ++k) {
+            if (k > 0) s += sR[r0 + k + P - 1][c] - sR[r0 + k - 1][c];
+            const int y = y0 + r0 + k;
+            if (x < w && y < hh) out[(size_t)y * w + x] = s;
+        }
     }
 }
 
