@@ -142,85 +142,99 @@ __global__ void k_convert(const __grid_constant__ PyrBatch B) {
 
 // ----------------------------------------------------------------- Sobel
 // Gx = sum_j s_j sum_i d_i I(x+i, y+j); Gy with the roles of the axes swapped.
-// A CTA makes a 32 x 8 block of one image: the (32 + S - 1) x (8 + S - 1)
-// input pixels of every channel (border replicated) go to shared memory, the
-// horizontal passes (d and s along x) are kept per input row, and the
-// vertical passes finish Gx and Gy (separable and exact in integers).
-constexpr int SB_TW = 32, SB_TH = 8;
+// A CTA of 32 x 8 threads makes a 32 x 16 block of one image (two rows per
+// thread): the (32 + S - 1) x (16 + S - 1) input pixels of every channel
+// (border replicated) go to shared memory, the horizontal passes (d and s
+// along x, both within int16) are kept per input row as one packed word, and
+// the vertical passes finish Gx and Gy (separable and exact in integers).
+constexpr int SB_TW = 32, SB_TH = 16, SB_TY = 8;
+__device__ __forceinline__ int sb_d(int S, int i) {
+    return S == 5 ? (i == 0 ? -1 : i == 1 ? -2 : i == 2 ? 0 : i == 3 ? 2 : 1) : (i - 1);
+}
+__device__ __forceinline__ int sb_s(int S, int i) {
+    return S == 5 ? (i == 0 ? 1 : i == 1 ? 4 : i == 2 ? 6 : i == 3 ? 4 : 1) : (i == 1 ? 2 : 1);
+}
 template <int S, int C>
-__global__ void __launch_bounds__(SB_TW * SB_TH) k_sobel(const __grid_constant__ PyrBatch B,
+__global__ void __launch_bounds__(SB_TW * SB_TY) k_sobel(const __grid_constant__ PyrBatch B,
                                                          int dir_only) {
     constexpr int R = S / 2, IW = SB_TW + S - 1, IH = SB_TH + S - 1;
     __shared__ uint8_t sI[C][IH][IW];
-    __shared__ int sD[C][IH][SB_TW], sS[C][IH][SB_TW];
+    __shared__ uint32_t sH[C][IH][SB_TW];               // (sum d v) low 16, (sum s v) high 16
     const PyrItem& it = B.it[blockIdx.z];
     const int w = it.sw, h = it.sh, row = it.srow;
     const int x0 = blockIdx.x * SB_TW, y0 = blockIdx.y * SB_TH;
     if (x0 >= w || y0 >= h) return;                     // the whole block (uniform)
     const size_t plane = it.splane;
     const uint8_t* in = it.src;
-    const int tid = threadIdx.y * SB_TW + threadIdx.x;
-    for (int e = tid; e < C * IH * IW; e += SB_TW * SB_TH) {
-        const int ch = e / (IH * IW), rc = e - ch * (IH * IW), r = rc / IW, c = rc - r * IW;
-        const int x = clampi(x0 - R + c, 0, w - 1), y = clampi(y0 - R + r, 0, h - 1);
-        sI[ch][r][c] = in[ch * plane + (size_t)y * row + x];
-    }
-    __syncthreads();
-    for (int e = tid; e < C * IH * SB_TW; e += SB_TW * SB_TH) {
-        const int ch = e / (IH * SB_TW), rc = e - ch * (IH * SB_TW), r = rc / SB_TW,
-                  c = rc - r * SB_TW;
-        int sd = 0, ss = 0;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < IH; r += SB_TY) {
+        const uint8_t* src = in + (size_t)clampi(y0 - R + r, 0, h - 1) * row;
+        for (int c = tx; c < IW; c += SB_TW) {
+            const int x = clampi(x0 - R + c, 0, w - 1);
 #pragma unroll
-        for (int i = 0; i < S; ++i) {
-            const int v = sI[ch][r][c + i];
-            sd += (S == 5 ? (i == 0 ? -1 : i == 1 ? -2 : i == 2 ? 0 : i == 3 ? 2 : 1)
-                          : (i - 1)) * v;
-            ss += (S == 5 ? (i == 0 ? 1 : i == 1 ? 4 : i == 2 ? 6 : i == 3 ? 4 : 1)
-                          : (i == 1 ? 2 : 1)) * v;
+            for (int ch = 0; ch < C; ++ch) sI[ch][r][c] = src[ch * plane + x];
         }
-        sD[ch][r][c] = sd;
-        sS[ch][r][c] = ss;
     }
     __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    if (x >= w || y >= h) return;
-    int g[2 * C];
+    for (int r = ty; r < IH; r += SB_TY)
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch) {
+            int sd = 0, ss = 0;
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                const int v = sI[ch][r][tx + i];
+                sd += sb_d(S, i) * v;
+                ss += sb_s(S, i) * v;
+            }
+            sH[ch][r][tx] = (uint32_t)(uint16_t)sd | ((uint32_t)ss << 16);
+        }
+    __syncthreads();
+    const int x = x0 + tx;
+    int g[2][2 * C];
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) {
-        int gx = 0, gy = 0;
+        int gx0 = 0, gy0 = 0, gx1 = 0, gy1 = 0;
 #pragma unroll
-        for (int j = 0; j < S; ++j) {
-            const int sj = S == 5 ? (j == 0 ? 1 : j == 1 ? 4 : j == 2 ? 6 : j == 3 ? 4 : 1)
-                                  : (j == 1 ? 2 : 1);
-            const int dj = S == 5 ? (j == 0 ? -1 : j == 1 ? -2 : j == 2 ? 0 : j == 3 ? 2 : 1)
-                                  : (j - 1);
-            gx += sj * sD[ch][threadIdx.y + j][threadIdx.x];
-            gy += dj * sS[ch][threadIdx.y + j][threadIdx.x];
+        for (int j = 0; j <= S; ++j) {                  // rows 2 ty .. 2 ty + S
+            const uint32_t v = sH[ch][2 * ty + j][tx];
+            const int sd = (int)(int16_t)(v & 0xffffu), ss = (int)(v >> 16);
+            if (j < S) { gx0 += sb_s(S, j) * sd; gy0 += sb_d(S, j) * ss; }
+            if (j > 0) { gx1 += sb_s(S, j - 1) * sd; gy1 += sb_d(S, j - 1) * ss; }
         }
-        if (dir_only == 1) {                  // direction only: G ./ |G|
-            gx = (gx > 0) - (gx < 0);
-            gy = (gy > 0) - (gy < 0);
-        } else if (dir_only == 2) {           // 8-sector angle as an integer unit vector
-            const int ax = abs(gx), ay = abs(gy);
-            int cx, cy;
-            if (gx == 0 && gy == 0) { cx = 0; cy = 0; }
-            else if (408 * ay <= 169 * ax) { cx = gx > 0 ? 64 : -64; cy = 0; }
-            else if (408 * ax <= 169 * ay) { cx = 0; cy = gy > 0 ? 64 : -64; }
-            else { cx = gx > 0 ? 45 : -45; cy = gy > 0 ? 45 : -45; }
-            gx = cx; gy = cy;
+        int gx[2] = {gx0, gx1}, gy[2] = {gy0, gy1};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            int a = gx[k], b2 = gy[k];
+            if (dir_only == 1) {                  // direction only: G ./ |G|
+                a = (a > 0) - (a < 0);
+                b2 = (b2 > 0) - (b2 < 0);
+            } else if (dir_only == 2) {           // 8-sector angle as an integer unit vector
+                const int ax = abs(a), ay = abs(b2);
+                int cx, cy;
+                if (a == 0 && b2 == 0) { cx = 0; cy = 0; }
+                else if (408 * ay <= 169 * ax) { cx = a > 0 ? 64 : -64; cy = 0; }
+                else if (408 * ax <= 169 * ay) { cx = 0; cy = b2 > 0 ? 64 : -64; }
+                else { cx = a > 0 ? 45 : -45; cy = b2 > 0 ? 45 : -45; }
+                a = cx; b2 = cy;
+            }
+            g[k][ch] = a;
+            g[k][C + ch] = b2;
         }
-        g[ch] = gx;
-        g[C + ch] = gy;
     }
-    // pixel-interleaved int16, written as 32-bit words (2C is even)
-    // and the same words with every value a split into signed bytes
-    // a = 128 a_h + a_l (a_l in [-64, 63]) for the dp2a cross products
-    const size_t w0 = ((size_t)y * it.drow + (size_t)x * 2 * C) / 2;
-    uint32_t* dst = reinterpret_cast<uint32_t*>(it.dst) + w0;
+    // pixel-interleaved int16, written as 32-bit words (2C is even), and the
+    // same words with every value a split into signed bytes a = 128 a_h + a_l
+    // (a_l in [-64, 63]) for the dp2a cross products
 #pragma unroll
-    for (int k = 0; k < C; ++k) {
-        dst[k] = (uint32_t)(uint16_t)g[2 * k] | ((uint32_t)(uint16_t)g[2 * k + 1] << 16);
-        it.split[w0 + k] = (uint32_t)split_bytes(g[2 * k], g[2 * k + 1]);
+    for (int k = 0; k < 2; ++k) {
+        const int y = y0 + 2 * ty + k;
+        if (x >= w || y >= h) continue;
+        const size_t w0 = ((size_t)y * it.drow + (size_t)x * 2 * C) / 2;
+        uint32_t* dst = reinterpret_cast<uint32_t*>(it.dst) + w0;
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            dst[q] = (uint32_t)(uint16_t)g[k][2 * q] | ((uint32_t)(uint16_t)g[k][2 * q + 1] << 16);
+            it.split[w0 + q] = (uint32_t)split_bytes(g[k][2 * q], g[k][2 * q + 1]);
+        }
     }
 }
 
@@ -300,13 +314,14 @@ pgm_status launch_pyramid_batch(const pgm_params* p, int n, const PyrPlan* plans
                     it.dst = pyrs[base + k] + pp.desc_off[s][l]; it.drow = pp.desc_row[l];
                     it.split = reinterpret_cast<uint32_t*>(pyrs[base + k] + pp.split_off[s][l]);
                 }
-                dim3 g = grid(mw, mh, m);
+                dim3 g((mw + SB_TW - 1) / SB_TW, (mh + SB_TH - 1) / SB_TH, m);
+                const dim3 sblk(SB_TW, SB_TY);
                 if (p->sobel == 5) {
-                    if (C == 1) k_sobel<5, 1><<<g, blk, 0, st>>>(B, dir_only);
-                    else k_sobel<5, 3><<<g, blk, 0, st>>>(B, dir_only);
+                    if (C == 1) k_sobel<5, 1><<<g, sblk, 0, st>>>(B, dir_only);
+                    else k_sobel<5, 3><<<g, sblk, 0, st>>>(B, dir_only);
                 } else {
-                    if (C == 1) k_sobel<3, 1><<<g, blk, 0, st>>>(B, dir_only);
-                    else k_sobel<3, 3><<<g, blk, 0, st>>>(B, dir_only);
+                    if (C == 1) k_sobel<3, 1><<<g, sblk, 0, st>>>(B, dir_only);
+                    else k_sobel<3, 3><<<g, sblk, 0, st>>>(B, dir_only);
                 }
             }
         if (cudaGetLastError() != cudaSuccess) return PGM_ERR_CUDA;
