@@ -208,7 +208,7 @@ __device__ __forceinline__ unsigned long long tile_cost(
 // target, a repeat of the current match or of the other candidate), draw the
 // first Philox block of every seed for the random search (Eq. 5), place the
 // target window at the median match, and stage the reference region, the
-// window and the window's sums |b|^2.  Rows move as bulk asynchronous copies
+// window and the window's sums |b|^2; then they join the consumers on tile n.  Rows move as bulk asynchronous copies
 // (one per row, 16-byte aligned, completing on the buffer's mbarrier); the
 // words outside the image (replicated border) and a ragged row end go by
 // 4-byte copies.  A barrier per tile hands the buffers over.
@@ -837,7 +837,8 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
                                 s_rec[cur ^ 1], &s_hdr[cur ^ 1], &s_next[cur ^ 1], s_geom, pend_bar,
                                 warp - PP_CONS, lane);
             }
-        } else {
+        }
+        {   // every warp: the current tile's seeds (producers join once done)
             const TileHdr H = s_hdr[cur];
             if (!__all_sync(FULL, mbar_wait(bar0 + 8u * (unsigned)cur, (unsigned)(n >> 1) & 1u))) {
                 if (lane == 0) {
