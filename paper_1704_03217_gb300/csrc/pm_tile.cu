@@ -208,10 +208,11 @@ __device__ __forceinline__ unsigned long long tile_cost(
 // target, a repeat of the current match or of the other candidate), draw the
 // first Philox block of every seed for the random search (Eq. 5), place the
 // target window at the median match, and stage the reference region, the
-// window and the window's sums |b|^2; then they join the consumers on tile n.  Rows move as bulk asynchronous copies
-// (one per row, 16-byte aligned, completing on the buffer's mbarrier); the
-// words outside the image (replicated border) and a ragged row end go by
-// 4-byte copies.  A barrier per tile hands the buffers over.
+// window and the window's sums |b|^2; then they join the consumers on tile
+// n.  Rows move as bulk asynchronous copies (one per row, 16-byte aligned,
+// completing on the buffer's mbarrier); the words outside the image
+// (replicated border) and a ragged row end go by 4-byte copies.  A barrier
+// per tile hands the buffers over.
 //
 // Shared layout.  Every staged row is 16-byte aligned: shared word j of a
 // row holds image word x0 * wpp - sh + j, with sh = x0 * wpp mod 4.  The
