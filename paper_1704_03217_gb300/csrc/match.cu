@@ -110,19 +110,21 @@ __global__ void __launch_bounds__(256) k_box(const __grid_constant__ LvlBatch B)
     const int16_t* img = ref ? D.ref : D.tgt;
     const int pitch = ref ? D.ref_pitch : D.tgt_pitch;
     const int iw = BOX_TW + P - 1, ih = BOX_TH + P - 1;
-    for (int e = threadIdx.x; e < iw * ih; e += blockDim.x) {
-        const int r = e / iw, c = e - r * iw;
-        const int x = clampi(x0 - h + c, 0, w - 1), y = clampi(y0 - h + r, 0, hh - 1);
-        const uint32_t* px =
-            reinterpret_cast<const uint32_t*>(img + (size_t)y * pitch) + (size_t)x * (NCH / 2);
-        uint32_t n = 0;
+    // a warp per row, lanes along it
+    for (int r = threadIdx.x >> 5; r < ih; r += blockDim.x >> 5) {
+        const uint32_t* row = reinterpret_cast<const uint32_t*>(
+            img + (size_t)clampi(y0 - h + r, 0, hh - 1) * pitch);
+        for (int c = threadIdx.x & 31; c < iw; c += 32) {
+            const uint32_t* px = row + (size_t)clampi(x0 - h + c, 0, w - 1) * (NCH / 2);
+            uint32_t n = 0;
 #pragma unroll
-        for (int c2 = 0; c2 < NCH / 2; ++c2) {
-            const uint32_t v = __ldg(px + c2);
-            const int a = lo16(v), b = hi16(v);
-            n += (uint32_t)(a * a) + (uint32_t)(b * b);
+            for (int c2 = 0; c2 < NCH / 2; ++c2) {
+                const uint32_t v = __ldg(px + c2);
+                const int a = lo16(v), b = hi16(v);
+                n += (uint32_t)(a * a) + (uint32_t)(b * b);
+            }
+            sN[r][c] = n;
         }
-        sN[r][c] = n;
     }
     __syncthreads();
     // row sums: thread -> (row, run of BOX_RUN outputs); consecutive threads
