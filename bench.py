@@ -375,6 +375,10 @@ def run_ours(a):
                               * B * max(3, a.steps // 4) / (tot * 1e-3) / 1e9}
             del mv
 
+    batched = None
+    if not a.no_variants and rank == 0:
+        batched = run_batched(api, prm, dev)
+
     serving = None
     if a.serve > 0 and rank == 0:
         serving = run_serving(api, prm, a.serve, dev)
@@ -411,6 +415,7 @@ def run_ours(a):
                                "init": sum(sum(e["init"]) for e in ev_counts),
                                "pm_global": sum(sum(e["pm_global"]) for e in ev_counts)},
             "variants": variants,
+            "batched": batched,
             "serving": serving,
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -419,6 +424,73 @@ def run_ours(a):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_batched(api, prm, dev, n=64, reps=3):
+    """The mixed-size batch: n pairs of sizes drawn uniformly from 320x240,
+    640x480, 1024x436, 1242x375 and 1920x1080, from resident device images,
+    (a) in shared launches (batched pyramids, matching in launches of up to 32
+    pairs, batched filter) captured once as a CUDA graph and replayed, and
+    (b) in the plain form: each pair's two pyramids, its match and its filter
+    launched one pair after the other.  Pairs/s from CUDA events over `reps`
+    runs each; both forms must export the same matches."""
+    import numpy as np
+    import torch
+    from paper_1704_03217_gb300 import synth
+    rng = np.random.default_rng(77)
+    pairs = []
+    for _ in range(n):                       # RGB pairs for the colour descriptor
+        w, h = synth.BATCH_SIZES[int(rng.integers(len(synth.BATCH_SIZES)))]
+        pairs.append(synth.sintel_like_pair(int(rng.integers(1 << 30)), w, h,
+                                            t_max=min(150.0, w / 8))[:2])
+    i1 = [torch.from_numpy(np.ascontiguousarray(p[0])).to(dev) for p in pairs]
+    i2 = [torch.from_numpy(np.ascontiguousarray(p[1])).to(dev) for p in pairs]
+    P1 = [api.Pyramid(prm, x.shape[1], x.shape[0], dev) for x in i1]
+    P2 = [api.Pyramid(prm, x.shape[1], x.shape[0], dev) for x in i2]
+    W = [api.Workspace(prm, q1.w, q1.h, q2.w, q2.h, dev) for q1, q2 in zip(P1, P2)]
+    caps = [w.layout(0, 0)[0] * w.layout(0, 0)[1] for w in W]
+    rows = [torch.empty((max(c, 1), 4), dtype=torch.int32, device=dev) for c in caps]
+    cnt = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(n)]
+    sids = list(range(n))
+
+    def shared():
+        api.build_pyramids(prm, i1 + i2, P1 + P2)
+        api.match_batch(prm, P1, P2, sids, W)
+        api.filter_batch(prm, W, rows, cnt)
+
+    def plain():
+        for k in range(n):
+            P1[k].build(i1[k])
+            P2[k].build(i2[k])
+            api.match(prm, P1[k], P2[k], sids[k], W[k])
+            api.filter_into(prm, W[k], rows[k], cnt[k])
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    shared()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        shared()
+    t_shared = timed(graph.replay)
+    got_shared = [int(c.item()) for c in cnt]
+    t_plain = timed(plain)
+    got_plain = [int(c.item()) for c in cnt]
+    assert got_shared == got_plain, "batched and single-pair matches differ"
+    sizes = sorted({"%dx%d" % (p[0].shape[1], p[0].shape[0]) for p in pairs})
+    return {"pairs": n, "sizes": sizes, "data": "synthetic Sintel-like RGB pairs",
+            "batched_ms": t_shared, "batched_pairs_per_s": n / (t_shared * 1e-3),
+            "plain_ms": t_plain, "plain_pairs_per_s": n / (t_plain * 1e-3),
+            "speedup": t_plain / t_shared}
 
 
 def run_serving(api, prm, n, dev):
