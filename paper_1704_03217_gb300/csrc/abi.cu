@@ -219,6 +219,35 @@ void fill_dir(const pgm_params* p, const PairCtx& c, int l, int d, DirLvl* D) {
     D->sa2img = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sa2img[l][d]);
 }
 
+// The auxiliary stream of this thread on the current device, with its fork
+// and per-level join events (created once per thread and device; the
+// library allocates no device memory for them).
+struct Aux {
+    int dev = -1;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t lvl[MAXL] = {};
+};
+static thread_local Aux g_aux;
+
+static pgm_status aux_get(Aux** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PGM_ERR_CUDA;
+    if (g_aux.dev != dev) {
+        Aux a;
+        a.dev = dev;
+        if (cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess)
+            return PGM_ERR_CUDA;
+        for (int l = 0; l < MAXL; ++l)
+            if (cudaEventCreateWithFlags(&a.lvl[l], cudaEventDisableTiming) != cudaSuccess)
+                return PGM_ERR_CUDA;
+        g_aux = a;                   // the previous device's handles are kept alive
+    }
+    *out = &g_aux;
+    return PGM_OK;
+}
+
 pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) {
     Schedule sch;
     make_schedule(p, &sch);
@@ -237,12 +266,26 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
     for (int k = 0; k < n; ++k)           // reset the evaluation counters
         if (cudaMemsetAsync(ctx[k].ws + PGM_WS_EVALS_OFFSET, 0, 8 * PGM_WS_EVALS_COUNT, st) != cudaSuccess)
             return PGM_ERR_CUDA;
+    // per level and direction: box sums of |G|^2 over the target and the
+    // reference patches.  The coarsest level's come first on the caller's
+    // stream; the finer levels' are forked onto an auxiliary stream, where
+    // they overlap the initialisation and the coarse visits, and each is
+    // joined back before the first visit at its level.
+    bool joined[MAXL];
+    for (int l = 0; l < MAXL; ++l) joined[l] = true;
+    Aux* aux = nullptr;
     if (p->norm == PGM_L2SQ) {
-        // per level and direction: box sums of |G|^2 over the target patches
         bool needed[MAXL] = {false};
         for (int v = 0; v < sch.n; ++v) needed[sch.level[v]] = true;
-        for (int l = 0; l < p->levels; ++l) {
+        const int l0 = sch.level[0];
+        for (int l = p->levels - 1; l >= 0; --l) {
             if (!needed[l]) continue;
+            if (l != l0 && !aux) {
+                pgm_status r = aux_get(&aux);
+                if (r != PGM_OK) return r;
+                if (cudaEventRecord(aux->fork, st) != cudaSuccess ||
+                    cudaStreamWaitEvent(aux->s, aux->fork, 0) != cudaSuccess) return PGM_ERR_CUDA;
+            }
             memset(&B, 0, sizeof(B));
             B.n = n; B.level = l;
             int max_px = 0;
@@ -254,12 +297,20 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
                     np = B.d[k][d].rw * B.d[k][d].rh;
                     if (np > max_px) max_px = np;
                 }
-            pgm_status r = launch_box(B, nch, max_px, st);
+            pgm_status r = launch_box(B, nch, max_px, l == l0 ? st : aux->s);
             if (r != PGM_OK) return r;
+            if (l != l0) {
+                if (cudaEventRecord(aux->lvl[l], aux->s) != cudaSuccess) return PGM_ERR_CUDA;
+                joined[l] = false;
+            }
         }
     }
     for (int v = 0; v < sch.n; ++v) {
         const int l = sch.level[v];
+        if (!joined[l]) {
+            if (cudaStreamWaitEvent(st, aux->lvl[l], 0) != cudaSuccess) return PGM_ERR_CUDA;
+            joined[l] = true;
+        }
         memset(&B, 0, sizeof(B));
         B.n = n; B.level = l; B.visit = v;
         int max_seeds = 0, max_half = 0;
