@@ -11,7 +11,12 @@
 //     wide enough for the random-search square plus a margin, and the sum
 //     |b|^2 of every patch centre inside it.
 // Both are staged in unclamped pixel coordinates with the image border
-// replicated, so the inner loop needs no border tests.
+// replicated, so the inner loop needs no border tests.  A region that lies
+// inside its image moves as one 2D tensor copy (cp.async.bulk.tensor, a
+// tensor map per array and slot); one that needs the replicated border moves
+// row by row (a bulk copy per row plus 4-byte copies for the clamped words).
+// Two producer warps prepare tile n + 1 (seed records, window position,
+// copies) while the other warps score tile n.
 //
 // Lane l owns the words l, l + 32, ... of the flattened patch (P rows of P
 // pixels times the words per pixel, no padding), and the shared row pitch is
@@ -22,6 +27,9 @@
 // exact in integers, with sum |a|^2 per seed and sum |b|^2 per target pixel
 // computed by other kernels of the same visit.
 #include <limits.h>
+#include <mutex>
+
+#include <cuda.h>
 
 #include "match_common.cuh"
 
@@ -273,9 +281,9 @@ __host__ __device__ inline PpGeom pp_geom(int nch, int P, int sigma, int rs_W, i
     g.cw = g.win_w - P + 1;
     g.ch = g.win_h - P + 1;
     g.cwp = (g.cw + 2) & ~1;                           // + 1 centre of alignment shift
-    g.off_win = g.spr * g.ref_h;
-    g.off_sb = g.off_win + g.spw * g.win_h;            // a multiple of 4 words
-    g.words = (g.off_sb + 2 * g.cwp * g.ch + 3) & ~3;
+    g.off_win = (g.spr * g.ref_h + 31) & ~31;          // regions start 128-byte aligned
+    g.off_sb = (g.off_win + g.spw * g.win_h + 31) & ~31;
+    g.words = (g.off_sb + 2 * g.cwp * g.ch + 31) & ~31;
     return g;
 }
 
@@ -313,6 +321,26 @@ struct TileHdr { int pair, dir, i0, j0, rx0, wx0, wy0, use_win, shr, shw, shs, p
 struct PtSched { int nk, total, dir, ndir; int cum[2 * MAXB + 1]; };
 
 constexpr int NO_CAND = INT_MIN;            // no propagated candidate
+
+// Tensor maps of the staged arrays for each slot of a launch (slot k as in
+// PtSched): [0] the reference split words (box spr x ref_h words), [1] the
+// target words (box spw x win_h), [2] the target sums |b|^2 (uint64, box
+// cwp x ch).  A region inside its image moves as one 2D copy; ok[k] = 0, or
+// a region that needs the replicated border, goes row by row.
+constexpr int PP_MAPS = 32;
+struct PtMaps {
+    CUtensorMap m[PP_MAPS][3];
+    int ok[PP_MAPS];
+};
+
+__device__ __forceinline__ void tma2d(unsigned dst, const CUtensorMap* map, int x, int y,
+                                      unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];\n"
+        ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
 
 __device__ __forceinline__ void pp_bar_producers() {
     asm volatile("bar.sync 1, %0;\n" ::"n"(32 * PP_PROD) : "memory");
@@ -403,9 +431,9 @@ __device__ __forceinline__ void mbar_arrive(unsigned bar) {
 // the window sums).
 template <int NCH>
 __device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& mc,
-                                           const PtSched& S, int t, unsigned buf, SeedRec* rec,
-                                           TileHdr* hdr, int* next, const PpGeom* geom,
-                                           unsigned bar, int pw, int lane) {
+                                           const PtSched& S, const PtMaps& TM, int t, unsigned buf,
+                                           SeedRec* rec, TileHdr* hdr, int* next,
+                                           const PpGeom* geom, unsigned bar, int pw, int lane) {
     constexpr int WPP = NCH / 2;
     int lo = 0, hi = S.nk - 1;                   // slot holding tile t:
     while (lo < hi) {                            // the last k with cum[k] <= t
@@ -420,16 +448,24 @@ __device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& 
     const int P = D.P, h = P / 2, sig = mc.sigma;
     const int rx0 = mc.c + sig * i0 - h, ry0 = mc.c + sig * j0 - h;
     const int shr = ((rx0 * WPP) % 4 + 4) % 4;
+    const bool tma = k < PP_MAPS && TM.ok[k] != 0 && (buf & 127u) == 0;
     fence_proxy_async();                         // earlier reads of this buffer come first
 
     if (pw == 1) {
         // the reference region does not depend on the seeds
         const Span sr = pp_span(rx0 * WPP, shr, G.ref_w * WPP, D.rw * WPP);
-        if (lane == 0 && sr.je > sr.jb)
-            mbar_expect_tx(bar, (unsigned)(sr.je - sr.jb) * 4u * (unsigned)G.ref_h);
-        __syncwarp();
-        pp_stage_rows<WPP>(buf, G.spr, D.ref_split, D.ref_pitch >> 1, D.rw, D.rh, ry0, G.ref_h, sr,
-                           bar, lane);
+        if (tma && rx0 >= 0 && rx0 + G.ref_w <= D.rw && ry0 >= 0 && ry0 + G.ref_h <= D.rh) {
+            if (lane == 0) {                     // inside the image: one 2D copy
+                mbar_expect_tx(bar, 4u * (unsigned)(G.spr * G.ref_h));
+                tma2d(buf, &TM.m[k][0], sr.gw0, ry0, bar);
+            }
+        } else {
+            if (lane == 0 && sr.je > sr.jb)
+                mbar_expect_tx(bar, (unsigned)(sr.je - sr.jb) * 4u * (unsigned)G.ref_h);
+            __syncwarp();
+            pp_stage_rows<WPP>(buf, G.spr, D.ref_split, D.ref_pitch >> 1, D.rw, D.rh, ry0, G.ref_h,
+                               sr, bar, lane);
+        }
     } else {
         const int t4 = mc.t & 3;
         const int sx = (t4 == 0 || t4 == 3) ? 1 : -1, sy = (t4 == 0 || t4 == 2) ? 1 : -1;
@@ -482,24 +518,27 @@ __device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& 
                 R.r1 = pack_u(rs_off(r.z, 1, mc.rs_W, mc.rs_mode), rs_off(r.w, 1, mc.rs_W, mc.rs_mode));
             }
         }
-        // window centre: median of the valid current matches, ranked by (value, lane)
+        // window centre: per component, the median of the valid current matches
         const bool v = R.s >= 0 && (R.f & F_VALID);
         const unsigned vm = __ballot_sync(FULL, v);
         const int nv = __popc(vm);
         const int ux = lo16((uint32_t)R.u), uy = hi16((uint32_t)R.u);
-        int rx = 0, ry = 0;
-        for (int o = 0; o < 32; ++o) {
-            const int ox = __shfl_sync(FULL, ux, o), oy = __shfl_sync(FULL, uy, o);
-            if ((vm >> o) & 1) {
-                rx += ox < ux || (ox == ux && o < lane);
-                ry += oy < uy || (oy == uy && o < lane);
-            }
+        // the (nv / 2)-th smallest of the valid components (0-based), one
+        // bit at a time from the top of the order-preserving 16-bit keys
+        const unsigned kx = (unsigned)(ux + 32768), ky = (unsigned)(uy + 32768);
+        unsigned cx = vm, cy = vm;
+        int nx = nv / 2, ny = nv / 2;
+#pragma unroll
+        for (int bit = 15; bit >= 0; --bit) {
+            const unsigned zx = __ballot_sync(FULL, !((kx >> bit) & 1u)) & cx;
+            const unsigned zy = __ballot_sync(FULL, !((ky >> bit) & 1u)) & cy;
+            const int px = __popc(zx), py = __popc(zy);
+            if (nx < px) cx = zx; else { nx -= px; cx &= ~zx; }
+            if (ny < py) cy = zy; else { ny -= py; cy &= ~zy; }
         }
         const int rho = max(1, mc.rs_W);
-        const unsigned mx = __ballot_sync(FULL, v && rx == nv / 2);
-        const unsigned my = __ballot_sync(FULL, v && ry == nv / 2);
-        const int medx = __shfl_sync(FULL, ux, mx ? __ffs(mx) - 1 : 0);
-        const int medy = __shfl_sync(FULL, uy, my ? __ffs(my) - 1 : 0);
+        const int medx = __shfl_sync(FULL, ux, cx ? __ffs(cx) - 1 : 0);
+        const int medy = __shfl_sync(FULL, uy, cy ? __ffs(cy) - 1 : 0);
         // the window slots of the candidates known now (the current match
         // and the propagated ones)
         const int wx0 = nv > 0 ? mc.c + sig * i0 - h + medx - rho - mc.slack : 0;
@@ -536,7 +575,14 @@ __device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& 
     const TileHdr H = *hdr;
     const unsigned win = buf + 4u * (unsigned)G.off_win, sbb = buf + 4u * (unsigned)G.off_sb;
     if (pw == 0) {
-        if (H.use_win) {
+        const bool win_in = H.wx0 >= 0 && H.wx0 + G.win_w <= D.tw && H.wy0 >= 0 &&
+                            H.wy0 + G.win_h <= D.th;
+        if (H.use_win && tma && win_in) {
+            if (lane == 0) {                     // inside the image: one 2D copy
+                mbar_arrive_tx(bar, 4u * (unsigned)(G.spw * G.win_h));
+                tma2d(win, &TM.m[k][1], H.wx0 * WPP - H.shw, H.wy0, bar);
+            }
+        } else if (H.use_win) {
             const Span sw = pp_span(H.wx0 * WPP, H.shw, G.win_w * WPP, D.tw * WPP);
             if (lane == 0) {
                 if (sw.je > sw.jb) mbar_arrive_tx(bar, (unsigned)(sw.je - sw.jb) * 4u * (unsigned)G.win_h);
@@ -555,7 +601,13 @@ __device__ __forceinline__ void pp_produce(const LvlBatch& B, const MatchConst& 
         const bool bulk = H.use_win && (D.tw & 1) == 0;
         unsigned bytes = 0;
         int c_lo = 0;
-        if (bulk) {
+        if (bulk && tma) {
+            // one 2D copy; entries outside the image read as zero (don't-care)
+            if (lane == 0) {
+                mbar_arrive_tx(bar, 8u * (unsigned)(G.cwp * G.ch));
+                tma2d(sbb, &TM.m[k][2], cx0 - H.shs, cy0, bar);
+            }
+        } else if (bulk) {
             const int a0 = cx0 - H.shs;                       // even
             c_lo = max(a0, 0);
             const int c_hi = min(a0 + G.cwp, D.tw);
@@ -792,8 +844,8 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
 template <int NCH, int M, int NA, int SPW, int SPR>
 __global__ void __launch_bounds__(PP_THREADS, 2)
 k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_constant__ PtSched S,
-       const int buf_words) {
-    extern __shared__ __align__(16) uint32_t sm[];
+       const __grid_constant__ PtMaps TM, const int buf_words) {
+    extern __shared__ __align__(128) uint32_t sm[];
     __shared__ SeedRec s_rec[2][PT_NACT];
     __shared__ TileHdr s_hdr[2];
     __shared__ PpGeom s_geom[2];
@@ -823,7 +875,7 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
     }
     int t = blockIdx.x;                          // the host launches at most S.total CTAs
     if (warp >= PP_CONS)
-        pp_produce<NCH>(B, mc, S, t, a_sm, s_rec[0], &s_hdr[0], &s_next[0], s_geom, bar0,
+        pp_produce<NCH>(B, mc, S, TM, t, a_sm, s_rec[0], &s_hdr[0], &s_next[0], s_geom, bar0,
                         warp - PP_CONS, lane);
     __syncthreads();
     unsigned pend_bar = 0, pend_par = 0;         // producers: copies not yet waited for
@@ -834,7 +886,7 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
             if (t + (int)gridDim.x < S.total) {
                 pend_bar = bar0 + 8u * (unsigned)(cur ^ 1);
                 pend_par = (unsigned)((n + 1) >> 1) & 1u;
-                pp_produce<NCH>(B, mc, S, t + gridDim.x, a_sm + 4u * (unsigned)((cur ^ 1) * buf_words),
+                pp_produce<NCH>(B, mc, S, TM, t + gridDim.x, a_sm + 4u * (unsigned)((cur ^ 1) * buf_words),
                                 s_rec[cur ^ 1], &s_hdr[cur ^ 1], &s_next[cur ^ 1], s_geom, pend_bar,
                                 warp - PP_CONS, lane);
             }
@@ -915,7 +967,7 @@ template <int NCH>
 __global__ void __launch_bounds__(256, (NCH == 6 ? 2 : 3))
 k_cost_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
     constexpr int WPP = NCH / 2;
-    extern __shared__ __align__(16) uint32_t sm[];
+    extern __shared__ __align__(128) uint32_t sm[];
     __shared__ int s_seed[PC_N], s_u[PC_N], s_ux[PC_N], s_uy[PC_N];
     __shared__ unsigned char s_f[PC_N];
     __shared__ unsigned long long s_sa[PC_N];
@@ -1028,8 +1080,8 @@ pgm_status launch_c(const LvlBatch& B, const MatchConst& mc, int tiles, int smem
 // once (the occupancy query is cached per specialisation, device and
 // shared-memory size), never more than there are tiles.
 template <int NCH, int M, int NA, int SPW, int SPR>
-pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, const PtSched& S, int buf_words,
-                    cudaStream_t st) {
+pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, const PtSched& S, const PtMaps& TM,
+                    int buf_words, cudaStream_t st) {
     const int smem = 2 * buf_words * 4;
     static int configured = 0;                 // opt-in above 48 KB once per specialisation
     static int cache_dev = -1, cache_smem = -1, cache_cap = 0;
@@ -1052,7 +1104,7 @@ pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, const PtSched& S, i
         cache_smem = smem;
     }
     const int grid = S.total < cache_cap ? S.total : cache_cap;
-    kern<<<grid, PP_THREADS, smem, st>>>(B, mc, S, buf_words);
+    kern<<<grid, PP_THREADS, smem, st>>>(B, mc, S, TM, buf_words);
     return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
 }
 
@@ -1062,20 +1114,20 @@ pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, const PtSched& S, i
 // an upper bound of the group count with run-time masks.
 template <int NCH>
 pgm_status launch_dir(const LvlBatch& B, const MatchConst& mc, const PtSched& S, const PpGeom& G,
-                      int buf_words, cudaStream_t st) {
+                      const PtMaps& TM, int buf_words, cudaStream_t st) {
     if constexpr (NCH == 6) {
         if (G.q == 1 && G.M == 23 && G.nA == 15)
-            return (G.spw == 144 && G.spr == 112) ? launch_t<6, 23, 15, 144, 112>(B, mc, S, buf_words, st)
-                                                  : launch_t<6, 23, 15, 0, 0>(B, mc, S, buf_words, st);
+            return (G.spw == 144 && G.spr == 112) ? launch_t<6, 23, 15, 144, 112>(B, mc, S, TM, buf_words, st)
+                                                  : launch_t<6, 23, 15, 0, 0>(B, mc, S, TM, buf_words, st);
         if (G.q == 1 && G.M == 12 && G.nA == 11)
-            return (G.spw == 132 && G.spr == 100) ? launch_t<6, 12, 11, 132, 100>(B, mc, S, buf_words, st)
-                                                  : launch_t<6, 12, 11, 0, 0>(B, mc, S, buf_words, st);
-        if (G.q == 1 && G.M == 24 && G.nA == 16) return launch_t<6, 24, 16, 0, 0>(B, mc, S, buf_words, st);
-        if (G.M <= 8) return launch_t<6, 8, -1, 0, 0>(B, mc, S, buf_words, st);
-        if (G.M <= 16) return launch_t<6, 16, -1, 0, 0>(B, mc, S, buf_words, st);
-        return launch_t<6, 24, -1, 0, 0>(B, mc, S, buf_words, st);
+            return (G.spw == 132 && G.spr == 100) ? launch_t<6, 12, 11, 132, 100>(B, mc, S, TM, buf_words, st)
+                                                  : launch_t<6, 12, 11, 0, 0>(B, mc, S, TM, buf_words, st);
+        if (G.q == 1 && G.M == 24 && G.nA == 16) return launch_t<6, 24, 16, 0, 0>(B, mc, S, TM, buf_words, st);
+        if (G.M <= 8) return launch_t<6, 8, -1, 0, 0>(B, mc, S, TM, buf_words, st);
+        if (G.M <= 16) return launch_t<6, 16, -1, 0, 0>(B, mc, S, TM, buf_words, st);
+        return launch_t<6, 24, -1, 0, 0>(B, mc, S, TM, buf_words, st);
     } else {
-        return launch_t<NCH, 8, -1, 0, 0>(B, mc, S, buf_words, st);   // 2 channels: M <= 8
+        return launch_t<NCH, 8, -1, 0, 0>(B, mc, S, TM, buf_words, st);   // 2 channels: M <= 8
     }
 }
 }  // namespace
@@ -1137,6 +1189,100 @@ bool pm_tile_fits(const LvlBatch& B, const MatchConst& mc, int nch) {
     return mc.norm == PGM_L2SQ && pp_plan(B, mc, nch, S, G);
 }
 
+// ---------------------------------------------------------------- tensor maps
+// cuTensorMapEncodeTiled from the driver (no link against it), and a cache of
+// encoded maps keyed by their arguments: the maps of a level serve all of its
+// phases, and repeated steps on the same buffers encode nothing.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+struct MapKey {
+    const void* ptr;
+    unsigned long long dim0, dim1, pitch;
+    unsigned box0, box1, esize, pad;
+    bool operator==(const MapKey& o) const {
+        return ptr == o.ptr && dim0 == o.dim0 && dim1 == o.dim1 && pitch == o.pitch &&
+               box0 == o.box0 && box1 == o.box1 && esize == o.esize;
+    }
+};
+struct MapEntry { MapKey key; CUtensorMap map; bool used; };
+constexpr int MAP_CACHE = 1024;
+static std::mutex map_mu;
+static MapEntry map_cache[MAP_CACHE];
+
+// A 2D map of `esize`-byte elements (4 or 8): dim0 x dim1 elements, rows
+// `pitch` bytes apart, box0 x box1 elements per copy, zero fill outside.
+// False when the arguments break a tensor-map rule (then the slot stages
+// row by row).
+static bool map2d(CUtensorMap* out, const void* ptr, unsigned long long dim0,
+                  unsigned long long dim1, unsigned long long pitch, unsigned box0, unsigned box1,
+                  unsigned esize) {
+    if (box0 == 0 || box1 == 0 || box0 > 256 || box1 > 256 || box0 > dim0 || box1 > dim1 ||
+        (box0 * esize) % 16 != 0 || pitch % 16 != 0 || ((uintptr_t)ptr & 15) != 0 ||
+        pitch < dim0 * esize)
+        return false;
+    const EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const MapKey key{ptr, dim0, dim1, pitch, box0, box1, esize, 0};
+    size_t h = (uintptr_t)ptr;
+    h = h * 1000003u ^ (size_t)dim0;
+    h = h * 1000003u ^ (size_t)dim1;
+    h = h * 1000003u ^ (size_t)pitch;
+    h = h * 1000003u ^ (size_t)(box0 | (box1 << 9) | (esize << 18));
+    std::lock_guard<std::mutex> lock(map_mu);
+    MapEntry& e = map_cache[(h >> 4) % MAP_CACHE];
+    if (e.used && e.key == key) {
+        *out = e.map;
+        return true;
+    }
+    const cuuint64_t gdim[2] = {dim0, dim1}, gstride[1] = {pitch};
+    const cuuint32_t box[2] = {box0, box1}, estride[2] = {1, 1};
+    if (fn(out, esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2,
+           const_cast<void*>(ptr), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    e.key = key;
+    e.map = *out;
+    e.used = true;
+    return true;
+}
+
+// The maps of every slot of schedule S (one thread's launch parameters).
+static PtMaps& pp_maps(const LvlBatch& B, int nch, const PtSched& S, const PpGeom* G) {
+    static thread_local PtMaps TM;
+    const int wpp = nch / 2;
+    for (int k = 0; k < PP_MAPS; ++k) {
+        TM.ok[k] = 0;
+        if (k >= S.nk) continue;
+        const int pair = S.ndir == 2 ? k >> 1 : k, dir = S.ndir == 2 ? (k & 1) : S.dir;
+        const DirLvl& D = B.d[pair][dir];
+        const PpGeom& g = G[dir];
+        TM.ok[k] = (D.tw & 1) == 0 &&
+                   map2d(&TM.m[k][0], D.ref_split, (unsigned long long)D.rw * wpp, D.rh,
+                         2ull * D.ref_pitch, g.spr, g.ref_h, 4) &&
+                   map2d(&TM.m[k][1], D.tgt, (unsigned long long)D.tw * wpp, D.th,
+                         2ull * D.tgt_pitch, g.spw, g.win_h, 4) &&
+                   map2d(&TM.m[k][2], D.sb2, D.tw, D.th, 8ull * D.tw, g.cwp, g.ch, 8);
+    }
+    return TM;
+}
+
 static int device_sms() {
     static int dev_cached = -1, sms = 0;
     int dev = 0;
@@ -1167,15 +1313,17 @@ pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int 
     if (S[2].total <= 2 * device_sms()) {
         const int m = G[0].M > G[1].M ? G[0].M : G[1].M;
         *nlaunch = 1;
-        if (nch == 2) return launch_t<2, 8, -1, 0, 0>(B, mc, S[2], words, st);
-        if (m <= 8) return launch_t<6, 8, -1, 0, 0>(B, mc, S[2], words, st);
-        if (m <= 16) return launch_t<6, 16, -1, 0, 0>(B, mc, S[2], words, st);
-        return launch_t<6, 24, -1, 0, 0>(B, mc, S[2], words, st);
+        PtMaps& TM = pp_maps(B, nch, S[2], G);
+        if (nch == 2) return launch_t<2, 8, -1, 0, 0>(B, mc, S[2], TM, words, st);
+        if (m <= 8) return launch_t<6, 8, -1, 0, 0>(B, mc, S[2], TM, words, st);
+        if (m <= 16) return launch_t<6, 16, -1, 0, 0>(B, mc, S[2], TM, words, st);
+        return launch_t<6, 24, -1, 0, 0>(B, mc, S[2], TM, words, st);
     }
     for (int d = 0; d < 2; ++d) {
         if (S[d].total == 0) continue;
-        const pgm_status r = nch == 2 ? launch_dir<2>(B, mc, S[d], G[d], G[d].words, st)
-                                      : launch_dir<6>(B, mc, S[d], G[d], G[d].words, st);
+        PtMaps& TM = pp_maps(B, nch, S[d], G);
+        const pgm_status r = nch == 2 ? launch_dir<2>(B, mc, S[d], G[d], TM, G[d].words, st)
+                                      : launch_dir<6>(B, mc, S[d], G[d], TM, G[d].words, st);
         if (r != PGM_OK) return r;
         ++*nlaunch;
     }

@@ -143,11 +143,14 @@ __global__ void k_convert(const __grid_constant__ PyrBatch B) {
 // ----------------------------------------------------------------- Sobel
 // Gx = sum_j s_j sum_i d_i I(x+i, y+j); Gy with the roles of the axes swapped.
 // A CTA of 32 x 8 threads makes a 32 x 16 block of one image (two rows per
-// thread): the (32 + S - 1) x (16 + S - 1) input pixels of every channel
-// (border replicated) go to shared memory, the horizontal passes (d and s
-// along x, both within int16) are kept per input row as one packed word, and
-// the vertical passes finish Gx and Gy (separable and exact in integers).
-constexpr int SB_TW = 32, SB_TH = 16, SB_TY = 8;
+// thread).  The (32 + S - 1) x (16 + S - 1) input pixels of every channel
+// (border replicated) go to shared memory, as aligned 32-bit words for blocks
+// away from the left and right borders; the horizontal passes (d and s along
+// x, both within int16) are kept per input row as one packed word, and the
+// vertical passes finish Gx and Gy (separable and exact in integers).  The
+// output words are staged in shared memory and leave as contiguous 16-byte
+// stores, one tile row of each output array at a time.
+constexpr int SB_TW = 32, SB_TH = 16, SB_TY = 8, SB_XO = 4;   // SB_XO: staged columns left of x0
 __device__ __forceinline__ int sb_d(int S, int i) {
     return S == 5 ? (i == 0 ? -1 : i == 1 ? -2 : i == 2 ? 0 : i == 3 ? 2 : 1) : (i - 1);
 }
@@ -157,22 +160,35 @@ __device__ __forceinline__ int sb_s(int S, int i) {
 template <int S, int C>
 __global__ void __launch_bounds__(SB_TW * SB_TY) k_sobel(const __grid_constant__ PyrBatch B,
                                                          int dir_only) {
-    constexpr int R = S / 2, IW = SB_TW + S - 1, IH = SB_TH + S - 1;
-    __shared__ uint8_t sI[C][IH][IW];
-    __shared__ uint32_t sH[C][IH][SB_TW];               // (sum d v) low 16, (sum s v) high 16
+    constexpr int R = S / 2, IH = SB_TH + S - 1;
+    constexpr int IWW = (SB_XO + SB_TW + R + 3) / 4;     // staged words per row (x0 - 4 .. )
+    constexpr int IW = 4 * IWW, NT = SB_TW * SB_TY;
+    constexpr int OW = SB_TW * C;                        // output words per tile row and array
+    __shared__ __align__(16) uint8_t sI[C][IH][IW];      // column c holds x = x0 - SB_XO + c
+    __shared__ uint32_t sH[C][IH][SB_TW];                // (sum d v) low 16, (sum s v) high 16
+    __shared__ __align__(16) uint32_t sO[2][SB_TH][OW];  // descriptor words, split words
     const PyrItem& it = B.it[blockIdx.z];
     const int w = it.sw, h = it.sh, row = it.srow;
     const int x0 = blockIdx.x * SB_TW, y0 = blockIdx.y * SB_TH;
     if (x0 >= w || y0 >= h) return;                     // the whole block (uniform)
     const size_t plane = it.splane;
     const uint8_t* in = it.src;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    for (int r = ty; r < IH; r += SB_TY) {
-        const uint8_t* src = in + (size_t)clampi(y0 - R + r, 0, h - 1) * row;
-        for (int c = tx; c < IW; c += SB_TW) {
-            const int x = clampi(x0 - R + c, 0, w - 1);
-#pragma unroll
-            for (int ch = 0; ch < C; ++ch) sI[ch][r][c] = src[ch * plane + x];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * SB_TW + tx;
+    if (x0 >= SB_XO && x0 + SB_TW + R <= w) {
+        // interior in x: rows start 16-byte aligned and x0 - SB_XO is a
+        // multiple of 4, so whole words are read; the words end inside the
+        // padded row (x0 - 4 + IW <= row)
+        for (int e = tid; e < C * IH * IWW; e += NT) {
+            const int ch = e / (IH * IWW), rem = e - ch * (IH * IWW), r = rem / IWW, k = rem - r * IWW;
+            const uint8_t* src = in + ch * plane + (size_t)clampi(y0 - R + r, 0, h - 1) * row;
+            *reinterpret_cast<uint32_t*>(&sI[ch][r][4 * k]) =
+                *reinterpret_cast<const uint32_t*>(src + x0 - SB_XO + 4 * k);
+        }
+    } else {
+        for (int e = tid; e < C * IH * IW; e += NT) {
+            const int ch = e / (IH * IW), rem = e - ch * (IH * IW), r = rem / IW, c = rem - r * IW;
+            const uint8_t* src = in + ch * plane + (size_t)clampi(y0 - R + r, 0, h - 1) * row;
+            sI[ch][r][c] = src[clampi(x0 - SB_XO + c, 0, w - 1)];
         }
     }
     __syncthreads();
@@ -182,14 +198,13 @@ __global__ void __launch_bounds__(SB_TW * SB_TY) k_sobel(const __grid_constant__
             int sd = 0, ss = 0;
 #pragma unroll
             for (int i = 0; i < S; ++i) {
-                const int v = sI[ch][r][tx + i];
+                const int v = sI[ch][r][SB_XO - R + tx + i];
                 sd += sb_d(S, i) * v;
                 ss += sb_s(S, i) * v;
             }
             sH[ch][r][tx] = (uint32_t)(uint16_t)sd | ((uint32_t)ss << 16);
         }
     __syncthreads();
-    const int x = x0 + tx;
     int g[2][2 * C];
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) {
@@ -221,19 +236,39 @@ __global__ void __launch_bounds__(SB_TW * SB_TY) k_sobel(const __grid_constant__
             g[k][C + ch] = b2;
         }
     }
-    // pixel-interleaved int16, written as 32-bit words (2C is even), and the
-    // same words with every value a split into signed bytes a = 128 a_h + a_l
+    // pixel-interleaved int16 as 32-bit words (2C is even), and the same
+    // words with every value a split into signed bytes a = 128 a_h + a_l
     // (a_l in [-64, 63]) for the dp2a cross products
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int y = y0 + 2 * ty + k;
-        if (x >= w || y >= h) continue;
-        const size_t w0 = ((size_t)y * it.drow + (size_t)x * 2 * C) / 2;
-        uint32_t* dst = reinterpret_cast<uint32_t*>(it.dst) + w0;
+    for (int k = 0; k < 2; ++k)
 #pragma unroll
         for (int q = 0; q < C; ++q) {
-            dst[q] = (uint32_t)(uint16_t)g[k][2 * q] | ((uint32_t)(uint16_t)g[k][2 * q + 1] << 16);
-            it.split[w0 + q] = (uint32_t)split_bytes(g[k][2 * q], g[k][2 * q + 1]);
+            sO[0][2 * ty + k][tx * C + q] =
+                (uint32_t)(uint16_t)g[k][2 * q] | ((uint32_t)(uint16_t)g[k][2 * q + 1] << 16);
+            sO[1][2 * ty + k][tx * C + q] = (uint32_t)split_bytes(g[k][2 * q], g[k][2 * q + 1]);
+        }
+    __syncthreads();
+    // tile row r of array a starts at word (y0 + r) rw + x0 C: rows of rw =
+    // drow / 2 words (drow a multiple of 8) and x0 C a multiple of 32, so
+    // 16-byte aligned (the arrays start 256-byte aligned)
+    const size_t rw = (size_t)(it.drow >> 1);
+    uint32_t* const dst0 = reinterpret_cast<uint32_t*>(it.dst) + (size_t)x0 * C;
+    uint32_t* const dst1 = it.split + (size_t)x0 * C;
+    const int nr = min(SB_TH, h - y0);
+    if (x0 + SB_TW <= w) {
+        constexpr int NQ = OW / 4;
+        for (int e = tid; e < 2 * SB_TH * NQ; e += NT) {
+            const int a = e / (SB_TH * NQ), rem = e - a * (SB_TH * NQ), r = rem / NQ, q = rem - r * NQ;
+            if (r >= nr) continue;
+            const uint4 v = *reinterpret_cast<const uint4*>(&sO[a][r][4 * q]);
+            *reinterpret_cast<uint4*>((a ? dst1 : dst0) + (size_t)(y0 + r) * rw + 4 * q) = v;
+        }
+    } else {
+        const int nw = (w - x0) * C;                    // ragged right edge: words
+        for (int e = tid; e < 2 * SB_TH * OW; e += NT) {
+            const int a = e / (SB_TH * OW), rem = e - a * (SB_TH * OW), r = rem / OW, q = rem - r * OW;
+            if (r >= nr || q >= nw) continue;
+            (a ? dst1 : dst0)[(size_t)(y0 + r) * rw + q] = sO[a][r][q];
         }
     }
 }
