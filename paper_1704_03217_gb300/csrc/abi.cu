@@ -224,8 +224,9 @@ void fill_dir(const pgm_params* p, const PairCtx& c, int l, int d, DirLvl* D) {
 // library allocates no device memory for them).
 struct Aux {
     int dev = -1;
-    cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr;
+    cudaStream_t s = nullptr;        // box filters of the finer levels
+    cudaStream_t s2 = nullptr;       // backward-direction search phases
+    cudaEvent_t fork = nullptr, sfork = nullptr, sjoin = nullptr;
     cudaEvent_t lvl[MAXL] = {};
 };
 static thread_local Aux g_aux;
@@ -237,7 +238,10 @@ static pgm_status aux_get(Aux** out) {
         Aux a;
         a.dev = dev;
         if (cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess)
+            cudaStreamCreateWithFlags(&a.s2, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&a.sfork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&a.sjoin, cudaEventDisableTiming) != cudaSuccess)
             return PGM_ERR_CUDA;
         for (int l = 0; l < MAXL; ++l)
             if (cudaEventCreateWithFlags(&a.lvl[l], cudaEventDisableTiming) != cudaSuccess)
@@ -357,12 +361,29 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
             r = launch_cost_fill(B, mc, nch, maxP, max_seeds, st);
             if (r != PGM_OK) return r;
         }
+        // the two directions search independently until the consistency
+        // check: when each phase is one launch per direction, the backward
+        // ones go on an auxiliary stream and overlap the forward ones (the
+        // kernel time profile keeps them on the caller's stream)
+        cudaStream_t st2 = nullptr;
+        if (fused && !g_prof.on && pm_tile_split(B, mc, nch)) {
+            if (!aux) {
+                r = aux_get(&aux);
+                if (r != PGM_OK) return r;
+            }
+            if (cudaEventRecord(aux->sfork, st) != cudaSuccess ||
+                cudaStreamWaitEvent(aux->s2, aux->sfork, 0) != cudaSuccess) return PGM_ERR_CUDA;
+            st2 = aux->s2;
+        }
         for (int t = 0; t < T; ++t)
             for (int col = 0; col < 2; ++col) {
                 mc.t = t; mc.colour = col; mc.refresh = fused && t == 0;
-                r = launch_pm_phase(B, mc, nch, maxP, max_half, st);
+                r = launch_pm_phase(B, mc, nch, maxP, max_half, st, st2);
                 if (r != PGM_OK) return r;
             }
+        if (st2 && (cudaEventRecord(aux->sjoin, st2) != cudaSuccess ||
+                    cudaStreamWaitEvent(st, aux->sjoin, 0) != cudaSuccess))
+            return PGM_ERR_CUDA;
         mc.t = 0; mc.colour = 0; mc.refresh = 0;
         r = launch_consist(B, mc, max_seeds, st);
         if (r != PGM_OK) return r;

@@ -727,14 +727,14 @@ pgm_status launch_cost_fill(const LvlBatch& B, const MatchConst& mc, int nch, in
 }
 
 pgm_status launch_pm_phase(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
-                           int max_seeds, cudaStream_t st) {
+                           int max_seeds, cudaStream_t st, cudaStream_t st2) {
     if (max_seeds <= 0) return PGM_OK;
     KScope ks(PGM_K_PM, st);
     dim3 g((max_seeds + 7) / 8, 2, B.n);   // max_seeds: half-row width x rows
     if (mc.norm == PGM_L2SQ) {
         bool handled = false;
         int nl = 0;
-        pgm_status r = launch_pm_tile(B, mc, nch, maxP, &nl, &handled, st);
+        pgm_status r = launch_pm_tile(B, mc, nch, maxP, &nl, &handled, st, st2);
         if (handled) ks.n = nl;
         if (r != PGM_OK || handled) return r;
         if (mc.refresh) return PGM_ERR_UNSUPPORTED;     // the per-seed kernel does no refresh

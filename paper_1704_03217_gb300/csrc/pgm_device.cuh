@@ -152,8 +152,10 @@ pgm_status launch_init(const LvlBatch& B, const MatchConst& mc, int nch, int max
                        int max_seeds, cudaStream_t st);
 pgm_status launch_cost_fill(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
                             int max_seeds, cudaStream_t st);
+// st2 (may be null): the stream of the backward direction when pm_tile_split
+// says the phase runs one launch per direction
 pgm_status launch_pm_phase(const LvlBatch& B, const MatchConst& mc, int nch, int maxP,
-                           int max_seeds, cudaStream_t st);
+                           int max_seeds, cudaStream_t st, cudaStream_t st2);
 pgm_status launch_consist(const LvlBatch& B, const MatchConst& mc, int max_seeds,
                           cudaStream_t st);
 pgm_status launch_transfer(const XferBatch& X, int max_seeds, cudaStream_t st);
@@ -166,8 +168,11 @@ pgm_status launch_init_tile(const LvlBatch& B, const MatchConst& mc, int nch, bo
 // true when the tile search kernel takes this batch (it then also does the
 // cost refresh of a visit's first iteration, MatchConst::refresh)
 bool pm_tile_fits(const LvlBatch& B, const MatchConst& mc, int nch);
+// true when the tile search kernel takes this batch with one launch per
+// direction (phases larger than one tile per resident CTA)
+bool pm_tile_split(const LvlBatch& B, const MatchConst& mc, int nch);
 pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP, int* nlaunch,
-                          bool* handled, cudaStream_t st);
+                          bool* handled, cudaStream_t st, cudaStream_t st2);
 pgm_status launch_cost_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
                             cudaStream_t st);
 // filter.cu

@@ -1283,6 +1283,14 @@ static PtMaps& pp_maps(const LvlBatch& B, int nch, const PtSched& S, const PpGeo
     return TM;
 }
 
+static int device_sms();
+
+bool pm_tile_split(const LvlBatch& B, const MatchConst& mc, int nch) {
+    PtSched S[3];
+    PpGeom G[2];
+    return mc.norm == PGM_L2SQ && pp_plan(B, mc, nch, S, G) && S[2].total > 2 * device_sms();
+}
+
 static int device_sms() {
     static int dev_cached = -1, sms = 0;
     int dev = 0;
@@ -1300,7 +1308,7 @@ static int device_sms() {
 // consumer; a larger one runs each direction in its own launch of the
 // consumer specialised for its layout.  *nlaunch: kernels launched.
 pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP, int* nlaunch,
-                          bool* handled, cudaStream_t st) {
+                          bool* handled, cudaStream_t st, cudaStream_t st2) {
     (void)maxP;
     *handled = false;
     *nlaunch = 0;
@@ -1322,8 +1330,9 @@ pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int 
     for (int d = 0; d < 2; ++d) {
         if (S[d].total == 0) continue;
         PtMaps& TM = pp_maps(B, nch, S[d], G);
-        const pgm_status r = nch == 2 ? launch_dir<2>(B, mc, S[d], G[d], TM, G[d].words, st)
-                                      : launch_dir<6>(B, mc, S[d], G[d], TM, G[d].words, st);
+        const cudaStream_t sd = d == 1 && st2 ? st2 : st;
+        const pgm_status r = nch == 2 ? launch_dir<2>(B, mc, S[d], G[d], TM, G[d].words, sd)
+                                      : launch_dir<6>(B, mc, S[d], G[d], TM, G[d].words, sd);
         if (r != PGM_OK) return r;
         ++*nlaunch;
     }
