@@ -647,6 +647,9 @@ template <int M, int NA>
 struct PpLay {
     static constexpr int A0 = NA >= 0 ? NA : 0;
     static constexpr int NB = M - A0 > 0 ? M - A0 : 1;
+    // P = 15 with 6 channels: B groups of g = 2 rows, so a lane's word in B
+    // group b sits b * 2 rows below its word in group 0 (the host checks g)
+    static constexpr int GB = (M == 23 && NA == 15) ? 2 : 0;
 };
 
 // Window slot of target centre (qx, qy): the byte offset of its patch
@@ -666,13 +669,15 @@ template <int M, int NA, int SPW>
 __device__ __forceinline__ long long pp_dot_win(const int (&b)[M],
                                                 const Offs<PpLay<M, NA>::NB>& off,
                                                 const PpGeom& G, unsigned base, int lane) {
-    constexpr int A0 = PpLay<M, NA>::A0;
+    constexpr int A0 = PpLay<M, NA>::A0, GB = SPW > 0 ? PpLay<M, NA>::GB : 0;
     const int spw = SPW > 0 ? SPW : G.spw;
-    const unsigned basel = base + 4u * (unsigned)lane;
+    const unsigned basel = base + 4u * (unsigned)lane, baseb = base + off.at(0);
     int l0 = 0, l1 = 0, h0 = 0, h1 = 0;                 // two chains each
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-        const unsigned addr = m < A0 ? basel + 4u * (unsigned)(m * spw) : base + off.at(m - A0);
+        const unsigned addr = m < A0 ? basel + 4u * (unsigned)(m * spw)
+                              : GB > 0 ? baseb + 4u * (unsigned)((m - A0) * GB * spw)
+                                       : base + off.at(m - A0);
         const int v = lds32(addr);
         if (m & 1) { l1 = __dp2a_lo(v, b[m], l1); h1 = __dp2a_hi(v, b[m], h1); }
         else { l0 = __dp2a_lo(v, b[m], l0); h0 = __dp2a_hi(v, b[m], h0); }
@@ -686,8 +691,9 @@ __device__ __forceinline__ long long pp_dot_win(const int (&b)[M],
 template <int NCH, int M, int NA, int SPW>
 __device__ __forceinline__ long long pp_dot_glob(const int (&b)[M],
                                                  const Offs<PpLay<M, NA>::NB>& off,
-                                                 const DirLvl& D, const PpGeom& G, int qx, int qy,
-                                                 int lane) {
+                                                 const unsigned short* offw, const DirLvl& D,
+                                                 const PpGeom& G, int qx, int qy, int lane) {
+    constexpr int GB = SPW > 0 ? PpLay<M, NA>::GB : 0;
     constexpr int WPP = NCH / 2, A0 = PpLay<M, NA>::A0;
     const int h = D.P / 2, spw = SPW > 0 ? SPW : G.spw;
     const int pitchw = D.tgt_pitch >> 1;
@@ -697,7 +703,7 @@ __device__ __forceinline__ long long pp_dot_glob(const int (&b)[M],
     for (int m = 0; m < M; ++m) {
         int row = m, col = lane;
         if (m >= A0) {
-            const int o = (int)(off.at(m - A0) >> 2);
+            const int o = (int)((GB > 0 ? (unsigned)offw[m * 32 + lane] : off.at(m - A0)) >> 2);
             row = o / spw;
             col = o - row * spw;
         }
@@ -727,9 +733,11 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
     const int P = D.P, h = P / 2, sig = mc.sigma, spr = SPR > 0 ? SPR : G.spr;
     const unsigned a_ref = buf, a_tw = buf + 4u * (unsigned)G.off_win;
     const unsigned a_sb = buf + 4u * (unsigned)G.off_sb;
+    constexpr int GB = SPW > 0 && SPR > 0 ? PpLay<M, NA>::GB : 0;
     Offs<NB> off;                           // byte offsets of the lane's table-addressed words
 #pragma unroll
-    for (int m = 0; m < NB; ++m) off.p[m] = A0 + m < M ? offw[(A0 + m) * 32 + lane] : 0u;
+    for (int m = 0; m < NB; ++m)
+        off.p[m] = A0 + m < M && (GB == 0 || m == 0) ? offw[(A0 + m) * 32 + lane] : 0u;
     // zero references: B-group lanes without a word, and past the last row
     const bool has_b = G.S == 0 || lane % G.S < G.wl;
     const int mask_b = has_b ? -1 : 0;
@@ -753,9 +761,12 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
         const unsigned rbase = a_ref + 4u * (unsigned)((a / (PT_TW / 2)) * sig * spr + H.shr +
                                                        (R.px - h - H.rx0) * WPP);
         const unsigned rbasel = rbase + 4u * (unsigned)lane;
+        const unsigned rbaseb = GB > 0 ? rbase + offr[A0 * 32 + lane] : 0u;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-            b[m] = lds32(m < A0 ? rbasel + 4u * (unsigned)(m * spr) : rbase + offr[m * 32 + lane]);
+            b[m] = lds32(m < A0 ? rbasel + 4u * (unsigned)(m * spr)
+                         : GB > 0 ? rbaseb + 4u * (unsigned)((m - A0) * GB * spr)
+                                  : rbase + offr[m * 32 + lane]);
             if (NA >= 0) {
                 if (m >= NA) b[m] &= (m == M - 1) ? mask_last : mask_b;
             } else {
@@ -814,7 +825,7 @@ __device__ __forceinline__ void pp_consume(const LvlBatch& B, const MatchConst& 
                 cr = pp_dot_win<M, NA, SPW>(b, off, G, a_tw + (unsigned)(slot & 0xffff), lane);
             } else {
                 sb = D.sb2[(size_t)qy * D.tw + qx];
-                cr = pp_dot_glob<NCH, M, NA, SPW>(b, off, D, G, qx, qy, lane);
+                cr = pp_dot_glob<NCH, M, NA, SPW>(b, off, offw, D, G, qx, qy, lane);
                 ++n_glob;
             }
             const unsigned long long cst = xcost(R.sa, sb, cr);
@@ -864,8 +875,11 @@ k_pm_t(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 2 * PP_MMAX * 32; e += PP_THREADS) {
-        const int d = e / (PP_MMAX * 32), i = e - d * (PP_MMAX * 32), m = i >> 5, l = i & 31;
+    constexpr int MT0 = NA >= 0 ? NA : 0;        // groups read through the tables: [MT0, M)
+    const int d0 = S.ndir == 2 ? 0 : S.dir, nd = S.ndir == 2 ? 2 : 1;
+    for (int e = threadIdx.x; e < nd * (M - MT0) * 32; e += PP_THREADS) {
+        const int d = d0 + e / ((M - MT0) * 32), i = MT0 * 32 + e % ((M - MT0) * 32);
+        const int m = i >> 5, l = i & 31;
         const PpGeom& G = s_geom[d];
         int row, col;
         bool valid;
@@ -1117,7 +1131,7 @@ pgm_status launch_dir(const LvlBatch& B, const MatchConst& mc, const PtSched& S,
                       const PtMaps& TM, int buf_words, cudaStream_t st) {
     if constexpr (NCH == 6) {
         if (G.q == 1 && G.M == 23 && G.nA == 15)
-            return (G.spw == 144 && G.spr == 112) ? launch_t<6, 23, 15, 144, 112>(B, mc, S, TM, buf_words, st)
+            return (G.spw == 144 && G.spr == 112 && G.g == 2) ? launch_t<6, 23, 15, 144, 112>(B, mc, S, TM, buf_words, st)
                                                   : launch_t<6, 23, 15, 0, 0>(B, mc, S, TM, buf_words, st);
         if (G.q == 1 && G.M == 12 && G.nA == 11)
             return (G.spw == 132 && G.spr == 100) ? launch_t<6, 12, 11, 132, 100>(B, mc, S, TM, buf_words, st)
