@@ -76,16 +76,21 @@ __global__ void k_down(const __grid_constant__ PyrBatch B, int C) {
 }
 
 // ------------------------------------------------------- colour spaces
-// Integer cube root: float estimate, then exact correction.
+// Integer cube root of v <= 2^48: float estimate, then exact correction.  The
+// estimate is within a few hundredths of the real root (v rounded to float,
+// then a cube root of documented 1-ulp accuracy, for roots below 2^17), so
+// its integer part is off by at most one; two steps each way leave margin.
 __device__ __forceinline__ uint32_t icbrt48(unsigned long long v) {
     int c = (int)cbrtf((float)v);
 #pragma unroll
-    for (int it = 0; it < 3; ++it)
-        if (c > 0 && (unsigned long long)c * c * c > v) --c;
+    for (int it = 0; it < 2; ++it) {
+        const unsigned long long cc = (unsigned long long)(unsigned)c * (unsigned)c;
+        if (c > 0 && cc * (unsigned)c > v) --c;
+    }
 #pragma unroll
-    for (int it = 0; it < 3; ++it) {
-        unsigned long long n = (unsigned long long)(c + 1);
-        if (n * n * n <= v) ++c;
+    for (int it = 0; it < 2; ++it) {
+        const unsigned n = (unsigned)c + 1u;
+        if ((unsigned long long)n * n * n <= v) ++c;
     }
     return (uint32_t)c;
 }
@@ -93,7 +98,9 @@ __device__ __forceinline__ uint32_t icbrt48(unsigned long long v) {
 // CIELab companding function of t = T / (255 * 2^16), result scaled by 2^16.
 __device__ __forceinline__ long long lab_f(long long T) {
     if (T * 24389 > 216LL * 255 * 65536) {               // t > (6/29)^3
-        unsigned long long V = ((unsigned long long)T << 32) / 255ull;  // t * 2^48
+        // t * 2^48 = floor(T 2^32 / 255) = T (2^32 - 1) / 255 + floor(T / 255)
+        const uint32_t t32 = (uint32_t)T;                 // T < 2^24
+        const unsigned long long V = (unsigned long long)t32 * 16843009ull + t32 / 255u;
         return (long long)icbrt48(V);
     }
     long long num = T * (841 * 29) + 4LL * 65536 * 108 * 255;          // t * 841/108 + 4/29
@@ -112,8 +119,8 @@ __device__ __forceinline__ void to_lab(int r, int g, int b, int* o) {
     long long Z = 1164LL * r + 7175LL * g + 57197LL * b;
     long long fx = lab_f(X), fy = lab_f(Y), fz = lab_f(Z);
     long long Ls = fdiv((116 * fy - 16 * 65536) * 255 + 3276800, 6553600);
-    long long As = fdiv(500 * (fx - fy) + 128 * 65536 + 32768, 65536);
-    long long Bs = fdiv(200 * (fy - fz) + 128 * 65536 + 32768, 65536);
+    long long As = (500 * (fx - fy) + 128 * 65536 + 32768) >> 16;      // floor division
+    long long Bs = (200 * (fy - fz) + 128 * 65536 + 32768) >> 16;
     o[0] = clampi((int)Ls, 0, 255);
     o[1] = clampi((int)As, 0, 255);
     o[2] = clampi((int)Bs, 0, 255);
@@ -122,8 +129,8 @@ __device__ __forceinline__ void to_lab(int r, int g, int b, int* o) {
 __device__ __forceinline__ void to_ycrcb(int r, int g, int b, int* o) {
     int y = gray_q14(r, g, b);
     o[0] = y;
-    o[1] = clampi((int)fdiv((long long)(r - y) * 11682 + (128 << 14) + 8192, 16384), 0, 255);
-    o[2] = clampi((int)fdiv((long long)(b - y) * 9241 + (128 << 14) + 8192, 16384), 0, 255);
+    o[1] = clampi(((r - y) * 11682 + (128 << 14) + 8192) >> 14, 0, 255);   // floor division
+    o[2] = clampi(((b - y) * 9241 + (128 << 14) + 8192) >> 14, 0, 255);
 }
 
 __global__ void k_convert(const __grid_constant__ PyrBatch B) {
