@@ -19,6 +19,13 @@
  *    the legacy default stream).  The returned status covers argument checks
  *    and launch errors only; device-side failures are recorded in the
  *    workspace's error word and reported by pgm_sync_status().
+ *  - pgm_match and pgm_match_batch fork part of their work onto two streams
+ *    of the library's own (created once per host thread and device): the
+ *    box sums of the finer levels and the backward direction's search
+ *    phases.  Each fork starts from an event recorded on `stream` and is
+ *    joined back to `stream` by an event wait before the call returns, so
+ *    all of the call's work stays ordered on `stream` and is captured with
+ *    it into a CUDA graph.
  *  - Nothing throws across the ABI.  Calls on different workspaces may run
  *    concurrently from different host threads.
  *  - Results are a deterministic function of (params, images, stream_id):

@@ -219,24 +219,37 @@ void fill_dir(const pgm_params* p, const PairCtx& c, int l, int d, DirLvl* D) {
     D->sa2img = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sa2img[l][d]);
 }
 
-// The auxiliary stream of this thread on the current device, with its fork
-// and per-level join events (created once per thread and device; the
-// library allocates no device memory for them).
+// Auxiliary streams with their fork and join events, one set per (device,
+// caller stream) of each host thread, so that calls on different caller
+// streams never wait on each other's forked work.  Created on first use and
+// kept (the library allocates no device memory for them); with AUX_MAX sets
+// in use a call on a new caller stream does not fork (*out = null).
 struct Aux {
+    bool used = false;
     int dev = -1;
+    cudaStream_t key = nullptr;      // the caller's stream
     cudaStream_t s = nullptr;        // box filters of the finer levels
     cudaStream_t s2 = nullptr;       // backward-direction search phases
     cudaEvent_t fork = nullptr, sfork = nullptr, sjoin = nullptr;
     cudaEvent_t lvl[MAXL] = {};
 };
-static thread_local Aux g_aux;
+constexpr int AUX_MAX = 32;
+static thread_local Aux g_aux[AUX_MAX];
 
-static pgm_status aux_get(Aux** out) {
+static pgm_status aux_get(cudaStream_t st, Aux** out) {
+    *out = nullptr;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PGM_ERR_CUDA;
-    if (g_aux.dev != dev) {
+    for (int i = 0; i < AUX_MAX; ++i)
+        if (g_aux[i].used && g_aux[i].dev == dev && g_aux[i].key == st) {
+            *out = &g_aux[i];
+            return PGM_OK;
+        }
+    for (int i = 0; i < AUX_MAX; ++i) {
+        if (g_aux[i].used) continue;
         Aux a;
         a.dev = dev;
+        a.key = st;
         if (cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&a.s2, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -246,9 +259,11 @@ static pgm_status aux_get(Aux** out) {
         for (int l = 0; l < MAXL; ++l)
             if (cudaEventCreateWithFlags(&a.lvl[l], cudaEventDisableTiming) != cudaSuccess)
                 return PGM_ERR_CUDA;
-        g_aux = a;                   // the previous device's handles are kept alive
+        a.used = true;
+        g_aux[i] = a;
+        *out = &g_aux[i];
+        return PGM_OK;
     }
-    *out = &g_aux;
     return PGM_OK;
 }
 
@@ -278,17 +293,22 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
     bool joined[MAXL];
     for (int l = 0; l < MAXL; ++l) joined[l] = true;
     Aux* aux = nullptr;
+    bool aux_tried = false, forked = false;
     if (p->norm == PGM_L2SQ) {
         bool needed[MAXL] = {false};
         for (int v = 0; v < sch.n; ++v) needed[sch.level[v]] = true;
         const int l0 = sch.level[0];
         for (int l = p->levels - 1; l >= 0; --l) {
             if (!needed[l]) continue;
-            if (l != l0 && !aux) {
-                pgm_status r = aux_get(&aux);
+            if (l != l0 && !aux_tried) {
+                aux_tried = true;
+                pgm_status r = aux_get(st, &aux);
                 if (r != PGM_OK) return r;
+            }
+            if (l != l0 && aux && !forked) {
                 if (cudaEventRecord(aux->fork, st) != cudaSuccess ||
                     cudaStreamWaitEvent(aux->s, aux->fork, 0) != cudaSuccess) return PGM_ERR_CUDA;
+                forked = true;
             }
             memset(&B, 0, sizeof(B));
             B.n = n; B.level = l;
@@ -301,9 +321,10 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
                     np = B.d[k][d].rw * B.d[k][d].rh;
                     if (np > max_px) max_px = np;
                 }
-            pgm_status r = launch_box(B, nch, max_px, l == l0 ? st : aux->s);
+            const bool on_aux = l != l0 && aux;
+            pgm_status r = launch_box(B, nch, max_px, on_aux ? aux->s : st);
             if (r != PGM_OK) return r;
-            if (l != l0) {
+            if (on_aux) {
                 if (cudaEventRecord(aux->lvl[l], aux->s) != cudaSuccess) return PGM_ERR_CUDA;
                 joined[l] = false;
             }
@@ -367,13 +388,16 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
         // kernel time profile keeps them on the caller's stream)
         cudaStream_t st2 = nullptr;
         if (fused && !g_prof.on && pm_tile_split(B, mc, nch)) {
-            if (!aux) {
-                r = aux_get(&aux);
+            if (!aux_tried) {
+                aux_tried = true;
+                r = aux_get(st, &aux);
                 if (r != PGM_OK) return r;
             }
-            if (cudaEventRecord(aux->sfork, st) != cudaSuccess ||
-                cudaStreamWaitEvent(aux->s2, aux->sfork, 0) != cudaSuccess) return PGM_ERR_CUDA;
-            st2 = aux->s2;
+            if (aux) {
+                if (cudaEventRecord(aux->sfork, st) != cudaSuccess ||
+                    cudaStreamWaitEvent(aux->s2, aux->sfork, 0) != cudaSuccess) return PGM_ERR_CUDA;
+                st2 = aux->s2;
+            }
         }
         for (int t = 0; t < T; ++t)
             for (int col = 0; col < 2; ++col) {
