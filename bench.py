@@ -110,17 +110,21 @@ def run_reference(a):
 def pm_traffic_per_launch(pairs, launches):
     """DRAM bytes per k_pm_t launch: the committed ncu record's bytes over all
     search launches of one step, scaled to `pairs` per step and divided by
-    this step's `launches`; None when the kernel source changed since the
-    capture."""
+    this step's `launches`; None when the device code of the search kernel
+    (pm_tile.cu above its host-side section) changed since the capture."""
     import hashlib
     rec = os.path.join(ROOT, "profiles", "k_pm_t_traffic.json")
     src = os.path.join(ROOT, "paper_1704_03217_gb300", "csrc", "pm_tile.cu")
+    mark = "// Host side: launch configuration.  No device code below this line.\n"
     try:
         r = json.load(open(rec))
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        text = open(src, encoding="utf-8").read()
     except (OSError, ValueError):
         return None
-    if r.get("pm_tile_sha256") != h or "dram_bytes_per_step" not in r or launches <= 0:
+    if mark not in text:
+        return None
+    h = hashlib.sha256(text.split(mark)[0].encode("utf-8")).hexdigest()
+    if r.get("pm_tile_device_sha256") != h or "dram_bytes_per_step" not in r or launches <= 0:
         return None
     return r["dram_bytes_per_step"] * pairs / r["pairs"] / launches
 

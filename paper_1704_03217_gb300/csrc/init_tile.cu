@@ -159,7 +159,13 @@ __global__ void __launch_bounds__(IN_THREADS) k_init_t(const __grid_constant__ L
 template <int NCH>
 pgm_status launch_in(const LvlBatch& B, const MatchConst& mc, int groups, int smem,
                      cudaStream_t st) {
-    static int configured = 0;
+    static thread_local int cfg_dev = -1, configured = 0;   // per host thread and device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PGM_ERR_CUDA;
+    if (dev != cfg_dev) {
+        cfg_dev = dev;
+        configured = 0;
+    }
     if (configured < smem) {
         if (cudaFuncSetAttribute(k_init_t<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
             cudaSuccess) return PGM_ERR_CUDA;

@@ -1077,15 +1077,32 @@ k_cost_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
 #undef PGM_COST_SEEDS
 }
 
+// ===========================================================================
+// Host side: launch configuration.  No device code below this line.
+
+// Per-thread caches keyed by device: the shared-memory opt-in of a kernel is a
+// per-device attribute, and calls may come from several host threads.
+static bool opt_in_smem(const void* kern, int smem, int* cfg_dev, int* configured) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (dev != *cfg_dev) {
+        *cfg_dev = dev;
+        *configured = 0;
+    }
+    if (*configured < smem) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess) return false;
+        *configured = smem;
+    }
+    return true;
+}
+
 template <int NCH>
 pgm_status launch_c(const LvlBatch& B, const MatchConst& mc, int tiles, int smem_bytes,
                     cudaStream_t st) {
-    static int configured = 0;
-    if (configured < smem_bytes) {
-        if (cudaFuncSetAttribute(k_cost_t<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem_bytes) != cudaSuccess) return PGM_ERR_CUDA;
-        configured = smem_bytes;
-    }
+    static thread_local int cfg_dev = -1, configured = 0;
+    if (!opt_in_smem((const void*)k_cost_t<NCH>, smem_bytes, &cfg_dev, &configured))
+        return PGM_ERR_CUDA;
     k_cost_t<NCH><<<dim3(tiles, 2, B.n), 256, smem_bytes, st>>>(B, mc);
     return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
 }
@@ -1097,14 +1114,10 @@ template <int NCH, int M, int NA, int SPW, int SPR>
 pgm_status launch_t(const LvlBatch& B, const MatchConst& mc, const PtSched& S, const PtMaps& TM,
                     int buf_words, cudaStream_t st) {
     const int smem = 2 * buf_words * 4;
-    static int configured = 0;                 // opt-in above 48 KB once per specialisation
-    static int cache_dev = -1, cache_smem = -1, cache_cap = 0;
+    static thread_local int cfg_dev = -1, configured = 0;   // opt-in above 48 KB
+    static thread_local int cache_dev = -1, cache_smem = -1, cache_cap = 0;
     auto kern = k_pm_t<NCH, M, NA, SPW, SPR>;
-    if (configured < smem) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-            cudaSuccess) return PGM_ERR_CUDA;
-        configured = smem;
-    }
+    if (!opt_in_smem((const void*)kern, smem, &cfg_dev, &configured)) return PGM_ERR_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PGM_ERR_CUDA;
     if (dev != cache_dev || smem != cache_smem) {
@@ -1306,7 +1319,7 @@ bool pm_tile_split(const LvlBatch& B, const MatchConst& mc, int nch) {
 }
 
 static int device_sms() {
-    static int dev_cached = -1, sms = 0;
+    static thread_local int dev_cached = -1, sms = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (dev != dev_cached) {
