@@ -129,6 +129,56 @@ def pm_traffic_per_launch(pairs, launches):
     return r["dram_bytes_per_step"] * pairs / r["pairs"] / launches
 
 
+# ------------------------------------------------- HBM-bound stages (a1-a3, a7-a9)
+def visit_levels(levels, rounds):
+    """Levels of the visits in order (reading R15): m, then (m-1, m) x N,
+    then m-1 down to 0."""
+    m = levels - 1
+    if m == 0:
+        return [0]
+    seq = [m] + [m - 1, m] * rounds + list(range(m - 1, -1, -1))
+    return seq
+
+
+def hbm_stage_bytes(prm, w, h, pairs, matches_total):
+    """Compulsory DRAM bytes per step of the stages around the search, for
+    `pairs` pairs of w x h images (both images of a pair the same size):
+      pyramid (a1-a3): each input image read once (3 B/px) and, per scheme and
+        level, the descriptor and its split-byte copy written once
+        (2 x 2C x 2 B/px);
+      fields (a7-a9): per visit the consistency check reads both fields
+        (5 B per seed: u and flags) and writes flags (1 B) in each direction,
+        the transfer reads the source field (5 B per seed) and writes the
+        destination field (13 B: u, cost, flags); the final filter reads the
+        level-0 forward field (5 B per seed), writes its keep mask (1 B per
+        seed) and the match rows (16 B each)."""
+    L, sig = prm["levels"], prm["seed_stride"]
+    C = 3 if prm["color"] == 1 else 1
+    nsch = 2 if (C == 3 and prm.get("cs_sched", 0) == 0) else 1
+    dims = [(w, h)]
+    for _ in range(1, L):
+        dims.append(((dims[-1][0] + 1) // 2, (dims[-1][1] + 1) // 2))
+    px = sum(a * b for a, b in dims)
+    pyr = 2 * pairs * (3 * w * h + nsch * 2 * (2 * C) * 2 * px)
+    c = sig // 2
+    n = [((a - 1 - c) // sig + 1) * ((b - 1 - c) // sig + 1) for a, b in dims]
+    seq = visit_levels(L, prm.get("refine_rounds", 2))
+    f = 0
+    for v, l in enumerate(seq):
+        f += 2 * n[l] * (5 + 5 + 1)                      # consistency, both directions
+        if v > 0:
+            f += 2 * (n[seq[v - 1]] * 5 + n[l] * 13)     # transfer, both directions
+    f += n[0] * (5 + 1)                                  # final filter (per pair)
+    return {"pyramid": pyr, "fields": pairs * f + 16 * matches_total}
+
+
+def measured_hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
 # ------------------------------------------------------------- multi-rank
 def rank_seeds(rank, batch):
     """Synthetic pair seeds of one rank: disjoint across ranks."""
@@ -345,6 +395,16 @@ def run_ours(a):
     el_pm = sum(e["pm"][0] * PARAMS["patch_fwd"] ** 2 * nch + e["pm"][1] * PARAMS["patch_bwd"] ** 2 * nch
                 for e in ev_counts)                     # per step
     pm_launch_ms = kernel_ms["pm"] / max(1, kernel_launches["pm"])
+    hb = hbm_stage_bytes(PARAMS, W_IMG, H_IMG, B, sum(counts))
+    hpeak, hsrc = measured_hbm_peak()
+    hbm_stages = {"peak_GBps": hpeak, "peak_source": hsrc + " (copy bandwidth)",
+                  "note": "compulsory bytes per step over the stage's kernel time from the "
+                          "profiling pass (definitions in bench.hbm_stage_bytes)"}
+    for name, ms in (("pyramid", kernel_ms["pyramid"]),
+                     ("fields", kernel_ms["consist"] + kernel_ms["transfer"] + kernel_ms["filter"])):
+        gbs = hb[name] / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        hbm_stages[name] = {"bytes_per_step": hb[name], "ms_per_step": ms, "GBps": gbs,
+                            "frac": gbs / hpeak}
     el_per_launch = el_pm / max(1, kernel_launches["pm"])
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -413,6 +473,7 @@ def run_ours(a):
                          "l1_GBps": l1_gbs, "l1_peak_GBps": l1_peak, "l1_frac": l1_gbs / l1_peak,
                          "pm_ms_per_launch": pm_launch_ms,
                          "pm_launches_per_step": kernel_launches["pm"]},
+            "hbm_stages": hbm_stages,
             "kernel_ms_per_step": kernel_ms, "kernel_launches_per_step": kernel_launches,
             "evals_per_step": {"pm": sum(sum(e["pm"]) for e in ev_counts),
                                "cost": sum(sum(e["cost"]) for e in ev_counts),
