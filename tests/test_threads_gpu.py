@@ -65,3 +65,16 @@ def test_concurrent_host_threads(api):
         assert len(alone[k]) > 0
         for r in range(3):
             assert np.array_equal(out[k][r], alone[k]), (k, r)
+
+
+def test_many_caller_streams(api):
+    """More caller streams than the library keeps auxiliary stream sets for
+    (32 per host thread): calls on the later streams run without forking,
+    and every result still equals the first."""
+    p = api.Params(**PRM)
+    pair = synth.sintel_like_pair(7, W, H)
+    ref = _run(api, p, pair, 47, torch.cuda.Stream())
+    streams = [torch.cuda.Stream() for _ in range(40)]
+    for k, st in enumerate(streams):
+        got = _run(api, p, pair, 47, st)
+        assert np.array_equal(got, ref), k
