@@ -1333,7 +1333,9 @@ static int device_sms() {
 // per-seed kernel.  A small phase (at most one tile per resident CTA, the
 // coarse levels) runs both directions in one launch of the general
 // consumer; a larger one runs each direction in its own launch of the
-// consumer specialised for its layout.  *nlaunch: kernels launched.
+// consumer specialised for its layout, the backward one on st2 when given
+// (the two directions are independent within a phase).  *nlaunch: kernels
+// launched.
 pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int maxP, int* nlaunch,
                           bool* handled, cudaStream_t st, cudaStream_t st2) {
     (void)maxP;
