@@ -20,12 +20,14 @@
  *    and launch errors only; device-side failures are recorded in the
  *    workspace's error word and reported by pgm_sync_status().
  *  - pgm_match and pgm_match_batch fork part of their work onto two streams
- *    of the library's own (created once per host thread and device): the
- *    box sums of the finer levels and the backward direction's search
- *    phases.  Each fork starts from an event recorded on `stream` and is
- *    joined back to `stream` by an event wait before the call returns, so
- *    all of the call's work stays ordered on `stream` and is captured with
- *    it into a CUDA graph.
+ *    of the library's own: the box sums of the finer levels and the
+ *    backward direction's search phases.  The pair of streams belongs to
+ *    the caller's `stream` (created on first use, per host thread and
+ *    device, up to 32 caller streams per thread; calls on further streams
+ *    do not fork).  Each fork starts from an event recorded on `stream` and
+ *    is joined back to `stream` by an event wait before the call returns,
+ *    so all of the call's work stays ordered on `stream` and is captured
+ *    with it into a CUDA graph.
  *  - Nothing throws across the ABI.  Calls on different workspaces may run
  *    concurrently from different host threads.
  *  - Results are a deterministic function of (params, images, stream_id):
@@ -50,7 +52,7 @@ typedef enum {
     PGM_ERR_CUDA = 4,          /* a CUDA launch or API call failed            */
     PGM_ERR_TIMEOUT = 5,       /* a bounded device wait ran out               */
     PGM_ERR_DEVICE_BOUNDS = 6, /* a device-side index check failed            */
-    PGM_ERR_UNSUPPORTED = 7    /* valid but outside this build's limits       */
+    PGM_ERR_UNSUPPORTED = 7    /* valid but outside the library's limits      */
 } pgm_status;
 
 enum { PGM_GRAY = 0, PGM_RGB = 1 };                 /* params.color           */

@@ -465,7 +465,7 @@ const char* pgm_status_string(pgm_status s) {
     case PGM_ERR_CUDA: return "CUDA error";
     case PGM_ERR_TIMEOUT: return "device wait timed out";
     case PGM_ERR_DEVICE_BOUNDS: return "device-side bounds check failed";
-    case PGM_ERR_UNSUPPORTED: return "outside this build's limits";
+    case PGM_ERR_UNSUPPORTED: return "outside the library's limits";
     }
     return "unknown status";
 }
