@@ -1080,6 +1080,12 @@ k_cost_t(const __grid_constant__ LvlBatch B, const MatchConst mc) {
 // ===========================================================================
 // Host side: launch configuration.  No device code below this line.
 
+// The search kernel's parameters (batch, constants, schedule, tensor maps)
+// must fit the 32764-byte kernel parameter limit.
+static_assert(sizeof(LvlBatch) + sizeof(MatchConst) + sizeof(PtSched) + sizeof(PtMaps) +
+                  sizeof(int) + 256 <= 32764,
+              "k_pm_t parameters exceed the kernel parameter limit");
+
 // Per-thread caches keyed by device: the shared-memory opt-in of a kernel is a
 // per-device attribute, and calls may come from several host threads.
 static bool opt_in_smem(const void* kern, int smem, int* cfg_dev, int* configured) {
