@@ -227,3 +227,130 @@ def test_sector_pyramid_codes():
     for y in range(12):
         for x in range(17):
             assert (s[0, y, x], s[1, y, x]) == O.sector(int(g[0, y, x]), int(g[1, y, x]))
+
+
+# ---- Table 2 colour-space schedule and the level assembly (reading R1) ----
+# Table 2 of the paper, written out here independently of the oracle: the
+# colour space of each level (0, 1, 2) of the forward and the backward
+# gradient pyramid; reading R1 repeats the three columns for L > 3.
+TABLE2 = {0: (O.SP_RGB, O.SP_LAB, O.SP_YCRCB),       # forward pyramid
+          1: (O.SP_LAB, O.SP_YCRCB, O.SP_RGB)}       # backward pyramid
+
+
+def _brute_down(img):
+    """One pyramid step by the definition (5-tap binomial, +128 >> 8,
+    replicated border, even samples), vectorised over the output grid."""
+    h, w = img.shape
+    k = np.array([1, 4, 6, 4, 1], np.int64)
+    ys = np.arange((h + 1) // 2)[:, None]
+    xs = np.arange((w + 1) // 2)[None, :]
+    s = np.zeros((ys.shape[0], xs.shape[1]), np.int64)
+    for j in range(-2, 3):
+        for i in range(-2, 3):
+            yy = np.clip(2 * ys + j, 0, h - 1)
+            xx = np.clip(2 * xs + i, 0, w - 1)
+            s += k[j + 2] * k[i + 2] * img[yy, xx].astype(np.int64)
+    return ((s + 128) >> 8).astype(np.uint8)
+
+
+def test_brute_down_matches_loop_definition():
+    rng = np.random.default_rng(12)
+    img = rng.integers(0, 256, size=(7, 10), dtype=np.uint8)
+    k = [1, 4, 6, 4, 1]
+    out = _brute_down(img)
+    for y in range(out.shape[0]):
+        for x in range(out.shape[1]):
+            s = sum(k[i + 2] * k[j + 2] * int(img[brute.clamp(2 * y + j, 0, 6), brute.clamp(2 * x + i, 0, 9)])
+                    for i in range(-2, 3) for j in range(-2, 3))
+            assert out[y, x] == (s + 128) >> 8
+
+
+@pytest.mark.parametrize("L", [3, 6])
+def test_table2_schedule_and_level_assembly(L):
+    """Each level image of a colour pyramid is the RGB image pyramided by the
+    binomial step (in RGB), then converted to the Table 2 space of its level
+    and pyramid; the descriptor is the Sobel of that image, channels ordered
+    Gx of each colour channel then Gy of each.  A swapped row, a level off by
+    one or a conversion before the pyramid fails here."""
+    rng = np.random.default_rng(20 + L)
+    rgb = rng.integers(0, 256, size=(70, 83, 3), dtype=np.uint8)
+    planes = [[rgb[..., c] for c in range(3)]]
+    for _ in range(1, L):
+        planes.append([_brute_down(p) for p in planes[-1]])
+    prm = dict(levels=L, color=1, cs_sched=0, sobel=5)
+    P = O.Pyramid(prm, rgb)
+    assert P.schemes == 2 and P.channels == 3
+    for scheme in (0, 1):
+        for level in range(L):
+            lv = np.stack(planes[level], -1)
+            want = O.convert(TABLE2[scheme][level % 3], lv)
+            got = np.moveaxis(P.cimage(scheme, level), 0, -1)
+            assert got.shape == want.shape
+            assert (got == want).all(), (scheme, level)
+            d = P.desc(scheme, level)
+            for c in range(3):
+                gx, gy = O.sobel(np.ascontiguousarray(want[..., c]), 5)
+                assert (d[c] == gx).all() and (d[3 + c] == gy).all(), (scheme, level, c)
+    # the two properties the paper states for Table 2: within a pyramid any
+    # two of the three levels differ in space, and per level the forward and
+    # backward spaces differ
+    for s in (0, 1):
+        assert len(set(TABLE2[s])) == 3
+    assert all(TABLE2[0][l] != TABLE2[1][l] for l in range(3))
+
+
+def test_gray_and_plain_schedules():
+    """PGM-G/GD: the image is converted to gray first and one gray pyramid
+    serves both directions (reading R19); the plain schedule keeps RGB at every
+    level."""
+    rng = np.random.default_rng(31)
+    rgb = rng.integers(0, 256, size=(41, 29, 3), dtype=np.uint8)
+    g = O.convert(O.SP_GRAY, rgb)
+    want = [g]
+    for _ in range(2):
+        want.append(_brute_down(want[-1]))
+    P = O.Pyramid(dict(levels=3, color=0), rgb)
+    assert P.schemes == 1 and P.channels == 1
+    for l in range(3):
+        assert (P.cimage(0, l)[0] == want[l]).all()
+    Pp = O.Pyramid(dict(levels=3, color=1, cs_sched=1), rgb)
+    assert Pp.schemes == 1
+    lv = [rgb[..., c] for c in range(3)]
+    for l in range(3):
+        assert (np.moveaxis(Pp.cimage(0, l), 0, -1) == np.stack(lv, -1)).all()
+        lv = [_brute_down(p) for p in lv]
+
+
+# ---- direction-only descriptor G ./ |G| (reading R5) ----------------------
+def test_direction_sign_closed_forms():
+    """A ramp increasing along x has Gx > 0 and Gy = 0 everywhere (also at the
+    replicated border), so its direction code is (+1, 0); a decreasing ramp
+    gives (-1, 0); a ramp along y gives (0, +1); a constant gives 0 (0/0 := 0)."""
+    h, w = 9, 14
+    ramp = np.tile((np.arange(w) * 7).astype(np.uint8), (h, 1))
+    for S in (3, 5):
+        prm = dict(levels=1, color=0, descriptor=1, sobel=S)
+        d = O.Pyramid(prm, ramp).desc(0, 0)
+        assert (d[0] == 1).all() and (d[1] == 0).all()
+        d = O.Pyramid(prm, ramp[:, ::-1].copy()).desc(0, 0)
+        assert (d[0] == -1).all() and (d[1] == 0).all()
+        d = O.Pyramid(prm, np.ascontiguousarray(ramp.T)).desc(0, 0)
+        assert (d[0] == 0).all() and (d[1] == 1).all()
+        d = O.Pyramid(prm, np.full((h, w), 77, np.uint8)).desc(0, 0)
+        assert not d.any()
+
+
+@pytest.mark.parametrize("color", [0, 1])
+def test_direction_equals_sign_of_full_descriptor(color):
+    """descriptor = 1 is exactly the elementwise sign of descriptor = 0, channel
+    by channel, at every level and in both colour schemes."""
+    rng = np.random.default_rng(40 + color)
+    shape = (37, 52, 3) if color else (37, 52)
+    img = rng.integers(0, 256, size=shape, dtype=np.uint8)
+    full = O.Pyramid(dict(levels=3, color=color, descriptor=0), img)
+    dirn = O.Pyramid(dict(levels=3, color=color, descriptor=1), img)
+    for s in range(full.schemes):
+        for l in range(3):
+            f, d = full.desc(s, l), dirn.desc(s, l)
+            assert set(np.unique(d)) <= {-1, 0, 1}
+            assert (d == np.sign(f)).all(), (s, l)
