@@ -161,23 +161,26 @@ def test_cost_non_increasing_within_visit():
 
 
 @pytest.mark.slow
-def test_checkerboard_vs_sequential_margins():
-    """The checkerboard order is a reordering of the paper's scan: on the
-    noise-affine workload the two must agree statistically (frozen margins:
-    mean end-point error within 0.25 px, outlier rate within 2 points, inlier
-    count within 5 %)."""
-    prm = dict(levels=3, seed_stride=3, patch_fwd=8, patch_bwd=8, iters_coarse=6, iters_fine=6)
-    for seed in range(3):
-        f1, f2, gt = synth.noise_affine_pair(seed)
-        stats = []
-        for sched in (O.SCHED_CHECKERBOARD, O.SCHED_SEQUENTIAL):
-            _, _, M, rows = O.run_pair(prm, f1, f2, schedule=sched)
-            f = M.field(0, 0)
-            ny, nx = f["ux"].shape
-            jj, ii = np.mgrid[0:ny, 0:nx]
-            g = gt[1 + 3 * jj, 1 + 3 * ii]
-            inl = f["outlier"] == 0
-            epe = np.hypot(f["ux"] - g[..., 0], f["uy"] - g[..., 1])[inl]
-            stats.append((epe.mean(), (epe > 3).mean(), inl.sum()))
-        (e0, o0, n0), (e1, o1, n1) = stats
-        assert abs(e0 - e1) <= 0.25 and abs(o0 - o1) <= 0.02 and abs(n0 - n1) <= 0.05 * max(n0, n1)
+@pytest.mark.parametrize("name", ["c1", "c2", "c3"])
+def test_checkerboard_vs_sequential_margins(name):
+    """The checkerboard order reorders the paper's scan (Sec. III-B), so it
+    must not lose accuracy against it.  Per workload, on 10 seeds: the
+    checkerboard at the calibrated iteration counts against the paper's
+    sequential scan at the paper's counts (Sec. IV).  Frozen margins, one-sided
+    (both schedules are local searches of Eq. 3-5 and either may end in the
+    better optimum): mean end-point error of the inliers at most 0.25 px
+    higher, share of inliers with EPE > 3 px at most 2 points higher, at most
+    5 % fewer inliers."""
+    import multiprocessing as mp
+    import margins
+    jobs = []
+    for seed in range(10):
+        jobs.append((name, seed, O.SCHED_CHECKERBOARD, margins.CALIBRATED[name]))
+        jobs.append((name, seed, O.SCHED_SEQUENTIAL, {}))
+    with mp.get_context("spawn").Pool(min(8, mp.cpu_count())) as pool:
+        res = pool.map(margins.stats, jobs)
+    for seed in range(10):
+        (e0, o0, n0), (e1, o1, n1) = res[2 * seed], res[2 * seed + 1]
+        assert e0 - e1 <= 0.25, (seed, e0, e1)
+        assert o0 - o1 <= 0.02, (seed, o0, o1)
+        assert n0 >= 0.95 * n1, (seed, n0, n1)
