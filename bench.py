@@ -111,10 +111,10 @@ def pm_traffic_per_launch(pairs, launches):
     """DRAM bytes per k_pm_t launch: the committed ncu record's bytes over all
     search launches of one step, scaled to `pairs` per step and divided by
     this step's `launches`; None when the device code of the search kernel
-    (pm_tile.cu above its host-side section) changed since the capture."""
+    (pm_row.cu above its host-side section) changed since the capture."""
     import hashlib
     rec = os.path.join(ROOT, "profiles", "k_pm_t_traffic.json")
-    src = os.path.join(ROOT, "paper_1704_03217_gb300", "csrc", "pm_tile.cu")
+    src = os.path.join(ROOT, "paper_1704_03217_gb300", "csrc", "pm_row.cu")
     mark = "// Host side: launch configuration.  No device code below this line.\n"
     try:
         r = json.load(open(rec))

@@ -136,12 +136,16 @@ pgm_status pgm_build_pyramid_batch(const pgm_params* p, int n, const uint8_t* co
 
 /* Where one level's descriptor lives inside a pyramid buffer (for tests and
  * tools): int16 values, pixel-interleaved, `nch` = 2C channels per pixel in
- * the order Gx of each colour channel, then Gy of each; rows `row_elems`
- * int16 apart.  scheme 0 serves the forward field, 1 the backward field
- * (equal to 0 unless PGM_RGB with PGM_CS_PAPER). */
+ * the order Gx of each colour channel, then Gy of each, pixels `px_elems`
+ * int16 apart (8 for 6 channels, the last two zero; 2 for 2 channels), rows
+ * `row_elems` int16 apart.  offset_bytes locates pixel (0, 0); the array has
+ * a border of `border` pixels on every side that repeats the nearest image
+ * pixel (Sec. III-B patches read outside the image take the border value).
+ * scheme 0 serves the forward field, 1 the backward field (equal to 0 unless
+ * PGM_RGB with PGM_CS_PAPER). */
 pgm_status pgm_pyramid_desc_layout(const pgm_params* p, int w, int h, int scheme, int level,
                                    size_t* offset_bytes, int* lw, int* lh, int* nch,
-                                   int* row_elems);
+                                   int* row_elems, int* px_elems, int* border);
 /* Where one level's colour-converted uint8 image lives: C planes of lh rows,
  * rows `row_bytes` apart, planes `plane_bytes` apart. */
 pgm_status pgm_pyramid_image_layout(const pgm_params* p, int w, int h, int scheme, int level,
@@ -269,9 +273,9 @@ pgm_status pgm_sync_status(const pgm_params* p, int w1, int h1, int w2, int h2, 
  * [8, 72) eight uint64 counters of patch distances (Eq. 3) actually
  * evaluated: propagation/search forward, backward; cost refresh forward,
  * backward; exhaustive initialisation forward, backward; and, of the
- * propagation/search ones, those scored outside the shared-memory window
- * (from global memory) forward, backward.  pgm_match and pgm_match_batch
- * zero them at their start. */
+ * propagation/search and refresh ones, those scored outside the
+ * shared-memory window (from global memory) forward, backward.  pgm_match
+ * and pgm_match_batch zero them at their start. */
 #define PGM_WS_EVALS_OFFSET 8
 #define PGM_WS_EVALS_COUNT 8
 
@@ -311,6 +315,16 @@ typedef struct {
 /* NULL restores the defaults.  Errors: PGM_ERR_ARG (value out of range). */
 pgm_status pgm_set_tuning(const pgm_tuning* t);
 pgm_status pgm_get_tuning(pgm_tuning* t);
+
+/* Limit, in SM clock cycles, of every bounded wait inside the search kernel
+ * (a consumer waiting for a staged tile, the producer waiting for a free
+ * buffer); 0 restores the default of 2^31 cycles (about a second).  A wait
+ * that runs out sets PGM_ERR_TIMEOUT in the workspace status word
+ * (pgm_sync_status) and ends the kernel's work early; the copies already in
+ * flight are still waited for (with the default limit) before a block exits.
+ * Process-wide; meant for failure-detection tests (a limit of a few cycles
+ * makes the first wait run out).  Errors: PGM_ERR_ARG (cycles < 0). */
+pgm_status pgm_set_wait_limit(int64_t cycles);
 
 /* Nominal candidate evaluations of one pair under params (2 propagation + K
  * random-search candidates per seed and iteration, one cost per seed and

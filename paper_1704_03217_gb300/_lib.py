@@ -32,7 +32,7 @@ EXPORTS = [
     "pgm_match", "pgm_match_batch", "pgm_field_layout", "pgm_filter", "pgm_sync_status",
     "pgm_nominal_evals", "pgm_launch_count", "pgm_profile_enable", "pgm_profile_read",
     "pgm_filter_noalloc", "pgm_build_pyramid_batch", "pgm_filter_batch", "pgm_set_tuning",
-    "pgm_get_tuning",
+    "pgm_get_tuning", "pgm_set_wait_limit",
 ]
 
 
@@ -67,7 +67,7 @@ def load(path: str = LIB_PATH):
     L.pgm_status_string.argtypes = [i32]; L.pgm_status_string.restype = C.c_char_p
     L.pgm_pyramid_bytes.argtypes = [P, i32, i32]; L.pgm_pyramid_bytes.restype = sz
     L.pgm_build_pyramid.argtypes = [P, vp, i32, i32, i32, sz, vp, sz, vp]
-    L.pgm_pyramid_desc_layout.argtypes = [P, i32, i32, i32, i32, psz, pi, pi, pi, pi]
+    L.pgm_pyramid_desc_layout.argtypes = [P, i32, i32, i32, i32, psz, pi, pi, pi, pi, pi, pi]
     L.pgm_pyramid_image_layout.argtypes = [P, i32, i32, i32, i32, psz, pi, pi, pi, pi, psz]
     L.pgm_match_workspace_bytes.argtypes = [P, i32, i32, i32, i32]
     L.pgm_match_workspace_bytes.restype = sz
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
     L.pgm_filter_noalloc.argtypes = [P, i32, i32, vp, vp, vp, i64, vp, vp]
     L.pgm_set_tuning.argtypes = [C.POINTER(CTuning)]; L.pgm_set_tuning.restype = C.c_int
     L.pgm_get_tuning.argtypes = [C.POINTER(CTuning)]; L.pgm_get_tuning.restype = C.c_int
+    L.pgm_set_wait_limit.argtypes = [C.c_int64]; L.pgm_set_wait_limit.restype = C.c_int
     L.pgm_build_pyramid_batch.argtypes = [P, i32, C.POINTER(vp), C.POINTER(C.c_int32), psz,
                                           C.POINTER(vp), psz, vp]
     L.pgm_filter_batch.argtypes = [P, i32, C.POINTER(C.c_int32), C.POINTER(vp), psz,

@@ -85,15 +85,32 @@ class Pyramid:
             "pgm_build_pyramid")
         return self
 
-    def desc(self, scheme: int, level: int) -> torch.Tensor:
-        """(lh, lw, 2C) int16 view: Gx of each channel, then Gy of each."""
+    def desc_layout(self, scheme: int, level: int) -> dict:
         off, lw, lh, nch, row = C.c_size_t(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        pxe, bord = C.c_int(), C.c_int()
         check(_lib.load().pgm_pyramid_desc_layout(C.byref(self._cp), self.w, self.h, scheme,
                                                   level, C.byref(off), C.byref(lw), C.byref(lh),
-                                                  C.byref(nch), C.byref(row)),
+                                                  C.byref(nch), C.byref(row), C.byref(pxe),
+                                                  C.byref(bord)),
               "pgm_pyramid_desc_layout")
-        v = self.buf[off.value:off.value + 2 * row.value * lh.value].view(torch.int16)
-        return v.view(lh.value, row.value)[:, :lw.value * nch.value].reshape(lh.value, lw.value, nch.value)
+        return dict(offset=off.value, w=lw.value, h=lh.value, nch=nch.value, row=row.value,
+                    px=pxe.value, border=bord.value)
+
+    def desc_padded(self, scheme: int, level: int) -> torch.Tensor:
+        """(lh + 2 B, lw + 2 B, 2C) int16 view of the descriptor with its
+        replicated border of B pixels."""
+        d = self.desc_layout(scheme, level)
+        B, row, px = d["border"], d["row"], d["px"]
+        start = d["offset"] - 2 * (B * row + B * px)
+        v = self.buf[start:start + 2 * row * (d["h"] + 2 * B)].view(torch.int16)
+        v = v.view(d["h"] + 2 * B, row)[:, :(d["w"] + 2 * B) * px]
+        return v.reshape(d["h"] + 2 * B, d["w"] + 2 * B, px)[..., :d["nch"]]
+
+    def desc(self, scheme: int, level: int) -> torch.Tensor:
+        """(lh, lw, 2C) int16 view: Gx of each channel, then Gy of each."""
+        d = self.desc_layout(scheme, level)
+        B = d["border"]
+        return self.desc_padded(scheme, level)[B:B + d["h"], B:B + d["w"]]
 
     def cimage(self, scheme: int, level: int) -> torch.Tensor:
         """(C, lh, lw) uint8 view of the colour-converted level image."""

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpgm.so")
-SOURCES = ["abi.cu", "pyramid.cu", "match.cu", "pm_tile.cu", "init_tile.cu", "filter.cu",
+SOURCES = ["abi.cu", "pyramid.cu", "match.cu", "pm_row.cu", "init_tile.cu", "filter.cu",
            "filter_noalloc.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

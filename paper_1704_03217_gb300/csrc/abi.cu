@@ -16,6 +16,11 @@ static std::atomic<long long> g_launches{0};
 static std::atomic<int> g_slack{2}, g_chunk{MAXB};
 Tuning tuning() { return Tuning{g_slack.load(), g_chunk.load()}; }
 
+// bounded device waits (the search kernel's mbarrier waits), in SM cycles
+constexpr long long WAIT_DEFAULT = 1ll << 31;        // about 1 s at 2 GHz
+static std::atomic<long long> g_wait{WAIT_DEFAULT};
+long long wait_limit() { return g_wait.load(); }
+
 namespace {
 struct ProfEvent { int cls; int n; cudaEvent_t a, b; };
 struct ProfState {
@@ -96,6 +101,7 @@ bool make_pyr_plan(const pgm_params* p, int w, int h, PyrPlan* pp) {
     pp->C = p->color == PGM_RGB ? 3 : 1;
     pp->nch = 2 * pp->C;
     pp->nsch = (p->color == PGM_RGB && p->cs_sched == PGM_CS_PAPER) ? 2 : 1;
+    pp->pxw = px_words(pp->nch);
     size_t off = 0;
     for (int l = 0; l < pp->L; ++l) {
         pp->W[l] = l == 0 ? w : (pp->W[l - 1] + 1) / 2;
@@ -104,7 +110,8 @@ bool make_pyr_plan(const pgm_params* p, int w, int h, PyrPlan* pp) {
         pp->img_plane[l] = (size_t)pp->img_row[l] * pp->H[l];
         pp->img_off[l] = off;
         off = align_up(off + pp->img_plane[l] * pp->C, 256);
-        pp->desc_row[l] = (int)align_up((size_t)pp->W[l] * pp->nch, 8);
+        // padded row: W + 2 BORD pixels of 2 pxw int16 values, 16-byte multiple
+        pp->desc_row[l] = (int)align_up((size_t)(pp->W[l] + 2 * BORD) * 2 * pp->pxw, 8);
     }
     for (int s = 0; s < pp->nsch; ++s)
         for (int l = 0; l < pp->L; ++l) {
@@ -116,10 +123,15 @@ bool make_pyr_plan(const pgm_params* p, int w, int h, PyrPlan* pp) {
             } else {
                 pp->cimg_off[s][l] = pp->img_off[l];
             }
-            pp->desc_off[s][l] = off;
-            off = align_up(off + (size_t)pp->desc_row[l] * pp->H[l] * 2, 256);
-            pp->split_off[s][l] = off;
-            off = align_up(off + (size_t)pp->desc_row[l] * pp->H[l] * 2, 256);
+            // the padded arrays; pixel (0, 0) sits BORD rows and BORD pixels in
+            const size_t arr = (size_t)pp->desc_row[l] * (pp->H[l] + 2 * BORD) * 2;
+            const size_t inner = ((size_t)BORD * pp->desc_row[l] + (size_t)BORD * 2 * pp->pxw) * 2;
+            pp->desc_pad_off[s][l] = off;
+            pp->desc_off[s][l] = off + inner;
+            off = align_up(off + arr, 256);
+            pp->split_pad_off[s][l] = off;
+            pp->split_off[s][l] = off + inner;
+            off = align_up(off + arr, 256);
         }
     for (int s = pp->nsch; s < 2; ++s)
         for (int l = 0; l < pp->L; ++l) {
@@ -127,6 +139,8 @@ bool make_pyr_plan(const pgm_params* p, int w, int h, PyrPlan* pp) {
             pp->cimg_off[s][l] = pp->cimg_off[0][l];
             pp->desc_off[s][l] = pp->desc_off[0][l];
             pp->split_off[s][l] = pp->split_off[0][l];
+            pp->desc_pad_off[s][l] = pp->desc_pad_off[0][l];
+            pp->split_pad_off[s][l] = pp->split_pad_off[0][l];
         }
     pp->bytes = off + 256;     // tail slack: vector loads never leave the buffer
     return true;
@@ -150,7 +164,9 @@ bool make_ws_plan(const pgm_params* p, int w1, int h1, int w2, int h2, WsPlan* w
             wp->off_flags[l][d] = off; off = align_up(off + n, 256);
             wp->off_sa2[l][d] = off;   off = align_up(off + 8 * n, 256);
             const PyrPlan& t = d == 0 ? b : a;       // target image of this direction
-            wp->off_sb2[l][d] = off;   off = align_up(off + 8 * (size_t)t.W[l] * t.H[l], 256);
+            wp->sbp[l][d] = (t.W[l] + 1) & ~1;         // even: 16-byte rows for tensor copies
+            wp->off_sb2[l][d] = off;
+            off = align_up(off + 8 * (size_t)wp->sbp[l][d] * t.H[l], 256);
             wp->off_sa2img[l][d] = off;
             off = align_up(off + 8 * (size_t)r.W[l] * r.H[l], 256);
         }
@@ -208,7 +224,7 @@ void fill_dir(const pgm_params* p, const PairCtx& c, int l, int d, DirLvl* D) {
     D->nx = c.w.nx[l][d]; D->ny = c.w.ny[l][d];
     D->onx = c.w.nx[l][1 - d]; D->ony = c.w.ny[l][1 - d];
     D->P = d == 0 ? p->patch_fwd : p->patch_bwd;
-    D->pad = 0;
+    D->sbp = c.w.sbp[l][d];
     D->u = reinterpret_cast<int32_t*>(c.ws + c.w.off_u[l][d]);
     D->cost = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_cost[l][d]);
     D->flags = c.ws + c.w.off_flags[l][d];
@@ -532,12 +548,15 @@ pgm_status pgm_build_pyramid_batch(const pgm_params* p, int n, const uint8_t* co
 
 pgm_status pgm_pyramid_desc_layout(const pgm_params* p, int w, int h, int scheme, int level,
                                    size_t* offset_bytes, int* lw, int* lh, int* nch,
-                                   int* row_elems) {
+                                   int* row_elems, int* px_elems, int* border) {
     PyrPlan pp;
     if (!make_pyr_plan(p, w, h, &pp) || scheme < 0 || scheme > 1 || level < 0 ||
-        level >= pp.L || !offset_bytes || !lw || !lh || !nch || !row_elems) return PGM_ERR_ARG;
+        level >= pp.L || !offset_bytes || !lw || !lh || !nch || !row_elems || !px_elems ||
+        !border) return PGM_ERR_ARG;
     *offset_bytes = pp.desc_off[scheme][level];
     *lw = pp.W[level]; *lh = pp.H[level]; *nch = pp.nch; *row_elems = pp.desc_row[level];
+    *px_elems = 2 * pp.pxw;
+    *border = BORD;
     return PGM_OK;
 }
 
@@ -693,6 +712,12 @@ pgm_status pgm_set_tuning(const pgm_tuning* t) {
         t->pairs_per_launch > MAXB) return PGM_ERR_ARG;
     g_slack = t->window_slack;
     g_chunk = t->pairs_per_launch;
+    return PGM_OK;
+}
+
+pgm_status pgm_set_wait_limit(int64_t cycles) {
+    if (cycles < 0) return PGM_ERR_ARG;
+    g_wait = cycles == 0 ? WAIT_DEFAULT : (long long)cycles;
     return PGM_OK;
 }
 

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(IN_THREADS) k_init_t(const __grid_constant__ L
     for (int e = threadIdx.x; e < tph * tp; e += IN_THREADS) {
         const int r = e / tp, c = e - r * tp, px = c / WPP, wi = c - px * WPP;
         const int x = clampi(px - h, 0, D.tw - 1), y = clampi(r - h, 0, D.th - 1);
-        sT[e] = __ldg(t32 + (size_t)y * tpitch + (size_t)x * WPP + wi);
+        sT[e] = __ldg(t32 + (size_t)y * tpitch + (size_t)x * px_words(NCH) + wi);
     }
     const int rpitch = D.ref_pitch >> 1;
     for (int e = threadIdx.x; e < IN_SB * rw; e += IN_THREADS) {
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(IN_THREADS) k_init_t(const __grid_constant__ L
         const int si = s % D.nx, sj = s / D.nx;
         const int x = clampi(mc.c + sig * si + px - h, 0, D.rw - 1);
         const int y = clampi(mc.c + sig * sj + row - h, 0, D.rh - 1);
-        sR[e] = __ldg(D.ref_split + (size_t)y * rpitch + (size_t)x * WPP + wi);
+        sR[e] = __ldg(D.ref_split + (size_t)y * rpitch + (size_t)x * px_words(NCH) + wi);
     }
     __syncthreads();
 
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(IN_THREADS) k_init_t(const __grid_constant__ L
         for (int p = 0; p < IN_PB; ++p) {
             const int q = q0 + p * IN_THREADS;
             if (q >= nq) continue;
-            const unsigned long long sb = D.sb2[q];
+            const unsigned long long sb = D.sb2[(size_t)(q / D.tw) * D.sbp + q % D.tw];
 #pragma unroll
             for (int k = 0; k < IN_SB; ++k) {
                 const unsigned long long c = xcost(sa[k], sb, acc[p][k]);

@@ -37,7 +37,7 @@ __device__ __forceinline__ void load_ref(Ref<NCH, PPL>& R, const DirLvl& D, int 
         R.oy[m] = kk / P - h;
         int x = clampi(px + R.ox[m], 0, D.rw - 1), y = clampi(py + R.oy[m], 0, D.rh - 1);
         const uint32_t* w = reinterpret_cast<const uint32_t*>(D.ref + (size_t)y * D.ref_pitch +
-                                                              (size_t)x * NCH);
+                                                              (size_t)x * 2 * px_words(NCH));
 #pragma unroll
         for (int c = 0; c < NCH / 2; ++c) {
             uint32_t v = (k < P * P) ? __ldg(w + c) : 0u;
@@ -57,7 +57,7 @@ __device__ __forceinline__ unsigned long long warp_cost(const Ref<NCH, PPL>& R, 
         if (lane + 32 * m < P2) {
             int x = clampi(qx + R.ox[m], 0, D.tw - 1), y = clampi(qy + R.oy[m], 0, D.th - 1);
             const uint32_t* w = reinterpret_cast<const uint32_t*>(
-                D.tgt + (size_t)y * D.tgt_pitch + (size_t)x * NCH);
+                D.tgt + (size_t)y * D.tgt_pitch + (size_t)x * 2 * px_words(NCH));
             uint32_t s = 0;
 #pragma unroll
             for (int c = 0; c < NCH / 2; ++c) {
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_box(const __grid_constant__ LvlBatch B)
         const uint32_t* row = reinterpret_cast<const uint32_t*>(
             img + (size_t)clampi(y0 - h + r, 0, hh - 1) * pitch);
         for (int c = threadIdx.x & 31; c < iw; c += 32) {
-            const uint32_t* px = row + (size_t)clampi(x0 - h + c, 0, w - 1) * (NCH / 2);
+            const uint32_t* px = row + (size_t)clampi(x0 - h + c, 0, w - 1) * px_words(NCH);
             uint32_t n = 0;
 #pragma unroll
             for (int c2 = 0; c2 < NCH / 2; ++c2) {
@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(256) k_box(const __grid_constant__ LvlBatch B)
     // column sums: thread -> (column, run of BOX_RUN rows); a warp covers 32
     // consecutive columns, so the stores of one row are coalesced
     unsigned long long* out = ref ? D.sa2img : D.sb2;
+    const int opitch = ref ? w : D.sbp;
     constexpr int RUNS_Y = BOX_TH / BOX_RUN;
     for (int e = threadIdx.x; e < BOX_TW * RUNS_Y; e += blockDim.x) {
         const int c = e % BOX_TW, r0 = (e / BOX_TW) * BOX_RUN, x = x0 + c;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(256) k_box(const __grid_constant__ LvlBatch B)
         for (int k = 0; k < BOX_RUN; ++k) {
             if (k > 0) s += sR[r0 + k + P - 1][c] - sR[r0 + k - 1][c];
             const int y = y0 + r0 + k;
-            if (x < w && y < hh) out[(size_t)y * w + x] = s;
+            if (x < w && y < hh) out[(size_t)y * opitch + x] = s;
         }
     }
 }
@@ -169,8 +170,8 @@ __device__ __forceinline__ void fill_offsets(int* s_off, const DirLvl& D) {
     constexpr int WPP = NCH / 2;
     const int wpr = D.P * WPP, nw = D.P * wpr, pitchw = D.tgt_pitch >> 1;
     for (int k = threadIdx.x; k < 32 * MMAX; k += blockDim.x) {
-        const int row = k / wpr, col = k - row * wpr;
-        s_off[k] = k < nw ? row * pitchw + col : 0;
+        const int row = k / wpr, col = k - row * wpr, pix = col / WPP, wi = col - pix * WPP;
+        s_off[k] = k < nw ? row * pitchw + pix * px_words(NCH) + wi : 0;
     }
 }
 
@@ -192,7 +193,7 @@ __device__ __forceinline__ unsigned long long xload_ref(XRef<MMAX>& R, const Dir
             const int row = k / wpr, col = k - row * wpr;
             const int pix = col / WPP, wi = col - pix * WPP;
             const int x = clampi(px - h + pix, 0, D.rw - 1), y = clampi(py - h + row, 0, D.rh - 1);
-            const uint32_t v = __ldg(ref32 + (size_t)y * rpitchw + (size_t)x * WPP + wi);
+            const uint32_t v = __ldg(ref32 + (size_t)y * rpitchw + (size_t)x * px_words(NCH) + wi);
             const int a0 = lo16(v), a1 = hi16(v);
             R.b[m] = split_bytes(a0, a1);
             if (WANT_SA2) sa += (uint32_t)(a0 * a0) + (uint32_t)(a1 * a1);
@@ -212,7 +213,7 @@ __device__ __forceinline__ long long xcross(const XRef<MMAX>& R, const int* s_of
     const int x0 = qx - h, y0 = qy - h;
     int sl = 0, sh = 0;
     if (x0 >= 0 && y0 >= 0 && x0 + P <= D.tw && y0 + P <= D.th) {
-        const uint32_t* base = t32 + (size_t)y0 * pitchw + (size_t)x0 * WPP;
+        const uint32_t* base = t32 + (size_t)y0 * pitchw + (size_t)x0 * px_words(NCH);
         constexpr int CH = MMAX < 8 ? MMAX : 8;      // loads in flight per chunk
 #pragma unroll
         for (int m0 = 0; m0 < MMAX; m0 += CH) {
@@ -235,7 +236,7 @@ __device__ __forceinline__ long long xcross(const XRef<MMAX>& R, const int* s_of
                 const int row = k / wpr, col = k - row * wpr;
                 const int pix = col / WPP, wi = col - pix * WPP;
                 const int x = clampi(x0 + pix, 0, D.tw - 1), y = clampi(y0 + row, 0, D.th - 1);
-                const uint32_t v = __ldg(t32 + (size_t)y * pitchw + (size_t)x * WPP + wi);
+                const uint32_t v = __ldg(t32 + (size_t)y * pitchw + (size_t)x * px_words(NCH) + wi);
                 sl = __dp2a_lo((int)v, R.b[m], sl);
                 sh = __dp2a_hi((int)v, R.b[m], sh);
             }
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(256, 3) k_cost_x(const __grid_constant__ LvlBa
         if (lane == 0) D.flags[s] = f & ~F_VALID;
         return;
     }
-    const unsigned long long sb = D.sb2[(size_t)qy * D.tw + qx];
+    const unsigned long long sb = D.sb2[(size_t)qy * D.sbp + qx];
     const long long cr = xcross<NCH, MMAX>(R, s_off, D, qx, qy, lane);
     if (lane == 0) {
         D.cost[s] = xcost(sa, sb, cr);
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(256, 3) k_pm_x(const __grid_constant__ LvlBatc
         if (have && cu == bu) continue;
         const int qx = px + lo16(cu), qy = py + hi16(cu);
         if (!inside(D, qx, qy)) continue;
-        const unsigned long long sb = D.sb2[(size_t)qy * D.tw + qx];
+        const unsigned long long sb = D.sb2[(size_t)qy * D.sbp + qx];
         if (!loaded) { xload_ref<NCH, MMAX, false>(R, D, px, py, lane); loaded = true; }
         const unsigned long long c = xcost(sa, sb, xcross<NCH, MMAX>(R, s_off, D, qx, qy, lane));
         ++n_eval;
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(256, 3) k_pm_x(const __grid_constant__ LvlBatc
         const int cx = ux0 + dx, cy = uy0 + dy;
         const int qx = px + cx, qy = py + cy;
         if (!inside(D, qx, qy)) continue;
-        const unsigned long long sb = D.sb2[(size_t)qy * D.tw + qx];
+        const unsigned long long sb = D.sb2[(size_t)qy * D.sbp + qx];
         if (!loaded) { xload_ref<NCH, MMAX, false>(R, D, px, py, lane); loaded = true; }
         const unsigned long long c = xcost(sa, sb, xcross<NCH, MMAX>(R, s_off, D, qx, qy, lane));
         ++n_eval;
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(256) k_init(const __grid_constant__ LvlBatch B
     for (int k = threadIdx.x; k < P2; k += blockDim.x) {
         int x = clampi(px + k % P - h, 0, D.rw - 1), y = clampi(py + k / P - h, 0, D.rh - 1);
         const uint32_t* w = reinterpret_cast<const uint32_t*>(D.ref + (size_t)y * D.ref_pitch +
-                                                              (size_t)x * NCH);
+                                                              (size_t)x * 2 * px_words(NCH));
 #pragma unroll
         for (int c = 0; c < NCH / 2; ++c) {
             uint32_t v = __ldg(w + c);
@@ -397,7 +398,7 @@ __global__ void __launch_bounds__(256) k_init(const __grid_constant__ LvlBatch B
             const int16_t* row = D.tgt + (size_t)y * D.tgt_pitch;
             for (int ox = 0; ox < P; ++ox) {
                 const int x = clampi(qx + ox - h, 0, D.tw - 1);
-                const uint32_t* w = reinterpret_cast<const uint32_t*>(row + (size_t)x * NCH);
+                const uint32_t* w = reinterpret_cast<const uint32_t*>(row + (size_t)x * 2 * px_words(NCH));
                 const int* r = ref[oy * P + ox];
                 uint32_t sacc = 0;
 #pragma unroll

@@ -13,6 +13,12 @@ constexpr int MAXL = 12;         // pyramid levels supported
 constexpr int MAXB = 32;         // pairs per batched launch
 constexpr int MAXP = 16;         // largest patch side
 constexpr int MAXVIS = 4 * MAXL + 2 * 64 + 4;
+// Descriptor arrays carry a replicated border of BORD pixels on every side,
+// so that any patch (P <= MAXP) whose centre lies inside the image can be
+// read without clamping.  A colour pixel takes 4 words (6 int16 values and
+// one zero word, 16 bytes), a gray pixel 1 word.
+constexpr int BORD = MAXP / 2;
+__host__ __device__ constexpr int px_words(int nch) { return nch == 2 ? 1 : 4; }
 
 // seed flag bits
 constexpr uint8_t F_VALID = 1;   // field initialised at this seed
@@ -32,9 +38,12 @@ struct PyrPlan {
     size_t img_plane[MAXL];      // bytes per plane
     int space[2][MAXL];
     size_t cimg_off[2][MAXL];    // colour-converted image (aliases img if identity)
-    size_t desc_off[2][MAXL];    // int16 descriptors, pixel-interleaved
+    size_t desc_off[2][MAXL];    // int16 descriptors, pixel-interleaved: pixel (0, 0)
     size_t split_off[2][MAXL];   // same words with each value split into two signed bytes
-    int desc_row[MAXL];          // int16 elements per row (also 16-bit halves of a split row)
+    size_t desc_pad_off[2][MAXL];    // start of the padded arrays (pixel (-BORD, -BORD))
+    size_t split_pad_off[2][MAXL];
+    int desc_row[MAXL];          // int16 elements per padded row (also 16-bit halves of a split row)
+    int pxw;                     // 32-bit words per pixel (px_words)
     size_t bytes;
 };
 
@@ -44,6 +53,7 @@ struct WsPlan {
     size_t off_u[MAXL][2], off_cost[MAXL][2], off_flags[MAXL][2];
     size_t off_sa2[MAXL][2];     // per seed: sum of |G|^2 over its reference patch
     size_t off_sb2[MAXL][2];     // per target pixel: sum of |G|^2 over the patch there
+    int sbp[MAXL][2];            // row pitch (elements, even) of the target sums
     size_t off_sa2img[MAXL][2];  // per reference pixel: sum of |G|^2 over the patch there
     size_t off_err;              // uint32 device status word
     size_t off_label, off_size, off_bsum;   // filter scratch (level-0 forward lattice)
@@ -70,22 +80,22 @@ inline int rs_count(int W) { int K = 0; for (int w = W; w >= 1; w >>= 1) ++K; re
 // ------------------------------------------------------- kernel blocks
 // One direction of one pair at one level.
 struct DirLvl {
-    const int16_t* ref;          // descriptor of the reference image (this dir)
-    const int16_t* tgt;          // descriptor of the target image
-    const uint32_t* ref_split;   // reference descriptor in split-byte form
-    int32_t ref_pitch, tgt_pitch;// int16 elements per row
+    const int16_t* ref;          // descriptor of the reference image (this dir), pixel (0, 0)
+    const int16_t* tgt;          // descriptor of the target image, pixel (0, 0)
+    const uint32_t* ref_split;   // reference descriptor in split-byte form, pixel (0, 0)
+    int32_t ref_pitch, tgt_pitch;// int16 elements per (padded) row
     int32_t rw, rh, tw, th;      // reference / target image size
     int32_t nx, ny;              // lattice of this direction (on the reference)
     int32_t onx, ony;            // lattice of the other direction
     int32_t P;                   // patch side
-    int32_t pad;
+    int32_t sbp;                 // row pitch (elements) of sb2
     int32_t* u;                  // packed displacement (ux low 16, uy high 16)
     unsigned long long* cost;
     uint8_t* flags;
     const int32_t* ou;           // other direction: displacement
     const uint8_t* oflags;       //                  flags
     unsigned long long* sa2;     // per seed: sum over the reference patch of |G|^2
-    unsigned long long* sb2;     // per target pixel (row pitch tw): same over the target patch
+    unsigned long long* sb2;     // per target pixel (row pitch sbp): same over the target patch
     unsigned long long* sa2img;  // per reference pixel (row pitch rw): sum over its patch
 };
 
@@ -115,6 +125,7 @@ struct MatchConst {              // scalars common to one launch
     int32_t t, colour, tau2, rs_grid;   // rs_grid > 0: level-0 search on that grid only
     int32_t slack;                      // tuning: target-window margin of the tile kernels
     int32_t refresh;                    // search phase also scores the current matches first
+    int32_t cost_only;                  // score the current matches only (a visit without iterations)
 };
 
 // result-invariant tuning knobs (pgm_set_tuning)
@@ -135,9 +146,10 @@ constexpr int PYR_MAXB = 64;      // images per pyramid launch
 struct PyrItem {                  // one image in one pyramid launch
     const uint8_t* src;
     uint8_t* dst;
-    uint32_t* split;              // Sobel: split-byte copy of the descriptor
+    uint32_t* split;              // Sobel: split-byte copy of the descriptor (pixel (0, 0))
     int sw, sh, srow;             // source level size and row bytes
     int dw, dh, drow;             // destination level size and row bytes / int16 elements
+                                  // (Sobel: dst, split point at pixel (0, 0) of padded arrays)
     size_t splane, dplane;        // plane strides
     size_t pitch;                 // level 0: input row bytes
     int mode;                     // level 0: input mode; colour conversion: target space
@@ -160,7 +172,7 @@ pgm_status launch_consist(const LvlBatch& B, const MatchConst& mc, int max_seeds
                           cudaStream_t st);
 pgm_status launch_transfer(const XferBatch& X, int max_seeds, cudaStream_t st);
 pgm_status launch_box(const LvlBatch& B, int nch, int max_pixels, cudaStream_t st);
-// pm_tile.cu: *handled = false when the staged tile would not fit in shared memory
+// pm_row.cu (search and cost refresh on staged tiles) and init_tile.cu:
 // exhaustive init, squared L2, target image staged in shared memory;
 // *handled = false when it does not apply (the caller uses the direct kernel)
 pgm_status launch_init_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,

@@ -155,8 +155,13 @@ __global__ void k_convert(const __grid_constant__ PyrBatch B) {
 // away from the left and right borders; the horizontal passes (d and s along
 // x, both within int16) are kept per input row as one packed word, and the
 // vertical passes finish Gx and Gy (separable and exact in integers).  The
-// output words are staged in shared memory and leave as contiguous 16-byte
-// stores, one tile row of each output array at a time.
+// output words (px_words per pixel: 3 data words and a zero word for colour,
+// one word for gray) are staged in shared memory and leave as contiguous
+// 16-byte stores, one tile row of each output array at a time.  A block at an
+// image edge also writes the replicated border of BORD pixels next to it (a
+// border pixel repeats the descriptor of the nearest image pixel, which the
+// block holds), so every patch with its centre in the image can be read
+// without clamping.
 constexpr int SB_TW = 32, SB_TH = 16, SB_TY = 8, SB_XO = 4;   // SB_XO: staged columns left of x0
 __device__ __forceinline__ int sb_d(int S, int i) {
     return S == 5 ? (i == 0 ? -1 : i == 1 ? -2 : i == 2 ? 0 : i == 3 ? 2 : 1) : (i - 1);
@@ -170,7 +175,8 @@ __global__ void __launch_bounds__(SB_TW * SB_TY) k_sobel(const __grid_constant__
     constexpr int R = S / 2, IH = SB_TH + S - 1;
     constexpr int IWW = (SB_XO + SB_TW + R + 3) / 4;     // staged words per row (x0 - 4 .. )
     constexpr int IW = 4 * IWW, NT = SB_TW * SB_TY;
-    constexpr int OW = SB_TW * C;                        // output words per tile row and array
+    constexpr int PXW = px_words(2 * C);                 // words per pixel in the output arrays
+    constexpr int OW = SB_TW * PXW;                      // output words per tile row and array
     __shared__ __align__(16) uint8_t sI[C][IH][IW];      // column c holds x = x0 - SB_XO + c
     __shared__ uint32_t sH[C][IH][SB_TW];                // (sum d v) low 16, (sum s v) high 16
     __shared__ __align__(16) uint32_t sO[2][SB_TH][OW];  // descriptor words, split words
@@ -249,33 +255,41 @@ __global__ void __launch_bounds__(SB_TW * SB_TY) k_sobel(const __grid_constant__
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
-        for (int q = 0; q < C; ++q) {
-            sO[0][2 * ty + k][tx * C + q] =
-                (uint32_t)(uint16_t)g[k][2 * q] | ((uint32_t)(uint16_t)g[k][2 * q + 1] << 16);
-            sO[1][2 * ty + k][tx * C + q] = (uint32_t)split_bytes(g[k][2 * q], g[k][2 * q + 1]);
+        for (int q = 0; q < PXW; ++q) {
+            const bool dw = q < C;
+            sO[0][2 * ty + k][tx * PXW + q] =
+                dw ? (uint32_t)(uint16_t)g[k][2 * q] | ((uint32_t)(uint16_t)g[k][2 * q + 1] << 16) : 0u;
+            sO[1][2 * ty + k][tx * PXW + q] = dw ? (uint32_t)split_bytes(g[k][2 * q], g[k][2 * q + 1]) : 0u;
         }
     __syncthreads();
-    // tile row r of array a starts at word (y0 + r) rw + x0 C: rows of rw =
-    // drow / 2 words (drow a multiple of 8) and x0 C a multiple of 32, so
-    // 16-byte aligned (the arrays start 256-byte aligned)
-    const size_t rw = (size_t)(it.drow >> 1);
-    uint32_t* const dst0 = reinterpret_cast<uint32_t*>(it.dst) + (size_t)x0 * C;
-    uint32_t* const dst1 = it.split + (size_t)x0 * C;
-    const int nr = min(SB_TH, h - y0);
-    if (x0 + SB_TW <= w) {
+    // dst and split point at pixel (0, 0) of padded arrays with rows of rw
+    // words (a multiple of 4); pixel (x, y) starts at word y rw + x PXW, and
+    // x0 PXW is a multiple of 32 words, so tile rows are 16-byte aligned
+    const ptrdiff_t rw = (ptrdiff_t)(it.drow >> 1);
+    uint32_t* const dst0 = reinterpret_cast<uint32_t*>(it.dst);
+    uint32_t* const dst1 = it.split;
+    // this block's output: its tile, widened by the border where it touches
+    // an image edge
+    const bool left = x0 == 0, right = x0 + SB_TW >= w, top = y0 == 0, bottom = y0 + SB_TH >= h;
+    const int xa = left ? -BORD : x0, xb = right ? w + BORD : x0 + SB_TW;
+    const int ya = top ? -BORD : y0, yb = bottom ? h + BORD : y0 + SB_TH;
+    if (!(left || right || top || bottom)) {
         constexpr int NQ = OW / 4;
         for (int e = tid; e < 2 * SB_TH * NQ; e += NT) {
             const int a = e / (SB_TH * NQ), rem = e - a * (SB_TH * NQ), r = rem / NQ, q = rem - r * NQ;
-            if (r >= nr) continue;
             const uint4 v = *reinterpret_cast<const uint4*>(&sO[a][r][4 * q]);
-            *reinterpret_cast<uint4*>((a ? dst1 : dst0) + (size_t)(y0 + r) * rw + 4 * q) = v;
+            *reinterpret_cast<uint4*>((a ? dst1 : dst0) + (ptrdiff_t)(y0 + r) * rw +
+                                      (ptrdiff_t)x0 * PXW + 4 * q) = v;
         }
     } else {
-        const int nw = (w - x0) * C;                    // ragged right edge: words
-        for (int e = tid; e < 2 * SB_TH * OW; e += NT) {
-            const int a = e / (SB_TH * OW), rem = e - a * (SB_TH * OW), r = rem / OW, q = rem - r * OW;
-            if (r >= nr || q >= nw) continue;
-            (a ? dst1 : dst0)[(size_t)(y0 + r) * rw + q] = sO[a][r][q];
+        // a border pixel takes the words of the nearest image pixel, which
+        // lies in this tile
+        const int nxw = (xb - xa) * PXW, nrow = yb - ya;
+        for (int e = tid; e < 2 * nrow * nxw; e += NT) {
+            const int a = e / (nrow * nxw), rem = e - a * (nrow * nxw), r = rem / nxw, cw = rem - r * nxw;
+            const int y = ya + r, x = xa + cw / PXW, q = cw - (cw / PXW) * PXW;
+            const int sy = clampi(y, 0, h - 1) - y0, sx = clampi(x, 0, w - 1) - x0;
+            (a ? dst1 : dst0)[(ptrdiff_t)y * rw + (ptrdiff_t)x * PXW + q] = sO[a][sy][sx * PXW + q];
         }
     }
 }

@@ -38,9 +38,10 @@ def test_pyramid_bytes_match_the_abi_layout():
     for scheme in (0, 1):
         for level in range(bench.PARAMS["levels"]):
             off, lw, lh, nch, row = C.c_size_t(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+            pxe, bord = C.c_int(), C.c_int()
             assert L.pgm_pyramid_desc_layout(C.byref(cp), w, h, scheme, level, C.byref(off),
                                              C.byref(lw), C.byref(lh), C.byref(nch),
-                                             C.byref(row)) == 0
+                                             C.byref(row), C.byref(pxe), C.byref(bord)) == 0
             desc += lw.value * lh.value * nch.value * 2      # int16 descriptor
     want = 2 * pairs * (3 * w * h + 2 * desc)              # + the split copy, + the input
     got = bench.hbm_stage_bytes(bench.PARAMS, w, h, pairs, 0)["pyramid"]

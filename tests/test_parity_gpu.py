@@ -50,6 +50,34 @@ def test_pyramid_parity(api, prm, shape):
     compare_pyramid(P, O.Pyramid(O.make_params(prm), img), str(prm))
 
 
+@pytest.mark.parametrize("prm,shape", [
+    (dict(levels=4, color=0), (157, 301)),       # level 2 is 76 x 40: h = 8 (mod 16)
+    (dict(levels=3, color=1), (99, 211, 3)),
+    (dict(levels=2, color=1), (24, 56, 3)),      # w = 24 (mod 32), h = 8 (mod 16)
+    (dict(levels=2, color=0, descriptor=1), (40, 88)),
+])
+def test_descriptor_border(api, prm, shape):
+    """The replicated border of the padded descriptor arrays (patches read
+    outside the image take the nearest image pixel, Sec. III-B): every border
+    pixel equals the oracle's descriptor at the clamped position."""
+    rng = np.random.default_rng(shape[0] * 7 + shape[1])
+    img = rng.integers(0, 256, size=shape, dtype=np.uint8)
+    p = api.Params(**prm)
+    P = api.build_pyramid(p, torch.from_numpy(img).cuda())
+    torch.cuda.synchronize()
+    Q = O.Pyramid(O.make_params(prm), img)
+    for s in range(Q.schemes):
+        for l in range(Q.levels):
+            g = P.desc_padded(s, l).cpu().numpy()
+            o = Q.desc(s, l).transpose(1, 2, 0)
+            B = P.desc_layout(s, l)["border"]
+            h, w = o.shape[:2]
+            ys = np.clip(np.arange(-B, h + B), 0, h - 1)
+            xs = np.clip(np.arange(-B, w + B), 0, w - 1)
+            bad = np.argwhere((g != o[ys][:, xs]).any(-1))
+            assert bad.size == 0, (prm, s, l, (bad[:5] - B).tolist())
+
+
 def test_match_every_visit_c1(api):
     """256x192 gray (noise-affine workload): the state after each of the 7
     visits of the L = 3 schedule, at every level and in both directions."""
