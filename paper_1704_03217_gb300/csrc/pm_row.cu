@@ -101,8 +101,9 @@ namespace {
 struct __align__(16) RowRec {       // one active seed of a staged tile
     int s, px, py, f;               // seed index (-1: none), centre, flags after the refresh
     int u, nb0, nb1, K;             // current match; propagated candidates to score; search count
-    int r0, r1, f0, pad0;           // random-search offsets k = 0, 1 (packed like u); flags as read
-    int wu, w0, w1, pad1;           // window slots (row_slot) of u, nb0, nb1
+    int r0, r1, f0, wr0;            // random-search offsets k = 0, 1 (packed like u); flags as read;
+    int wu, w0, w1, wr1;            // window slots (row_slot) of u, nb0, nb1, and of the search
+                                    // candidates k = 0, 1 around u (-2: not scored)
     unsigned long long cost, sa;    // current cost, sum |a|^2 of the reference patch
 };
 
@@ -241,7 +242,7 @@ __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSch
         const int i = i0 + 2 * (a % (PR_TW / 2)) + ((j + mc.colour) & 1);
         RowRec R;
         R.s = -1; R.px = 0; R.py = 0; R.f = 0; R.u = 0; R.nb0 = NO_CAND; R.nb1 = NO_CAND; R.K = 0;
-        R.r0 = 0; R.r1 = 0; R.f0 = 0; R.pad0 = 0; R.wu = -1; R.w0 = -1; R.w1 = -1; R.pad1 = 0;
+        R.r0 = 0; R.r1 = 0; R.f0 = 0; R.wr0 = -2; R.wu = -1; R.w0 = -1; R.w1 = -1; R.wr1 = -2;
         R.cost = INF; R.sa = 0;
         if (i < D.nx && j < D.ny) {
             const int s = j * D.nx + i;
@@ -326,6 +327,18 @@ __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSch
         R.wu = R.s >= 0 ? row_slot(G, H, P, R.px + lo16((uint32_t)R.u), R.py + hi16((uint32_t)R.u)) : -1;
         R.w0 = R.nb0 != NO_CAND ? row_slot(G, H, P, R.px + lo16((uint32_t)R.nb0), R.py + hi16((uint32_t)R.nb0)) : -1;
         R.w1 = R.nb1 != NO_CAND ? row_slot(G, H, P, R.px + lo16((uint32_t)R.nb1), R.py + hi16((uint32_t)R.nb1)) : -1;
+        // the first two search candidates around the current match, the
+        // centre of the search unless a propagated match wins
+        if (R.s >= 0 && (R.f & F_VALID) && R.K > 0) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const uint32_t o = (uint32_t)(k ? R.r1 : R.r0);
+                const int qx = R.px + ux + lo16(o), qy = R.py + uy + hi16(o);
+                const bool ok = k < R.K && o != 0u && inside(D, qx, qy);
+                const int w = ok ? row_slot(G, H, P, qx, qy) : -2;
+                if (k) R.wr1 = w; else R.wr0 = w;
+            }
+        }
         rec[b][a] = R;
         if (lane == 0) {
             hdr[b] = H;
@@ -530,7 +543,21 @@ __device__ void pr_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
             const int K = R.K;
             if (have && K > 0) {
                 const int cx0 = lo16((uint32_t)bu), cy0 = hi16((uint32_t)bu);
-                for (int k = 0; k < K; ++k) {
+                int k = 0;
+                if (bu == Ru && (Rf & F_VALID)) {    // centre = current match: slots from the producer
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const int w = c ? R.wr1 : R.wr0;
+                        if (w == -2) continue;
+                        const uint32_t o = (uint32_t)(c ? R.r1 : R.r0);
+                        const int dx = lo16(o), dy = hi16(o);
+                        const unsigned long long v = eval(w, px + cx0 + dx, py + cy0 + dy);
+                        ++n_eval;
+                        if (v < bc) { bc = v; bu = pack_u(cx0 + dx, cy0 + dy); }
+                    }
+                    k = 2;
+                }
+                for (; k < K; ++k) {
                     int dx, dy;
                     if (k < 2) {
                         const uint32_t o = (uint32_t)(k ? R.r1 : R.r0);
