@@ -102,6 +102,11 @@ void pgm_default_params(pgm_params* p);
 /* Static description of a status code. */
 const char* pgm_status_string(pgm_status s);
 
+/* For the last PGM_ERR_CUDA returned to the calling host thread: the library
+ * step and the CUDA error behind it ("" if there was none).  The text stays
+ * valid until the thread's next failing call.  Never fails. */
+const char* pgm_error_detail(void);
+
 /* ------------------------------------------------------------------ */
 /* Gradient pyramid (Sec. III-A Eq. 1-2, Sec. III-D, Sec. III-E Table 2) */
 /* ------------------------------------------------------------------ */
@@ -247,13 +252,17 @@ pgm_status pgm_filter_batch(const pgm_params* p, int n, const int32_t* dims, voi
  *                 uint8 flags); read only.
  *   d_matches, max_matches, d_count: as for pgm_filter.
  * Result: identical to pgm_filter on the workspace holding that field.
- * The first call on each device looks up the array's device address with
- * the device current; make that first call before any stream capture.  All
- * calls share the one array and it keeps the last call's contents (every
- * call re-initialises what it reads), so calls whose work overlaps on the
- * GPU -- e.g. on two streams at once -- race and must be serialised.
- * Errors: PGM_ERR_ARG (NULL pointer, nx or ny < 0, misaligned d_matches),
- * PGM_ERR_UNSUPPORTED (nx * ny > PGM_NOALLOC_MAX_SEEDS), PGM_ERR_CUDA. */
+ * A call made outside a stream capture looks up the array's device address
+ * with the device current (so calls after a cudaDeviceReset find the
+ * array's new place); a call inside a capture uses the address an earlier
+ * call on that device found, so make one call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents
+ * (every call re-initialises what it reads), so calls whose work overlaps
+ * on the GPU -- e.g. on two streams at once -- race and must be serialised.
+ * Errors: PGM_ERR_ARG (NULL pointer, nx or ny < 0, d_matches not 16-byte
+ * aligned, d_u or d_count not 4-byte aligned; checked before anything is
+ * launched), PGM_ERR_UNSUPPORTED (nx * ny > PGM_NOALLOC_MAX_SEEDS),
+ * PGM_ERR_CUDA. */
 #define PGM_NOALLOC_MAX_SEEDS (1 << 20)
 pgm_status pgm_filter_noalloc(const pgm_params* p, int nx, int ny, const int32_t* d_u,
                               const uint8_t* d_flags, int32_t* d_matches, int64_t max_matches,

@@ -84,6 +84,9 @@ def lib():
         L.orc_field_get.argtypes = [C.c_void_p, C.c_int, C.c_int, i32p, i32p, u8p, u64p, u8p, u8p]
         L.orc_filter.argtypes = [P, C.c_void_p, i32p, C.c_int64, u8p]
         L.orc_filter.restype = C.c_int64
+        L.orc_filter_arrays.argtypes = [P, C.c_int, C.c_int, i32p, i32p, u8p, u8p, i32p,
+                                        C.c_int64, u8p]
+        L.orc_filter_arrays.restype = C.c_int64
         _lib = L
     return _lib
 
@@ -247,6 +250,21 @@ class Match:
         if getattr(self, "h", None):
             lib().orc_match_free(self.h)
             self.h = None
+
+
+def filter_arrays(params, ux, uy, valid, outlier):
+    """Region removal and export (Sec. III-E, III-G) on a level-0 forward
+    field given as (ny, nx) arrays: (rows [n][4] int32, keep (ny, nx) uint8)."""
+    p = params if isinstance(params, _Params) else make_params(params)
+    ny, nx = ux.shape
+    ux = np.ascontiguousarray(ux, np.int32); uy = np.ascontiguousarray(uy, np.int32)
+    va = np.ascontiguousarray(valid, np.uint8); ol = np.ascontiguousarray(outlier, np.uint8)
+    rows = np.zeros((max(nx * ny, 1), 4), np.int32)
+    keep = np.zeros(nx * ny, np.uint8)
+    n = lib().orc_filter_arrays(C.byref(p), nx, ny, _ptr(ux, C.c_int32), _ptr(uy, C.c_int32),
+                                _ptr(va, C.c_uint8), _ptr(ol, C.c_uint8), _ptr(rows, C.c_int32),
+                                nx * ny, _ptr(keep, C.c_uint8))
+    return rows[:n].copy(), keep.reshape(ny, nx)
 
 
 def run_pair(params, img1, img2, schedule=SCHED_CHECKERBOARD, stream_id=0):

@@ -712,15 +712,16 @@ void orc_field_get(const orc_match* m, int level, int dir, int32_t* ux, int32_t*
     if (oinit) memcpy(oinit, F->oinit, n);
 }
 
-/* Region removal (Sec. III-E, reading R16) on the level-0 forward field,
- * then the grid export of Sec. III-G (reading R17).  Inlier seeds (O = no)
- * that are 4-neighbours on the lattice join a region iff their displacements
- * differ by less than sqrt(region_dmax2); regions with fewer than min_region
- * seeds are removed.  Regions are found by breadth-first search. */
-int64_t orc_filter(const orc_params* p, const orc_match* m, int32_t* rows, int64_t max_rows,
-                   uint8_t* keep_out) {
-    const field_t* F = &m->f[0][0];
-    int nx = F->nx, ny = F->ny, n = nx * ny;
+/* Region removal (Sec. III-E, reading R16) on a level-0 forward field given
+ * as arrays (nx x ny seeds, raster order), then the grid export of Sec.
+ * III-G (reading R17).  Inlier seeds (valid, O = no) that are 4-neighbours on
+ * the lattice join a region iff their displacements differ by less than
+ * sqrt(region_dmax2); regions with fewer than min_region seeds are removed.
+ * Regions are found by breadth-first search. */
+int64_t orc_filter_arrays(const orc_params* p, int nx, int ny, const int32_t* ux,
+                          const int32_t* uy, const uint8_t* valid, const uint8_t* outl,
+                          int32_t* rows, int64_t max_rows, uint8_t* keep_out) {
+    int n = nx * ny;
     int sig = p->seed_stride, c = sig / 2;
     int* comp = (int*)malloc(sizeof(int) * (n + 1));
     int* queue = (int*)malloc(sizeof(int) * (n + 1));
@@ -728,7 +729,7 @@ int64_t orc_filter(const orc_params* p, const orc_match* m, int32_t* rows, int64
     for (int s = 0; s < n; ++s) comp[s] = -1;
     int ncomp = 0;
     for (int s0 = 0; s0 < n; ++s0) {
-        if (comp[s0] >= 0 || F->outl[s0] || !F->valid[s0]) continue;
+        if (comp[s0] >= 0 || outl[s0] || !valid[s0]) continue;
         int head = 0, tail = 0;
         queue[tail++] = s0; comp[s0] = ncomp;
         while (head < tail) {
@@ -738,8 +739,8 @@ int64_t orc_filter(const orc_params* p, const orc_match* m, int32_t* rows, int64
             for (int k = 0; k < 4; ++k) {
                 if (ni[k] < 0 || nj[k] < 0 || ni[k] >= nx || nj[k] >= ny) continue;
                 int t = nj[k] * nx + ni[k];
-                if (comp[t] >= 0 || F->outl[t] || !F->valid[t]) continue;
-                int64_t dx = F->ux[s] - F->ux[t], dy = F->uy[s] - F->uy[t];
+                if (comp[t] >= 0 || outl[t] || !valid[t]) continue;
+                int64_t dx = ux[s] - ux[t], dy = uy[s] - uy[t];
                 if (dx * dx + dy * dy >= p->region_dmax2) continue;
                 comp[t] = ncomp; queue[tail++] = t;
             }
@@ -756,10 +757,18 @@ int64_t orc_filter(const orc_params* p, const orc_match* m, int32_t* rows, int64
             int i = s % nx, j = s / nx;
             int x = c + sig * i, y = c + sig * j;
             rows[4 * cnt + 0] = x; rows[4 * cnt + 1] = y;
-            rows[4 * cnt + 2] = x + F->ux[s]; rows[4 * cnt + 3] = y + F->uy[s];
+            rows[4 * cnt + 2] = x + ux[s]; rows[4 * cnt + 3] = y + uy[s];
         }
         cnt++;
     }
     free(comp); free(queue); free(size);
     return cnt;
+}
+
+/* The same on the level-0 forward field of a match. */
+int64_t orc_filter(const orc_params* p, const orc_match* m, int32_t* rows, int64_t max_rows,
+                   uint8_t* keep_out) {
+    const field_t* F = &m->f[0][0];
+    return orc_filter_arrays(p, F->nx, F->ny, F->ux, F->uy, F->valid, F->outl, rows, max_rows,
+                             keep_out);
 }

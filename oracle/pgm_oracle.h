@@ -100,6 +100,12 @@ void       orc_field_get(const orc_match* m, int level, int dir, int32_t* ux, in
 /* rows: [max_rows][4] (x1, y1, x2, y2); returns the number of matches (may
  * exceed max_rows, in which case only max_rows are written). keep: optional
  * per-seed 0/1 of the level-0 forward lattice. */
+/* Region removal and export on a level-0 forward field given as arrays of
+ * nx x ny seeds (raster order): ux, uy displacements, valid and outlier flags
+ * (0/1).  Same rule and output as orc_filter. */
+int64_t orc_filter_arrays(const orc_params* p, int nx, int ny, const int32_t* ux,
+                          const int32_t* uy, const uint8_t* valid, const uint8_t* outl,
+                          int32_t* rows, int64_t max_rows, uint8_t* keep_out);
 int64_t orc_filter(const orc_params* p, const orc_match* m, int32_t* rows, int64_t max_rows,
                    uint8_t* keep);
 

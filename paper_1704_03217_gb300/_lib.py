@@ -32,7 +32,7 @@ EXPORTS = [
     "pgm_match", "pgm_match_batch", "pgm_field_layout", "pgm_filter", "pgm_sync_status",
     "pgm_nominal_evals", "pgm_launch_count", "pgm_profile_enable", "pgm_profile_read",
     "pgm_filter_noalloc", "pgm_build_pyramid_batch", "pgm_filter_batch", "pgm_set_tuning",
-    "pgm_get_tuning", "pgm_set_wait_limit",
+    "pgm_get_tuning", "pgm_set_wait_limit", "pgm_error_detail",
 ]
 
 
@@ -44,9 +44,10 @@ WS_EVALS_OFFSET, WS_EVALS_COUNT = 8, 8   # pm, cost, init, pm-from-global: fwd/b
 
 
 class PGMError(RuntimeError):
-    def __init__(self, code, where):
+    def __init__(self, code, where, detail=""):
         self.code = code
-        super().__init__("%s failed: %s (%d)" % (where, STATUS.get(code, "?"), code))
+        msg = "%s failed: %s (%d)" % (where, STATUS.get(code, "?"), code)
+        super().__init__(msg + (" [%s]" % detail if detail else ""))
 
 
 _lib = None
@@ -65,6 +66,7 @@ def load(path: str = LIB_PATH):
     pi, psz = C.POINTER(C.c_int), C.POINTER(C.c_size_t)
     L.pgm_default_params.argtypes = [P]; L.pgm_default_params.restype = None
     L.pgm_status_string.argtypes = [i32]; L.pgm_status_string.restype = C.c_char_p
+    L.pgm_error_detail.argtypes = []; L.pgm_error_detail.restype = C.c_char_p
     L.pgm_pyramid_bytes.argtypes = [P, i32, i32]; L.pgm_pyramid_bytes.restype = sz
     L.pgm_build_pyramid.argtypes = [P, vp, i32, i32, i32, sz, vp, sz, vp]
     L.pgm_pyramid_desc_layout.argtypes = [P, i32, i32, i32, i32, psz, pi, pi, pi, pi, pi, pi]
@@ -101,4 +103,5 @@ def load(path: str = LIB_PATH):
 
 def check(code, where):
     if code != 0:
-        raise PGMError(code, where)
+        detail = load().pgm_error_detail().decode() if code == 4 else ""
+        raise PGMError(code, where, detail)

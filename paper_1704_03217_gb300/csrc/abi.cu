@@ -1,8 +1,11 @@
 // abi.cu -- the extern "C" entry points of libpgm: argument checks, buffer
 // layouts (plans), the visit schedule of Fig. 5 and the launch sequence.
+#include <stdio.h>
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "pgm_device.cuh"
@@ -11,6 +14,37 @@ namespace pgm {
 
 // ------------------------------------------------------ launch accounting
 static std::atomic<long long> g_launches{0};
+
+// kernels whose shared-memory limit is raised on a device (smem_opt_in)
+static std::mutex g_optin_mu;
+static std::vector<std::pair<const void*, int>> g_optin;
+pgm_status smem_opt_in(const void* kern) {
+    int dev = 0;
+    PGM_TRY(cudaGetDevice(&dev), "shared-memory opt-in: cudaGetDevice");
+    std::lock_guard<std::mutex> lock(g_optin_mu);
+    for (const auto& e : g_optin)
+        if (e.first == kern && e.second == dev) return PGM_OK;
+    int max_optin = 0;
+    PGM_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
+            "shared-memory opt-in: device limit");
+    cudaFuncAttributes fa;
+    PGM_TRY(cudaFuncGetAttributes(&fa, kern), "shared-memory opt-in: kernel attributes");
+    // the kernel's static shared memory counts against the same limit
+    const int dyn = max_optin - (int)fa.sharedSizeBytes;
+    PGM_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn),
+            "shared-memory opt-in: set");
+    g_optin.emplace_back(kern, dev);
+    return PGM_OK;
+}
+
+// the CUDA call behind the last PGM_ERR_CUDA of each host thread
+static thread_local char g_detail[192];
+pgm_status cuda_fail(const char* site, cudaError_t e) {
+    snprintf(g_detail, sizeof(g_detail), "%s: %s (%d): %s", site, cudaGetErrorName(e), (int)e,
+             cudaGetErrorString(e));
+    (void)cudaGetLastError();     // reported by the status: not left for the caller's next check
+    return PGM_ERR_CUDA;
+}
 
 // ------------------------------------------------------------ tuning knobs
 static std::atomic<int> g_slack{2}, g_chunk{MAXB};
@@ -255,7 +289,7 @@ static thread_local Aux g_aux[AUX_MAX];
 static pgm_status aux_get(cudaStream_t st, Aux** out) {
     *out = nullptr;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return PGM_ERR_CUDA;
+    PGM_TRY(cudaGetDevice(&dev), "aux streams: cudaGetDevice");
     for (int i = 0; i < AUX_MAX; ++i)
         if (g_aux[i].used && g_aux[i].dev == dev && g_aux[i].key == st) {
             *out = &g_aux[i];
@@ -266,15 +300,13 @@ static pgm_status aux_get(cudaStream_t st, Aux** out) {
         Aux a;
         a.dev = dev;
         a.key = st;
-        if (cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&a.s2, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&a.sfork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&a.sjoin, cudaEventDisableTiming) != cudaSuccess)
-            return PGM_ERR_CUDA;
+        PGM_TRY(cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking), "aux streams: create");
+        PGM_TRY(cudaStreamCreateWithFlags(&a.s2, cudaStreamNonBlocking), "aux streams: create");
+        PGM_TRY(cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming), "aux streams: event");
+        PGM_TRY(cudaEventCreateWithFlags(&a.sfork, cudaEventDisableTiming), "aux streams: event");
+        PGM_TRY(cudaEventCreateWithFlags(&a.sjoin, cudaEventDisableTiming), "aux streams: event");
         for (int l = 0; l < MAXL; ++l)
-            if (cudaEventCreateWithFlags(&a.lvl[l], cudaEventDisableTiming) != cudaSuccess)
-                return PGM_ERR_CUDA;
+            PGM_TRY(cudaEventCreateWithFlags(&a.lvl[l], cudaEventDisableTiming), "aux streams: event");
         a.used = true;
         g_aux[i] = a;
         *out = &g_aux[i];
@@ -299,8 +331,8 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
     static thread_local LvlBatch B;       // ~8 KB: kept off the stack
     static thread_local XferBatch X;
     for (int k = 0; k < n; ++k)           // reset the evaluation counters
-        if (cudaMemsetAsync(ctx[k].ws + PGM_WS_EVALS_OFFSET, 0, 8 * PGM_WS_EVALS_COUNT, st) != cudaSuccess)
-            return PGM_ERR_CUDA;
+        PGM_TRY(cudaMemsetAsync(ctx[k].ws + PGM_WS_EVALS_OFFSET, 0, 8 * PGM_WS_EVALS_COUNT, st),
+                "match: zero the counters");
     // per level and direction: box sums of |G|^2 over the target and the
     // reference patches.  The coarsest level's come first on the caller's
     // stream; the finer levels' are forked onto an auxiliary stream, where
@@ -322,8 +354,8 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
                 if (r != PGM_OK) return r;
             }
             if (l != l0 && aux && !forked) {
-                if (cudaEventRecord(aux->fork, st) != cudaSuccess ||
-                    cudaStreamWaitEvent(aux->s, aux->fork, 0) != cudaSuccess) return PGM_ERR_CUDA;
+                PGM_TRY(cudaEventRecord(aux->fork, st), "match: fork box sums");
+                PGM_TRY(cudaStreamWaitEvent(aux->s, aux->fork, 0), "match: fork box sums");
                 forked = true;
             }
             memset(&B, 0, sizeof(B));
@@ -341,7 +373,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
             pgm_status r = launch_box(B, nch, max_px, on_aux ? aux->s : st);
             if (r != PGM_OK) return r;
             if (on_aux) {
-                if (cudaEventRecord(aux->lvl[l], aux->s) != cudaSuccess) return PGM_ERR_CUDA;
+                PGM_TRY(cudaEventRecord(aux->lvl[l], aux->s), "match: box sums done");
                 joined[l] = false;
             }
         }
@@ -349,7 +381,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
     for (int v = 0; v < sch.n; ++v) {
         const int l = sch.level[v];
         if (!joined[l]) {
-            if (cudaStreamWaitEvent(st, aux->lvl[l], 0) != cudaSuccess) return PGM_ERR_CUDA;
+            PGM_TRY(cudaStreamWaitEvent(st, aux->lvl[l], 0), "match: join box sums");
             joined[l] = true;
         }
         memset(&B, 0, sizeof(B));
@@ -410,8 +442,8 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
                 if (r != PGM_OK) return r;
             }
             if (aux) {
-                if (cudaEventRecord(aux->sfork, st) != cudaSuccess ||
-                    cudaStreamWaitEvent(aux->s2, aux->sfork, 0) != cudaSuccess) return PGM_ERR_CUDA;
+                PGM_TRY(cudaEventRecord(aux->sfork, st), "match: fork backward search");
+                PGM_TRY(cudaStreamWaitEvent(aux->s2, aux->sfork, 0), "match: fork backward search");
                 st2 = aux->s2;
             }
         }
@@ -421,9 +453,10 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
                 r = launch_pm_phase(B, mc, nch, maxP, max_half, st, st2);
                 if (r != PGM_OK) return r;
             }
-        if (st2 && (cudaEventRecord(aux->sjoin, st2) != cudaSuccess ||
-                    cudaStreamWaitEvent(st, aux->sjoin, 0) != cudaSuccess))
-            return PGM_ERR_CUDA;
+        if (st2) {
+            PGM_TRY(cudaEventRecord(aux->sjoin, st2), "match: join backward search");
+            PGM_TRY(cudaStreamWaitEvent(st, aux->sjoin, 0), "match: join backward search");
+        }
         mc.t = 0; mc.colour = 0; mc.refresh = 0;
         r = launch_consist(B, mc, max_seeds, st);
         if (r != PGM_OK) return r;
@@ -695,12 +728,12 @@ pgm_status pgm_sync_status(const pgm_params* p, int w1, int h1, int w2, int h2, 
     if (ws_bytes < wp.bytes) return PGM_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint32_t word = 0;
-    if (cudaMemcpyAsync(&word, static_cast<uint8_t*>(d_ws) + wp.off_err, 4,
-                        cudaMemcpyDeviceToHost, st) != cudaSuccess) return PGM_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return PGM_ERR_CUDA;
+    PGM_TRY(cudaMemcpyAsync(&word, static_cast<uint8_t*>(d_ws) + wp.off_err, 4,
+                            cudaMemcpyDeviceToHost, st), "sync_status: read the status word");
+    PGM_TRY(cudaStreamSynchronize(st), "sync_status: synchronize");
     if (word != 0) {
-        if (cudaMemsetAsync(static_cast<uint8_t*>(d_ws) + wp.off_err, 0, 4, st) != cudaSuccess)
-            return PGM_ERR_CUDA;
+        PGM_TRY(cudaMemsetAsync(static_cast<uint8_t*>(d_ws) + wp.off_err, 0, 4, st),
+                "sync_status: clear the status word");
         return (pgm_status)word;
     }
     return PGM_OK;
@@ -730,13 +763,15 @@ pgm_status pgm_get_tuning(pgm_tuning* t) {
 
 int64_t pgm_launch_count(void) { return (int64_t)g_launches.load(); }
 
+const char* pgm_error_detail(void) { return g_detail; }
+
 pgm_status pgm_profile_enable(int on) {
     if (on) {
         for (auto& e : g_prof.open) { g_prof.pool.push_back(e.a); g_prof.pool.push_back(e.b); }
         g_prof.open.clear();
         for (int k = 0; k < PGM_K_COUNT; ++k) { g_prof.ms[k] = 0; g_prof.launches[k] = 0; }
         cudaEvent_t probe = take_event();
-        if (!probe) return PGM_ERR_CUDA;
+        if (!probe) return cuda_fail("profile: event create", cudaErrorMemoryAllocation);
         g_prof.pool.push_back(probe);
     }
     g_prof.on = on != 0;
@@ -745,9 +780,9 @@ pgm_status pgm_profile_enable(int on) {
 
 pgm_status pgm_profile_read(double* ms, int64_t* launches) {
     for (auto& e : g_prof.open) {
-        if (cudaEventSynchronize(e.b) != cudaSuccess) return PGM_ERR_CUDA;
+        PGM_TRY(cudaEventSynchronize(e.b), "profile: event synchronize");
         float t = 0.f;
-        if (cudaEventElapsedTime(&t, e.a, e.b) != cudaSuccess) return PGM_ERR_CUDA;
+        PGM_TRY(cudaEventElapsedTime(&t, e.a, e.b), "profile: elapsed time");
         g_prof.ms[e.cls] += t;
         g_prof.launches[e.cls] += e.n;
         g_prof.pool.push_back(e.a);

@@ -179,7 +179,7 @@ pgm_status launch_filter_batch(const pgm_params* p, const FiltBatch& F, int max_
     k_scan_blocks<<<F.n, 1024, 0, st>>>(F);
     k_keep_write<<<g, 256, 0, st>>>(F);
     (void)p;
-    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+    return launch_status("filter: launch");
 }
 
 void filter_item(const WsPlan& wp, uint8_t* d_ws, int32_t* d_matches, int64_t max_matches,

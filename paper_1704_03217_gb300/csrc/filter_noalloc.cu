@@ -22,14 +22,20 @@ std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};   // device address of g_scratch, per device
 
 // The symbol's name is only a host-side handle: its device address has to be
-// asked for, once per device, with that device current.
-pgm_status scratch_address(void** out) {
+// asked for with the device current.  It is asked for again on every call
+// made outside a stream capture (the array moves if the device was reset);
+// during a capture the address cached by an earlier call is used.
+pgm_status scratch_address(cudaStream_t st, void** out) {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PGM_ERR_CUDA;
+    PGM_TRY(cudaGetDevice(&dev), "noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return cuda_fail("noalloc: device index", cudaErrorInvalidDevice);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    PGM_TRY(cudaStreamIsCapturing(st, &cap), "noalloc: capture status");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_addr[dev]) {
         void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return PGM_ERR_CUDA;
+        PGM_TRY(cudaGetSymbolAddress(&ptr, g_scratch), "noalloc: scratch address");
+        if (!ptr) return cuda_fail("noalloc: scratch address", cudaErrorInvalidSymbol);
         g_addr[dev] = ptr;
     }
     *out = g_addr[dev];
@@ -49,10 +55,11 @@ extern "C" pgm_status pgm_filter_noalloc(const pgm_params* p, int nx, int ny, co
     if (nx < 0 || ny < 0 || !d_count || max_matches < 0 || (max_matches > 0 && !d_matches))
         return PGM_ERR_ARG;
     if ((long long)nx * ny > 0 && (!d_u || !d_flags)) return PGM_ERR_ARG;
-    if (((uintptr_t)d_matches) & 15u) return PGM_ERR_ARG;
+    if ((((uintptr_t)d_matches) & 15u) || (((uintptr_t)d_u) & 3u) || (((uintptr_t)d_count) & 3u))
+        return PGM_ERR_ARG;
     if ((long long)nx * ny > (long long)kMaxSeeds) return PGM_ERR_UNSUPPORTED;
     void* base = nullptr;
-    r = scratch_address(&base);
+    r = scratch_address(static_cast<cudaStream_t>(stream), &base);
     if (r != PGM_OK) return r;
     int* label = static_cast<int*>(base);
     int* size = label + kMaxSeeds;

@@ -159,20 +159,9 @@ __global__ void __launch_bounds__(IN_THREADS) k_init_t(const __grid_constant__ L
 template <int NCH>
 pgm_status launch_in(const LvlBatch& B, const MatchConst& mc, int groups, int smem,
                      cudaStream_t st) {
-    static thread_local int cfg_dev = -1, configured = 0;   // per host thread and device
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return PGM_ERR_CUDA;
-    if (dev != cfg_dev) {
-        cfg_dev = dev;
-        configured = 0;
-    }
-    if (configured < smem) {
-        if (cudaFuncSetAttribute(k_init_t<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-            cudaSuccess) return PGM_ERR_CUDA;
-        configured = smem;
-    }
+    if (pgm_status r = smem_opt_in((const void*)k_init_t<NCH>); r != PGM_OK) return r;
     k_init_t<NCH><<<dim3(groups, 2, B.n), IN_THREADS, smem, st>>>(B, mc);
-    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+    return launch_status("init: launch");
 }
 
 }  // namespace

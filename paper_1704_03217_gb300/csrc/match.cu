@@ -662,7 +662,7 @@ inline int ppl_of(int maxP) {
     } while (0)
 
 inline pgm_status last_status() {
-    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+    return launch_status("match: launch");
 }
 
 }  // namespace

@@ -67,6 +67,26 @@ struct Schedule {
     int with_o[MAXVIS];          // transfer into this visit carries O (Eq. 8)
 };
 
+// Record, for this host thread, which CUDA call failed and how
+// (pgm_error_detail), and return PGM_ERR_CUDA.
+pgm_status cuda_fail(const char* site, cudaError_t e);
+// The status after kernel launches: PGM_OK, or PGM_ERR_CUDA recorded at site.
+inline pgm_status launch_status(const char* site) {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PGM_OK : cuda_fail(site, e);
+}
+#define PGM_TRY(call, site)                                         \
+    do {                                                            \
+        const cudaError_t pgm_e_ = (call);                          \
+        if (pgm_e_ != cudaSuccess) return ::pgm::cuda_fail(site, pgm_e_); \
+    } while (0)
+
+// Allow kernel `kern` the device's largest dynamic shared memory per block.
+// The limit is an attribute of the kernel on the current device, shared by
+// every host thread, so it is raised once per (kernel, device) to the
+// maximum (a launch still uses only what it asks for) and never lowered.
+pgm_status smem_opt_in(const void* kern);
+
 pgm_status check_params(const pgm_params* p);
 bool make_pyr_plan(const pgm_params* p, int w, int h, PyrPlan* pp);
 bool make_ws_plan(const pgm_params* p, int w1, int h1, int w2, int h2, WsPlan* wp);

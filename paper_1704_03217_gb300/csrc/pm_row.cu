@@ -166,16 +166,27 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
         : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
 // Wait for phase `parity` of an mbarrier; give up after `limit` cycles or
-// once another warp has flagged an abort.
+// once another warp has flagged an abort.  The first look does not block
+// (try_wait may suspend the thread for a while), so a limit of a few cycles
+// runs out at once unless the phase is already complete.
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long limit,
                                           const volatile int* abort) {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
+    if (mbar_test_wait(bar, parity)) return true;
+    for (;;) {
         if (abort && *abort) return false;
         if (clock64() - t0 > limit) return false;
+        if (mbar_try_wait(bar, parity)) return true;
     }
-    return true;
 }
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -650,23 +661,6 @@ static_assert(sizeof(LvlBatch) + sizeof(MatchConst) + sizeof(RowSched) + sizeof(
                   2 * sizeof(int) + sizeof(long long) + 256 <= 32764,
               "k_pm_r parameters exceed the kernel parameter limit");
 
-// Per-thread caches keyed by device: the shared-memory opt-in of a kernel is a
-// per-device attribute, and calls may come from several host threads.
-static bool opt_in_smem(const void* kern, int smem, int* cfg_dev, int* configured) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    if (dev != *cfg_dev) {
-        *cfg_dev = dev;
-        *configured = 0;
-    }
-    if (*configured < smem) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-            cudaSuccess) return false;
-        *configured = smem;
-    }
-    return true;
-}
-
 static int device_sms() {
     static thread_local int dev_cached = -1, sms = 0;
     int dev = 0;
@@ -825,16 +819,15 @@ long long wait_limit();
 template <int NCH, int PC>
 pgm_status launch_r(const LvlBatch& B, const MatchConst& mc, const RowSched& S, const RowMaps& TM,
                     int buf_words, cudaStream_t st) {
-    static thread_local int cfg_dev = -1, configured = 0;   // opt-in above 48 KB
     const int nbuf = 3L * buf_words * 4 <= 200L * 1024 ? 3 : 2;
     const int smem = nbuf * buf_words * 4;
     auto kern = k_pm_r<NCH, PC>;
-    if (!opt_in_smem((const void*)kern, smem, &cfg_dev, &configured)) return PGM_ERR_CUDA;
+    if (pgm_status r = smem_opt_in((const void*)kern); r != PGM_OK) return r;
     const int sms = device_sms();
-    if (sms <= 0) return PGM_ERR_CUDA;
+    if (sms <= 0) return cuda_fail("search: SM count", cudaErrorInvalidDevice);
     const int grid = S.total < sms ? S.total : sms;       // one CTA per SM (shared memory)
     kern<<<grid, 32 * (PR_PROD + pr_cons(NCH, PC)), smem, st>>>(B, mc, S, TM, buf_words, nbuf, wait_limit());
-    return cudaGetLastError() == cudaSuccess ? PGM_OK : PGM_ERR_CUDA;
+    return launch_status("search: launch");
 }
 
 // The consumer specialisation of a direction's patch side: compile-time sides

@@ -380,7 +380,7 @@ pgm_status launch_pyramid_batch(const pgm_params* p, int n, const PyrPlan* plans
                     else k_sobel<3, 3><<<g, sblk, 0, st>>>(B, dir_only);
                 }
             }
-        if (cudaGetLastError() != cudaSuccess) return PGM_ERR_CUDA;
+        if (pgm_status r = launch_status("pyramid: launch"); r != PGM_OK) return r;
     }
     return PGM_OK;
 }

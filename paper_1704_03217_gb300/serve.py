@@ -9,9 +9,21 @@ so their work overlaps on the GPU.  A finished batch releases its memory,
 which lets the next waiting requests in.  Latency is measured from arrival to
 the moment the matches are on the host.
 
+Failures are contained to the request that caused them:
+  - a request larger than the whole budget is rejected on arrival (its
+    ``error`` says why) and the loop goes on;
+  - a batch whose launch fails (an allocation failure, an argument error)
+    is put back at the head of the queue and its requests are retried one at
+    a time, so only the failing request is evicted;
+  - a request whose device-side status reports an error (a bounded wait that
+    ran out, a failed bounds check) is evicted when its batch completes,
+    without its matches; the others of the batch deliver theirs.
+``Faults`` injects the first two kinds on the host, for tests.
+
 The admission policy (``Scheduler``) is plain Python with no GPU dependency,
 so it is tested on the CPU with a fake clock; ``GpuExecutor`` runs batches
-through the library's batched entry points.
+through the library's batched entry points, on buffers kept resident in a
+pool of slots (pyramids, workspace, match rows) reused across batches.
 """
 import collections
 import time
@@ -31,10 +43,28 @@ class Request:
     done: float = None
     matches: np.ndarray = None
     nbytes: int = 0
+    error: str = None               # why the request was rejected or evicted
 
     @property
     def latency(self):
         return None if self.done is None else self.done - self.arrival
+
+
+@dataclass
+class Faults:
+    """Host-side fault injection: request ids whose launch fails as if an
+    allocation failed, and request ids reported with a device-side error when
+    their batch completes."""
+    alloc_fail: set = field(default_factory=set)
+    device_error: set = field(default_factory=set)
+
+
+class LaunchError(RuntimeError):
+    """A batch could not be launched; ``rids`` names the requests involved."""
+
+    def __init__(self, msg, rids):
+        super().__init__(msg)
+        self.rids = list(rids)
 
 
 class Scheduler:
@@ -46,18 +76,27 @@ class Scheduler:
         self.waiting = collections.deque()
         self.in_use = 0
         self.peak = 0
+        self.rejected = []
+        self.single = 0              # requests to admit one at a time (retries)
 
-    def arrive(self, req):
+    def arrive(self, req, now=0.0):
+        """Queue a request; one larger than the whole budget is rejected
+        (returns False, req.error set)."""
         req.nbytes = int(self.bytes_of(req))
         if req.nbytes > self.budget:
-            raise ValueError("request %d needs %d bytes, over the whole budget" % (req.rid, req.nbytes))
+            req.error = "rejected: needs %d bytes, over the %d-byte budget" % (req.nbytes, self.budget)
+            req.done = now
+            self.rejected.append(req)
+            return False
         self.waiting.append(req)
+        return True
 
     def admit(self, now):
         """Requests to launch now: oldest first, stopping at the first that does
-        not fit (no overtaking), at most max_batch."""
+        not fit (no overtaking), at most max_batch (1 while retrying)."""
         batch = []
-        while self.waiting and len(batch) < self.max_batch:
+        limit = 1 if self.single > 0 else self.max_batch
+        while self.waiting and len(batch) < limit:
             r = self.waiting[0]
             if r.arrival > now or self.in_use + r.nbytes > self.budget:
                 break
@@ -65,8 +104,19 @@ class Scheduler:
             self.in_use += r.nbytes
             r.admitted = now
             batch.append(r)
+        if batch and self.single > 0:
+            self.single -= 1
         self.peak = max(self.peak, self.in_use)
         return batch
+
+    def requeue_front(self, batch):
+        """A batch whose launch failed: release it and put its requests back at
+        the head of the queue, in order, to be retried one at a time."""
+        for r in reversed(batch):
+            self.in_use -= r.nbytes
+            r.admitted = None
+            self.waiting.appendleft(r)
+        self.single += len(batch)
 
     def complete(self, batch, now):
         for r in batch:
@@ -75,49 +125,68 @@ class Scheduler:
 
 
 def serve(requests, scheduler, executor, clock=time.perf_counter, idle_sleep=0.0002):
-    """Run the continuous-batching loop until every request is done.  Request
-    arrival times are relative to the start of the loop."""
+    """Run the continuous-batching loop until every request is done, matched or
+    failed (req.error).  Request arrival times are relative to the start of
+    the loop."""
     pending = sorted(requests, key=lambda r: r.arrival)
     t0 = clock()
     i, finished = 0, 0
     while finished < len(pending):
         now = clock() - t0
         while i < len(pending) and pending[i].arrival <= now:
-            scheduler.arrive(pending[i])
+            if not scheduler.arrive(pending[i], now):
+                finished += 1                      # rejected on arrival
             i += 1
         for batch in executor.poll():
             scheduler.complete(batch, clock() - t0)
             finished += len(batch)
         batch = scheduler.admit(clock() - t0)
         if batch:
-            executor.launch(batch)
+            try:
+                executor.launch(batch)
+            except (LaunchError, MemoryError, RuntimeError) as e:
+                if len(batch) > 1:
+                    scheduler.requeue_front(batch)   # retry singly: find the culprit
+                else:
+                    batch[0].error = "evicted: %s" % e
+                    scheduler.complete(batch, clock() - t0)
+                    finished += 1
         elif idle_sleep:
             time.sleep(idle_sleep)
     return pending
 
 
 def summary(done, wall=None):
-    lat = np.array([r.latency for r in done]) * 1e3
+    """Latency and throughput of the matched requests; failed ones counted."""
+    ok = [r for r in done if r.error is None]
+    lat = np.array([r.latency for r in ok]) * 1e3
     first = min(r.arrival for r in done)
     last = max(r.done for r in done)
     span = wall if wall is not None else (last - first)
-    return {"requests": len(done), "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "pairs_per_s": len(done) / span}
+    return {"requests": len(done), "failed": len(done) - len(ok),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "pairs_per_s": len(ok) / span}
 
 
 class GpuExecutor:
     """Runs admitted batches through the library: one CUDA stream per batch in
-    flight (a small pool), completion detected with events."""
+    flight (a small pool), completion detected with events.  The device
+    buffers of a request (two pyramids, a workspace, its match rows and count,
+    and pinned host copies of these) form a slot; slots are kept in a pool
+    keyed by the pair's sizes and reused, up to ``pool_bytes`` of idle slots."""
 
-    def __init__(self, params, streams=3, device="cuda"):
+    def __init__(self, params, streams=3, device="cuda", faults=None, pool_bytes=8 << 30):
         import torch
         from . import api
         self.torch, self.api = torch, api
         self.params, self.device = params, device
+        self.faults = faults or Faults()
         self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
         self.next = 0
-        self.inflight = []            # (event, batch, buffers)
+        self.inflight = []            # (event, batch, slots)
+        self.pool = collections.defaultdict(list)
+        self.pool_bytes, self.idle_bytes = int(pool_bytes), 0
+        self.slots_made = 0
 
     def bytes_of(self, req):
         from . import _lib
@@ -132,39 +201,85 @@ class GpuExecutor:
                 + L.pgm_match_workspace_bytes(C.byref(cp), w1, h1, w2, h2)
                 + req.img1.nbytes + req.img2.nbytes + 16 * nx * ny + 4)
 
+    def _key(self, r):
+        return r.img1.shape + r.img2.shape
+
+    def _take(self, r):
+        torch, api = self.torch, self.api
+        key = self._key(r)
+        if self.pool[key]:
+            slot = self.pool[key].pop()
+            self.idle_bytes -= slot["bytes"]
+            return slot
+        h1, w1 = r.img1.shape[:2]
+        h2, w2 = r.img2.shape[:2]
+        p1 = api.Pyramid(self.params, w1, h1, self.device)
+        p2 = api.Pyramid(self.params, w2, h2, self.device)
+        ws = api.Workspace(self.params, w1, h1, w2, h2, self.device)
+        nx, ny = ws.layout(0, 0)[:2]
+        cap = max(nx * ny, 1)
+        self.slots_made += 1
+        return {"key": key, "p1": p1, "p2": p2, "ws": ws,
+                "i1": torch.empty(r.img1.shape, dtype=torch.uint8, device=self.device),
+                "i2": torch.empty(r.img2.shape, dtype=torch.uint8, device=self.device),
+                "rows": torch.empty((cap, 4), dtype=torch.int32, device=self.device),
+                "cnt": torch.zeros(1, dtype=torch.int32, device=self.device),
+                "rows_h": torch.empty((cap, 4), dtype=torch.int32).pin_memory(),
+                "cnt_h": torch.empty(1, dtype=torch.int32).pin_memory(),
+                "bytes": self.bytes_of(r)}
+
+    def _give(self, slot):
+        if self.idle_bytes + slot["bytes"] <= self.pool_bytes:
+            self.pool[slot["key"]].append(slot)
+            self.idle_bytes += slot["bytes"]
+
     def launch(self, batch):
         torch, api = self.torch, self.api
+        bad = [r.rid for r in batch if r.rid in self.faults.alloc_fail]
+        if bad:
+            raise LaunchError("injected allocation failure (request %s)" % bad, bad)
+        slots = [self._take(r) for r in batch]
         st = self.streams[self.next % len(self.streams)]
         self.next += 1
         with torch.cuda.stream(st):
-            i1 = [torch.from_numpy(r.img1).to(self.device, non_blocking=True) for r in batch]
-            i2 = [torch.from_numpy(r.img2).to(self.device, non_blocking=True) for r in batch]
-            p1 = [api.Pyramid(self.params, x.shape[1], x.shape[0], self.device) for x in i1]
-            p2 = [api.Pyramid(self.params, x.shape[1], x.shape[0], self.device) for x in i2]
-            api.build_pyramids(self.params, i1 + i2, p1 + p2, st)
-            ws = [api.Workspace(self.params, a.w, a.h, b.w, b.h, self.device) for a, b in zip(p1, p2)]
+            for r, sl in zip(batch, slots):
+                sl["i1"].copy_(torch.from_numpy(r.img1), non_blocking=True)
+                sl["i2"].copy_(torch.from_numpy(r.img2), non_blocking=True)
+            p1 = [sl["p1"] for sl in slots]
+            p2 = [sl["p2"] for sl in slots]
+            api.build_pyramids(self.params, [sl["i1"] for sl in slots] + [sl["i2"] for sl in slots],
+                               p1 + p2, st)
+            ws = [sl["ws"] for sl in slots]
             api.match_batch(self.params, p1, p2, [r.stream_id for r in batch], ws, st)
-            caps = [w.layout(0, 0)[0] * w.layout(0, 0)[1] for w in ws]
-            rows = [torch.empty((max(c, 1), 4), dtype=torch.int32, device=self.device) for c in caps]
-            cnt = [torch.zeros(1, dtype=torch.int32, device=self.device) for _ in batch]
-            api.filter_batch(self.params, ws, rows, cnt, st)
-            rows_h = [r.to("cpu", non_blocking=True) for r in rows]
-            cnt_h = [c.to("cpu", non_blocking=True) for c in cnt]
+            api.filter_batch(self.params, ws, [sl["rows"] for sl in slots],
+                             [sl["cnt"] for sl in slots], st)
+            for sl in slots:
+                sl["rows_h"].copy_(sl["rows"], non_blocking=True)
+                sl["cnt_h"].copy_(sl["cnt"], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        self.inflight.append((ev, batch, (i1, i2, p1, p2, ws, rows, cnt, rows_h, cnt_h)))
+        self.inflight.append((ev, batch, slots))
 
     def poll(self):
         done, keep = [], []
-        for ev, batch, bufs in self.inflight:
+        for ev, batch, slots in self.inflight:
             if ev.query():
-                rows_h, cnt_h = bufs[7], bufs[8]
-                for r, rh, ch in zip(batch, rows_h, cnt_h):
-                    n = int(ch.item())
-                    r.matches = rh[:min(n, rh.shape[0])].numpy()
+                for r, sl in zip(batch, slots):
+                    try:
+                        sl["ws"].sync_status()          # device-side status word of the pair
+                        failed = "injected device error" if r.rid in self.faults.device_error else None
+                    except RuntimeError as e:
+                        failed = str(e)
+                    if failed:
+                        r.error = "evicted: %s" % failed
+                        r.matches = None
+                    else:
+                        n = int(sl["cnt_h"][0])
+                        r.matches = sl["rows_h"][:min(n, sl["rows_h"].shape[0])].numpy().copy()
+                    self._give(sl)
                 done.append(batch)
             else:
-                keep.append((ev, batch, bufs))
+                keep.append((ev, batch, slots))
         self.inflight = keep
         return done
 

@@ -89,3 +89,20 @@ def test_nominal_evals_match_hand_count(lib):
     per_visit = {0: 85 * 64, 1: 43 * 32, 2: 21 * 16}
     want = sum(2 * per_visit[l] * (1 + 6 * 4) for l in [2, 1, 2, 1, 2, 1, 0])
     assert nominal_evals(p, 256, 192, 256, 192) == want
+
+
+def test_noalloc_rejects_misaligned_pointers():
+    """pgm_filter_noalloc checks its pointers before it touches the device: a
+    displacement or count pointer that is not 4-byte aligned, or a match
+    buffer that is not 16-byte aligned, gives PGM_ERR_ARG without a GPU."""
+    from paper_1704_03217_gb300 import build, _lib
+    build.build()
+    L = _lib.load()
+    cp = _lib.CParams()
+    L.pgm_default_params(C.byref(cp))
+    good = dict(u=4096, f=8192, m=16384, c=32768)
+    for bad in (dict(u=4097), dict(u=4098), dict(c=32769), dict(m=16388)):
+        a = dict(good, **bad)
+        code = L.pgm_filter_noalloc(C.byref(cp), 8, 8, C.c_void_p(a["u"]), C.c_void_p(a["f"]),
+                                    C.c_void_p(a["m"]), 64, C.c_void_p(a["c"]), None)
+        assert code == 1, (bad, code)

@@ -354,3 +354,32 @@ def test_direction_equals_sign_of_full_descriptor(color):
             f, d = full.desc(s, l), dirn.desc(s, l)
             assert set(np.unique(d)) <= {-1, 0, 1}
             assert (d == np.sign(f)).all(), (s, l)
+
+
+# ---- region removal on given arrays (Sec. III-E, reading R16) -------------
+def test_filter_arrays_vs_union_find():
+    """The oracle's region removal on caller-supplied arrays agrees with the
+    brute-force union-find, and its rows are (x, y, x + ux, y + uy) of the
+    kept seeds in raster order."""
+    class F:
+        pass
+    rng = np.random.default_rng(50)
+    for ny, nx, dmax2, mreg in [(17, 23, 4, 3), (9, 40, 144, 9), (30, 30, 1, 2)]:
+        blocks = rng.integers(-6, 7, size=(ny // 3 + 1, nx // 3 + 1, 2))
+        u = np.repeat(np.repeat(blocks, 3, 0), 3, 1)[:ny, :nx]
+        u = u + (rng.random((ny, nx, 2)) < 0.15) * rng.integers(-3, 4, size=(ny, nx, 2))
+        ux, uy = u[..., 0].astype(np.int32), u[..., 1].astype(np.int32)
+        va = (rng.random((ny, nx)) > 0.05).astype(np.uint8)
+        ol = (rng.random((ny, nx)) < 0.1).astype(np.uint8)
+        rows, keep = O.filter_arrays(dict(seed_stride=3, min_region=mreg, region_dmax2=dmax2),
+                                     ux, uy, va, ol)
+        f = F()
+        f.nx, f.ny = nx, ny
+        f.ux, f.uy = ux.ravel().tolist(), uy.ravel().tolist()
+        f.valid, f.outl = va.ravel().tolist(), ol.ravel().tolist()
+        want = brute.region_keep(f, dmax2, mreg)
+        assert (keep == want).all()
+        jj, ii = np.nonzero(want)
+        x, y = 1 + 3 * ii, 1 + 3 * jj
+        exp = np.stack([x, y, x + ux[jj, ii], y + uy[jj, ii]], -1)
+        assert rows.shape == exp.shape and (rows == exp).all()

@@ -6,7 +6,7 @@ it finishes)."""
 import numpy as np
 import pytest
 
-from paper_1704_03217_gb300.serve import Request, Scheduler, serve, summary
+from paper_1704_03217_gb300.serve import Faults, LaunchError, Request, Scheduler, serve, summary
 
 
 class FakeClock:
@@ -19,13 +19,20 @@ class FakeClock:
 
 
 class FakeExecutor:
-    """A batch of n requests finishes `base + per * n` seconds after launch."""
+    """A batch of n requests finishes `base + per * n` seconds after launch.
+    Faults as in the GPU executor: a launch containing a request of
+    faults.alloc_fail raises; a request of faults.device_error completes
+    without matches."""
 
-    def __init__(self, clock, base=0.02, per=0.005):
+    def __init__(self, clock, base=0.02, per=0.005, faults=None):
         self.clock, self.base, self.per = clock, base, per
+        self.faults = faults or Faults()
         self.inflight, self.launched, self.max_inflight = [], [], 0
 
     def launch(self, batch):
+        bad = [r.rid for r in batch if r.rid in self.faults.alloc_fail]
+        if bad:
+            raise LaunchError("injected allocation failure", bad)
         self.inflight.append((self.clock.t + self.base + self.per * len(batch), batch))
         self.launched.append([r.rid for r in batch])
         self.max_inflight = max(self.max_inflight, len(self.inflight))
@@ -35,7 +42,10 @@ class FakeExecutor:
         self.inflight = [(t, b) for t, b in self.inflight if t > self.clock.t]
         for b in done:
             for r in b:
-                r.matches = np.array([[r.rid]])
+                if r.rid in self.faults.device_error:
+                    r.error, r.matches = "evicted: injected device error", None
+                else:
+                    r.matches = np.array([[r.rid]])
         return done
 
 
@@ -70,7 +80,50 @@ def test_large_request_waits_for_memory():
     assert reqs[1].admitted >= reqs[0].done
 
 
-def test_request_over_budget_is_rejected():
-    sch = Scheduler(budget_bytes=5, max_batch=2, bytes_of=lambda r: 6)
-    with pytest.raises(ValueError):
-        sch.arrive(_reqs(1, 0.0)[0])
+def test_request_over_budget_is_rejected_and_the_loop_goes_on():
+    clock = FakeClock()
+    ex = FakeExecutor(clock)
+    sizes = {k: 3 for k in range(8)}
+    sizes[2] = 6                                          # over the whole budget
+    sch = Scheduler(budget_bytes=5, max_batch=2, bytes_of=lambda r: sizes[r.rid])
+    reqs = serve(_reqs(8, 0.003), sch, ex, clock=clock, idle_sleep=0)
+    assert reqs[2].error.startswith("rejected") and reqs[2].matches is None
+    assert [r.rid for r in sch.rejected] == [2]
+    assert all(r.error is None and r.matches[0, 0] == r.rid for r in reqs if r.rid != 2)
+    assert sch.in_use == 0 and sch.peak <= 5
+    assert summary(reqs)["failed"] == 1
+
+
+def _run(faults, n=30, max_batch=4):
+    clock = FakeClock()
+    ex = FakeExecutor(clock, faults=faults)
+    sch = Scheduler(budget_bytes=12, max_batch=max_batch, bytes_of=lambda r: 3)
+    return serve(_reqs(n, 0.002), sch, ex, clock=clock, idle_sleep=0), sch, ex
+
+
+def test_failed_launch_evicts_only_the_culprit():
+    """An allocation failure fails the whole batch's launch; its requests are
+    retried one at a time, so only the failing request is evicted and
+    reported, and every other request gets exactly the matches it gets in a
+    run without faults."""
+    clean, _, _ = _run(Faults())
+    reqs, sch, ex = _run(Faults(alloc_fail={5, 17}))
+    assert [r.rid for r in reqs if r.error] == [5, 17]
+    assert all("allocation" in reqs[k].error and reqs[k].matches is None for k in (5, 17))
+    for a, b in zip(clean, reqs):
+        if b.rid not in (5, 17):
+            assert b.error is None and (a.matches == b.matches).all()
+    assert sch.in_use == 0 and sch.peak <= 12
+    order = [rid for b in ex.launched for rid in b]
+    assert order == [k for k in range(30) if k not in (5, 17)]     # still first come, first served
+
+
+def test_device_error_evicts_only_that_request():
+    clean, _, _ = _run(Faults())
+    reqs, sch, _ = _run(Faults(device_error={3, 4, 29}))
+    assert [r.rid for r in reqs if r.error] == [3, 4, 29]
+    for a, b in zip(clean, reqs):
+        if b.rid not in (3, 4, 29):
+            assert b.error is None and (a.matches == b.matches).all()
+    s = summary(reqs)
+    assert s["failed"] == 3 and s["requests"] == 30 and sch.in_use == 0

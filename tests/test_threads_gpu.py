@@ -78,3 +78,29 @@ def test_many_caller_streams(api):
     for k, st in enumerate(streams):
         got = _run(api, p, pair, 47, st)
         assert np.array_equal(got, ref), k
+
+
+def test_kernel_limits_shared_across_threads(api):
+    """Kernel attributes (the shared-memory limit of a launch) belong to the
+    device, not to a host thread: after worker threads ran small pairs, the
+    main thread's larger pair still launches and equals its first result."""
+    p = api.Params(**PRM)
+    big = synth.sintel_like_pair(11, 512, 300)
+    small = synth.sintel_like_pair(12, 256, 120)
+    first = _run(api, p, big, 50, torch.cuda.Stream())
+    errs = []
+
+    def work(k):
+        try:
+            torch.cuda.set_device(0)
+            _run(api, p, small, 60 + k, torch.cuda.Stream())
+        except Exception as e:                       # reported below
+            errs.append("thread %d: %r" % (k, e))
+
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(3)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errs, errs
+    assert np.array_equal(_run(api, p, big, 50, torch.cuda.Stream()), first)
