@@ -166,6 +166,12 @@ bool make_pyr_plan(const pgm_params* p, int w, int h, PyrPlan* pp) {
             pp->split_pad_off[s][l] = off;
             pp->split_off[s][l] = off + inner;
             off = align_up(off + arr, 256);
+            if (p->descriptor == PGM_DIR) {      // bit-planes of the sign codes
+                const int rowbits = (pp->W[l] + 2 * BORD) * pp->nch;
+                pp->bit_row[l] = (int)align_up((size_t)(rowbits + 31) / 32 + 4, 4);
+                pp->bits_off[s][l] = off;
+                off = align_up(off + 2 * 4 * (size_t)pp->bit_row[l] * (pp->H[l] + 2 * BORD), 256);
+            }
         }
     for (int s = pp->nsch; s < 2; ++s)
         for (int l = 0; l < pp->L; ++l) {
@@ -175,6 +181,7 @@ bool make_pyr_plan(const pgm_params* p, int w, int h, PyrPlan* pp) {
             pp->split_off[s][l] = pp->split_off[0][l];
             pp->desc_pad_off[s][l] = pp->desc_pad_off[0][l];
             pp->split_pad_off[s][l] = pp->split_pad_off[0][l];
+            pp->bits_off[s][l] = pp->bits_off[0][l];
         }
     pp->bytes = off + 256;     // tail slack: vector loads never leave the buffer
     return true;
@@ -267,6 +274,10 @@ void fill_dir(const pgm_params* p, const PairCtx& c, int l, int d, DirLvl* D) {
     D->sa2 = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sa2[l][d]);
     D->sb2 = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sb2[l][d]);
     D->sa2img = reinterpret_cast<unsigned long long*>(c.ws + c.w.off_sa2img[l][d]);
+    D->rbit_row = R.bit_row[l];
+    D->tbit_row = T.bit_row[l];
+    D->ref_bits = R.bit_row[l] ? reinterpret_cast<const uint32_t*>(rp + R.bits_off[s][l]) : nullptr;
+    D->tgt_bits = T.bit_row[l] ? reinterpret_cast<const uint32_t*>(tp + T.bits_off[s][l]) : nullptr;
 }
 
 // Auxiliary streams with their fork and join events, one set per (device,
@@ -328,6 +339,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
     mc.tau2 = p->tau2;
     mc.rs_grid = p->rs_grid;
     mc.slack = tuning().slack;
+    mc.descriptor = p->descriptor;
     static thread_local LvlBatch B;       // ~8 KB: kept off the stack
     static thread_local XferBatch X;
     for (int k = 0; k < n; ++k)           // reset the evaluation counters

@@ -44,6 +44,12 @@ struct PyrPlan {
     size_t split_pad_off[2][MAXL];
     int desc_row[MAXL];          // int16 elements per padded row (also 16-bit halves of a split row)
     int pxw;                     // 32-bit words per pixel (px_words)
+    // direction descriptor only: two bit-planes per scheme and level (nonzero,
+    // then sign), rows of bit_row words covering the padded row of the
+    // descriptor, bit (x + BORD) * nch + c of row y + BORD for value c of
+    // pixel (x, y); the sign plane follows the nonzero plane's H + 2 BORD rows
+    size_t bits_off[2][MAXL];
+    int bit_row[MAXL];           // words per bit-plane row (a multiple of 4), 0: no planes
     size_t bytes;
 };
 
@@ -117,6 +123,9 @@ struct DirLvl {
     unsigned long long* sa2;     // per seed: sum over the reference patch of |G|^2
     unsigned long long* sb2;     // per target pixel (row pitch sbp): same over the target patch
     unsigned long long* sa2img;  // per reference pixel (row pitch rw): sum over its patch
+    const uint32_t* ref_bits;    // direction descriptor: bit-planes of the reference (padded row 0)
+    const uint32_t* tgt_bits;    //                       ... of the target
+    int32_t rbit_row, tbit_row;  // words per bit-plane row (0: no planes)
 };
 
 struct LvlBatch {
@@ -146,6 +155,7 @@ struct MatchConst {              // scalars common to one launch
     int32_t slack;                      // tuning: target-window margin of the tile kernels
     int32_t refresh;                    // search phase also scores the current matches first
     int32_t cost_only;                  // score the current matches only (a visit without iterations)
+    int32_t descriptor;                 // PGM_FULL, PGM_DIR (bit-plane search), PGM_SECTOR
 };
 
 // result-invariant tuning knobs (pgm_set_tuning)
@@ -174,6 +184,9 @@ struct PyrItem {                  // one image in one pyramid launch
     size_t pitch;                 // level 0: input row bytes
     int mode;                     // level 0: input mode; colour conversion: target space
     int pad;
+    uint32_t* bits;               // Sobel, direction descriptor: bit-planes (padded row 0)
+    int brow;                     // words per bit-plane row
+    int pad2;
 };
 struct PyrBatch { int n; int pad; PyrItem it[PYR_MAXB]; };
 pgm_status launch_pyramid_batch(const pgm_params* p, int n, const PyrPlan* plans,

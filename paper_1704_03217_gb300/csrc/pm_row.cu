@@ -67,6 +67,10 @@ struct RowGeom {
     int sp;                           // words per shared row (reference region and window)
     int cw, ch, cwp;                  // window centres (cw x ch), row pitch of their sums (even)
     int off_win, off_sb, words;       // word offsets in a buffer, its size (multiples of 32)
+    // bit-plane form (direction descriptor): words per staged bit row of the
+    // reference region and of the window, offsets of their sign planes (the
+    // nonzero planes start at 0 and off_win)
+    int bwr, bww, off_rs, off_ws;
 };
 
 __host__ __device__ inline RowGeom rg_geom(int nch, int P, int sigma, int rs_W, int slack) {
@@ -93,6 +97,24 @@ __host__ __device__ inline RowGeom rg_geom(int nch, int P, int sigma, int rs_W, 
     g.off_win = (g.sp * g.ref_h + 31) & ~31;            // regions start 128-byte aligned
     g.off_sb = (g.off_win + g.sp * g.win_h + 31) & ~31;
     g.words = (g.off_sb + 2 * g.cwp * g.ch + 31) & ~31;
+    return g;
+}
+
+// The same staging for bit-planes (direction descriptor): a row of P pixels
+// is P nch bits, read as NW aligned words from a staged row that starts at a
+// 16-byte boundary (up to 127 bits before the first pixel); row pitches are 4
+// (mod 8) words, so the 16 rows a half-warp reads meet at most 2 to a bank.
+__host__ __device__ inline RowGeom rg_geom_bits(int nch, int P, int sigma, int rs_W, int slack) {
+    RowGeom g = rg_geom(nch, P, sigma, rs_W, slack);
+    const int nw = nch == 6 ? 4 : 2;                      // words a lane reads per row
+    auto pitch = [](int need) { while (need % 8 != 4) ++need; return need; };
+    g.bwr = pitch((127 + sigma * (PR_TW - 1) * nch) / 32 + nw);
+    g.bww = pitch((127 + (g.win_w - P) * nch) / 32 + nw);
+    g.off_rs = (g.bwr * g.ref_h + 31) & ~31;
+    g.off_win = (g.off_rs + g.bwr * g.ref_h + 31) & ~31;
+    g.off_ws = (g.off_win + g.bww * g.win_h + 31) & ~31;
+    g.words = (g.off_ws + g.bww * g.win_h + 31) & ~31;
+    g.off_sb = 0;
     return g;
 }
 
@@ -201,17 +223,32 @@ __device__ __forceinline__ int row_slot(const RowGeom& G, const RowHdr& H, int P
     return (y0 * G.sp + H.shw + x0 * G.pxw) | ((y0 * G.cwp + H.shs + x0) << 16);
 }
 
+// The slot of a candidate for the producer: row_slot, or for the bit-plane
+// form its patch corner (y0, x0) in the window as y0 << 16 | x0 (-1 outside).
+template <bool BITS>
+__device__ __forceinline__ int pr_slot(const RowGeom& G, const RowHdr& H, int P, int qx, int qy) {
+    if constexpr (BITS) {
+        const int x0 = qx - P / 2 - H.wx0, y0 = qy - P / 2 - H.wy0;
+        if (!H.use_win || x0 < 0 || y0 < 0 || x0 + P > G.win_w || y0 + P > G.win_h) return -1;
+        return (y0 << 16) | x0;
+    } else {
+        return row_slot(G, H, P, qx, qy);
+    }
+}
+
 // Producer warp p: stage the CTA's tiles n = p, p + PR_PROD, ... (launch tiles
 // blockIdx.x + n * gridDim.x) into buffer n mod nbuf.
-template <int NCH>
+template <int NCH, bool BITS, int NPROD, int NBUFMAX>
 __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSched& S,
                            const RowMaps& TM, int buf_words, int nbuf, unsigned a_sm,
                            RowRec (*rec)[PR_NACT], RowHdr* hdr, int* next, const RowGeom* geom,
                            unsigned full0, unsigned empty0, volatile int* abort, long long limit,
                            int pw, int lane) {
     constexpr int PXW = px_words(NCH);
-    int lastn[PR_NBUF] = {-1, -1, -1};       // the tile this warp last armed in each buffer
-    for (int n = pw;; n += PR_PROD) {
+    int lastn[NBUFMAX];                      // the tile this warp last armed in each buffer
+#pragma unroll
+    for (int b = 0; b < NBUFMAX; ++b) lastn[b] = -1;
+    for (int n = pw;; n += NPROD) {
         const int t = blockIdx.x + n * gridDim.x;
         if (t >= S.total) break;
         const int b = n % nbuf;
@@ -239,12 +276,20 @@ __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSch
         const int i0 = (tt % tiles_x) * PR_TW, j0 = (tt / tiles_x) * PR_TH;
         const int P = D.P, h = P / 2, sig = mc.sigma;
         const int rx0 = mc.c + sig * i0 - h, ry0 = mc.c + sig * j0 - h;
-        const int shr = PXW == 4 ? 0 : ((rx0 + BORD) & 3);
+        // bit-plane form: first staged word (a multiple of 4) and bit shift
+        const int rbit = (rx0 + BORD) * NCH, rws = (rbit >> 5) & ~3;
+        const int shr = BITS ? rbit - 32 * rws : PXW == 4 ? 0 : ((rx0 + BORD) & 3);
         const unsigned buf = a_sm + 4u * (unsigned)(b * buf_words);
         fence_proxy_async();                         // the consumers' reads of this buffer come first
         if (lane == 0) {                             // the reference region does not depend on the seeds
-            mbar_expect_tx(full, 4u * (unsigned)(G.sp * G.ref_h));
-            tma2d(buf, &TM.m[k][0], PXW == 4 ? 2 * (rx0 + BORD) : rx0 + BORD - shr, ry0 + BORD, full);
+            if constexpr (BITS) {                    // nonzero rows, then sign rows H + 2 BORD below
+                mbar_expect_tx(full, 8u * (unsigned)(G.bwr * G.ref_h));
+                tma2d(buf, &TM.m[k][0], rws, ry0 + BORD, full);
+                tma2d(buf + 4u * (unsigned)G.off_rs, &TM.m[k][0], rws, D.rh + 2 * BORD + ry0 + BORD, full);
+            } else {
+                mbar_expect_tx(full, 4u * (unsigned)(G.sp * G.ref_h));
+                tma2d(buf, &TM.m[k][0], PXW == 4 ? 2 * (rx0 + BORD) : rx0 + BORD - shr, ry0 + BORD, full);
+            }
         }
         // the seed of this lane: active seed a = lane of the tile (Eq. 4 candidates, Eq. 5 draws)
         const int t4 = mc.t & 3;
@@ -305,17 +350,20 @@ __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSch
             }
         }
         // window centre: per component, the median of the valid current
-        // matches, the (nv / 2)-th smallest (0-based) found one bit at a time
-        // from the top of the order-preserving 16-bit keys
+        // matches, the (nv / 2)-th smallest (0-based), found one bit at a time
+        // over the offsets from the smallest value (only the bits in which the
+        // tile's values differ)
         const bool v = R.s >= 0 && (R.f & F_VALID);
         const unsigned vm = __ballot_sync(FULL, v);
         const int nv = __popc(vm);
         const int ux = lo16((uint32_t)R.u), uy = hi16((uint32_t)R.u);
-        const unsigned kx = (unsigned)(ux + 32768), ky = (unsigned)(uy + 32768);
+        const int lox = __reduce_min_sync(FULL, v ? ux : INT_MAX);
+        const int loy = __reduce_min_sync(FULL, v ? uy : INT_MAX);
+        const unsigned kx = v ? (unsigned)(ux - lox) : 0u, ky = v ? (unsigned)(uy - loy) : 0u;
+        const unsigned span = __reduce_or_sync(FULL, kx | ky);
         unsigned cx = vm, cy = vm;
         int mx = nv / 2, my = nv / 2;
-#pragma unroll
-        for (int bit = 15; bit >= 0; --bit) {
+        for (int bit = span ? 31 - __clz(span) : -1; bit >= 0; --bit) {
             const unsigned zx = __ballot_sync(FULL, !((kx >> bit) & 1u)) & cx;
             const unsigned zy = __ballot_sync(FULL, !((ky >> bit) & 1u)) & cy;
             const int px_ = __popc(zx), py_ = __popc(zy);
@@ -331,13 +379,14 @@ __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSch
         H.wx0 = nv > 0 ? rx0 + medx - rho - mc.slack : 0;
         H.wy0 = nv > 0 ? ry0 + medy - rho - mc.slack : 0;
         H.shr = shr;
-        H.shw = PXW == 4 ? 0 : ((H.wx0 + BORD) & 3);
+        const int wbit = (H.wx0 + BORD) * NCH, wws = (wbit >> 5) & ~3;
+        H.shw = BITS ? wbit - 32 * wws : PXW == 4 ? 0 : ((H.wx0 + BORD) & 3);
         H.shs = (H.wx0 + h) & 1;
-        H.pad0 = 0; H.pad1 = 0;
+        H.pad0 = wws; H.pad1 = 0;
         // the window slots of the candidates known now
-        R.wu = R.s >= 0 ? row_slot(G, H, P, R.px + lo16((uint32_t)R.u), R.py + hi16((uint32_t)R.u)) : -1;
-        R.w0 = R.nb0 != NO_CAND ? row_slot(G, H, P, R.px + lo16((uint32_t)R.nb0), R.py + hi16((uint32_t)R.nb0)) : -1;
-        R.w1 = R.nb1 != NO_CAND ? row_slot(G, H, P, R.px + lo16((uint32_t)R.nb1), R.py + hi16((uint32_t)R.nb1)) : -1;
+        R.wu = R.s >= 0 ? pr_slot<BITS>(G, H, P, R.px + lo16((uint32_t)R.u), R.py + hi16((uint32_t)R.u)) : -1;
+        R.w0 = R.nb0 != NO_CAND ? pr_slot<BITS>(G, H, P, R.px + lo16((uint32_t)R.nb0), R.py + hi16((uint32_t)R.nb0)) : -1;
+        R.w1 = R.nb1 != NO_CAND ? pr_slot<BITS>(G, H, P, R.px + lo16((uint32_t)R.nb1), R.py + hi16((uint32_t)R.nb1)) : -1;
         // the first two search candidates around the current match, the
         // centre of the search unless a propagated match wins
         if (R.s >= 0 && (R.f & F_VALID) && R.K > 0) {
@@ -346,7 +395,7 @@ __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSch
                 const uint32_t o = (uint32_t)(k ? R.r1 : R.r0);
                 const int qx = R.px + ux + lo16(o), qy = R.py + uy + hi16(o);
                 const bool ok = k < R.K && o != 0u && inside(D, qx, qy);
-                const int w = ok ? row_slot(G, H, P, qx, qy) : -2;
+                const int w = ok ? pr_slot<BITS>(G, H, P, qx, qy) : -2;
                 if (k) R.wr1 = w; else R.wr0 = w;
             }
         }
@@ -358,10 +407,17 @@ __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSch
         __syncwarp();
         if (lane == 0) {
             if (H.use_win) {
-                mbar_arrive_tx(full, 4u * (unsigned)(G.sp * G.win_h) + 8u * (unsigned)(G.cwp * G.ch));
-                tma2d(buf + 4u * (unsigned)G.off_win, &TM.m[k][1],
-                      PXW == 4 ? 2 * (H.wx0 + BORD) : H.wx0 + BORD - H.shw, H.wy0 + BORD, full);
-                tma2d(buf + 4u * (unsigned)G.off_sb, &TM.m[k][2], H.wx0 + h - H.shs, H.wy0 + h, full);
+                if constexpr (BITS) {
+                    mbar_arrive_tx(full, 8u * (unsigned)(G.bww * G.win_h));
+                    tma2d(buf + 4u * (unsigned)G.off_win, &TM.m[k][1], wws, H.wy0 + BORD, full);
+                    tma2d(buf + 4u * (unsigned)G.off_ws, &TM.m[k][1], wws,
+                          D.th + 2 * BORD + H.wy0 + BORD, full);
+                } else {
+                    mbar_arrive_tx(full, 4u * (unsigned)(G.sp * G.win_h) + 8u * (unsigned)(G.cwp * G.ch));
+                    tma2d(buf + 4u * (unsigned)G.off_win, &TM.m[k][1],
+                          PXW == 4 ? 2 * (H.wx0 + BORD) : H.wx0 + BORD - H.shw, H.wy0 + BORD, full);
+                    tma2d(buf + 4u * (unsigned)G.off_sb, &TM.m[k][2], H.wx0 + h - H.shs, H.wy0 + h, full);
+                }
             } else {
                 mbar_arrive(full);
             }
@@ -643,11 +699,270 @@ k_pm_r(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
     __syncthreads();
     volatile int* abort = &s_abort;
     if (warp >= pr_cons(NCH, PC))
-        pr_produce<NCH>(B, mc, S, TM, buf_words, nbuf, a_sm, s_rec, s_hdr, s_next, s_geom, full0,
+        pr_produce<NCH, false, PR_PROD, PR_NBUF>(B, mc, S, TM, buf_words, nbuf, a_sm, s_rec, s_hdr, s_next, s_geom, full0,
                         empty0, abort, limit, warp - pr_cons(NCH, PC), lane);
     else
         pr_consume<NCH, PC>(B, mc, S, buf_words, nbuf, a_sm, sm, s_rec, s_hdr, s_next, s_geom,
                             full0, empty0, abort, limit, lane);
+}
+
+// ------------------------------------------------------------------
+// Bit-plane search (direction descriptor, Sec. III-F: every value a sign in
+// {-1, 0, +1}).  With a nonzero plane nz and a sign plane s, a channel pair
+// (a, b) gives (a - b)^2 = 1 when exactly one is zero and 4 when both are
+// nonzero with opposite signs, else 0 (|a - b| = 1, 2 for the L1 cost), so a
+// 32-bit word of 32 values costs popc(nzA ^ nzB) + 4 popc(nzA & nzB & (sA ^ sB)).
+// A warp scores one seed at a time, two candidates per step: lane r of
+// half-warp h works on patch row r of candidate h (rows past P count zero);
+// it keeps the row's reference bits in registers (NR words per plane) and
+// reads the candidate row as NW staged words per plane, aligned by funnel
+// shifts.  The cost of a candidate is the half-warp sum; costs fit 32 bits.
+template <int NCH, int PC>
+__device__ void pr_consume_bits(const LvlBatch& B, const MatchConst& mc, const RowSched& S,
+                                int buf_words, int nbuf, unsigned a_sm, RowRec (*rec)[PR_NACT],
+                                const RowHdr* hdr, int* next, const RowGeom* geom, unsigned full0,
+                                unsigned empty0, volatile int* abort, long long limit, int lane) {
+    constexpr int NR = NCH == 6 ? 3 : 1;          // aligned words per row and plane
+    constexpr int NW = NR + 1;                    // staged words read per row and plane
+    constexpr unsigned INF32 = 0xffffffffu;
+    const int hf = lane >> 4, r = lane & 15;
+    const unsigned fac = mc.norm == PGM_L2SQ ? 2u : 1u;      // 4 = 1 << 2, 2 = 1 << 1
+    for (int n = 0;; ++n) {
+        const int t = blockIdx.x + n * gridDim.x;
+        if (t >= S.total) break;
+        const int b = n % nbuf;
+        if (!__all_sync(FULL, mbar_wait(full0 + 8u * b, (unsigned)(n / nbuf) & 1u, limit, abort))) {
+            if (lane == 0 && !*abort) {
+                for (int k = 0; k < B.n; ++k) atomicOr(B.err[k], (unsigned)PGM_ERR_TIMEOUT);
+                *abort = 1;
+            }
+            break;
+        }
+        const RowHdr H = hdr[b];
+        const RowGeom& G = geom[H.dir];
+        const DirLvl& D = B.d[H.pair][H.dir];
+        const int P = PC > 0 ? PC : G.P, h = P / 2;
+        const bool live = r < P;
+        const int rr = live ? r : 0;
+        unsigned msk[NR];                             // the row's bits in each aligned word
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const int nb = P * NCH - 32 * k;
+            msk[k] = !live || nb <= 0 ? 0u : nb >= 32 ? 0xffffffffu : (1u << nb) - 1u;
+        }
+        const unsigned buf = a_sm + 4u * (unsigned)(b * buf_words);
+        const unsigned a_rn = buf, a_rs = buf + 4u * (unsigned)G.off_rs;
+        const unsigned a_wn = buf + 4u * (unsigned)G.off_win, a_ws = buf + 4u * (unsigned)G.off_ws;
+        const int tplane = D.tbit_row * (D.th + 2 * BORD);   // words from the nonzero to the sign plane
+        unsigned n_eval = 0, n_cost = 0, n_glob = 0;
+        for (;;) {
+            int a = 0;
+            if (lane == 0) a = atomicAdd(next + b, 1);
+            a = __shfl_sync(FULL, a, 0);
+            if (a >= PR_NACT) break;
+            const RowRec R = rec[b][a];
+            const int s = R.s;
+            if (s < 0) continue;
+            const int Rf = R.f, Ru = R.u;
+            bool have = Rf & F_VALID;
+            if (!have && R.nb0 == NO_CAND && R.nb1 == NO_CAND) {
+                if (lane == 0 && Rf != R.f0) D.flags[s] = (uint8_t)Rf;
+                continue;
+            }
+            const int px = R.px, py = R.py;
+            // the reference bits of patch row rr
+            unsigned an[NR], as[NR];
+            {
+                const int bit = H.shr + (px - h - H.rx0) * NCH, w = bit >> 5, sh = bit & 31;
+                const unsigned rown = a_rn + 4u * (unsigned)((py - h - H.ry0 + rr) * G.bwr + w);
+                const unsigned rows = a_rs + 4u * (unsigned)((py - h - H.ry0 + rr) * G.bwr + w);
+                unsigned vn[NW], vs[NW];
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    vn[k] = (unsigned)lds32(rown + 4u * k);
+                    vs[k] = (unsigned)lds32(rows + 4u * k);
+                }
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    an[k] = __funnelshift_r(vn[k], vn[k + 1], sh) & msk[k];
+                    as[k] = __funnelshift_r(vs[k], vs[k + 1], sh);
+                }
+            }
+            // cost of this half-warp's candidate (window slot y0 << 16 | x0,
+            // or -1: from the padded bit-planes in global memory); INF32 when
+            // !valid (the lanes then read the window origin)
+            auto eval = [&](bool valid, int slot, int qx, int qy) -> unsigned {
+                if (!valid) { slot = H.use_win ? 0 : -1; qx = 0; qy = 0; }
+                unsigned vn[NW], vs[NW];
+                int sh;
+                if (slot >= 0) {
+                    const int bit = H.shw + (slot & 0xffff) * NCH, w = bit >> 5;
+                    sh = bit & 31;
+                    const unsigned o = 4u * (unsigned)(((slot >> 16) + rr) * G.bww + w);
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) {
+                        vn[k] = (unsigned)lds32(a_wn + o + 4u * k);
+                        vs[k] = (unsigned)lds32(a_ws + o + 4u * k);
+                    }
+                } else {
+                    const int bit = (qx - h + BORD) * NCH, w = bit >> 5;
+                    sh = bit & 31;
+                    const uint32_t* rowp = D.tgt_bits + (size_t)(qy - h + rr + BORD) * D.tbit_row + w;
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) {
+                        vn[k] = __ldg(rowp + k);
+                        vs[k] = __ldg(rowp + tplane + k);
+                    }
+                }
+                unsigned c = 0;
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    const unsigned tn = __funnelshift_r(vn[k], vn[k + 1], sh);
+                    const unsigned ts = __funnelshift_r(vs[k], vs[k + 1], sh);
+                    c += (unsigned)__popc((an[k] ^ tn) & msk[k]) +
+                         ((unsigned)__popc(an[k] & tn & (as[k] ^ ts)) << fac);
+                }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+                const unsigned gl = __ballot_sync(FULL, valid && slot < 0);
+                if (lane == 0) n_glob += __popc(gl & 0x00010001u);
+                return valid ? c : INF32;
+            };
+            unsigned bc = have ? (unsigned)R.cost : INF32;   // R.cost is INF when refreshing
+            if (mc.refresh) bc = INF32;
+            int32_t bu = Ru;
+            // stage 1 in order: the current match (refresh), the propagated ones
+            unsigned pm = ((mc.refresh && have) ? 1u : 0u) | (R.nb0 != NO_CAND ? 2u : 0u) |
+                          (R.nb1 != NO_CAND ? 4u : 0u);
+            while (pm) {
+                const int iA = __ffs(pm) - 1;
+                pm &= pm - 1;
+                const int iB = pm ? __ffs(pm) - 1 : -1;
+                if (pm) pm &= pm - 1;
+                const int me = hf ? iB : iA;
+                const int cu = me == 0 ? Ru : me == 1 ? R.nb0 : R.nb1;
+                const int sl = me == 0 ? R.wu : me == 1 ? R.w0 : R.w1;
+                const unsigned c = eval(me >= 0, sl, px + lo16((uint32_t)cu), py + hi16((uint32_t)cu));
+                const unsigned co = __shfl_xor_sync(FULL, c, 16);
+                const unsigned cA = hf ? co : c, cB = hf ? c : co;
+                const int uA = iA == 0 ? Ru : iA == 1 ? R.nb0 : R.nb1;
+                const int uB = iB == 1 ? R.nb0 : R.nb1;
+                if (iA == 0) ++n_cost; else ++n_eval;
+                if (cA < bc) { bc = cA; bu = uA; have = true; }
+                if (iB >= 0) {
+                    ++n_eval;
+                    if (cB < bc) { bc = cB; bu = uB; have = true; }
+                }
+            }
+            // stage 2: the limited random search (Eq. 5) around the match held
+            // after propagation, offsets k0 and k0 + 1 per step
+            const int K = R.K;
+            if (have && K > 0) {
+                const int ux0 = lo16((uint32_t)bu), uy0 = hi16((uint32_t)bu);
+                const bool atu = bu == Ru && (Rf & F_VALID);      // slots from the producer
+                for (int k0 = 0; k0 < K; k0 += 2) {
+                    const int k = k0 + hf;
+                    int dx = 0, dy = 0;
+                    if (k < 2) {
+                        const uint32_t o = (uint32_t)(k ? R.r1 : R.r0);
+                        dx = lo16(o);
+                        dy = hi16(o);
+                    } else if (k < K) {
+                        const uint4 rq = philox(
+                            make_uint4((uint32_t)s,
+                                       ((uint32_t)B.visit << 16) | ((uint32_t)H.dir << 15) | (uint32_t)mc.t,
+                                       ((uint32_t)B.level << 16) | (uint32_t)(k >> 1),
+                                       B.stream_id[H.pair]),
+                            mc.key0, mc.key1);
+                        dx = rs_off((k & 1) ? rq.z : rq.x, k, mc.rs_W, mc.rs_mode);
+                        dy = rs_off((k & 1) ? rq.w : rq.y, k, mc.rs_W, mc.rs_mode);
+                    }
+                    const int qx = px + ux0 + dx, qy = py + uy0 + dy;   // tested before packing
+                    int sl;
+                    bool valid;
+                    if (atu && k < 2) {
+                        const int w = k ? R.wr1 : R.wr0;
+                        valid = w != -2;
+                        sl = valid ? w : 0;
+                    } else {
+                        valid = k < K && !(dx == 0 && dy == 0) && inside(D, qx, qy);
+                        sl = valid ? pr_slot<true>(G, H, P, qx, qy) : 0;
+                    }
+                    const unsigned c = eval(valid, sl, qx, qy);
+                    const unsigned co = __shfl_xor_sync(FULL, c, 16);
+                    const unsigned vb = __ballot_sync(FULL, valid);
+                    const unsigned cA = hf ? co : c, cB = hf ? c : co;
+                    const int dxA = __shfl_sync(FULL, dx, 0), dyA = __shfl_sync(FULL, dy, 0);
+                    const int dxB = __shfl_sync(FULL, dx, 16), dyB = __shfl_sync(FULL, dy, 16);
+                    if (vb & 1u) {
+                        ++n_eval;
+                        if (cA < bc) { bc = cA; bu = pack_u(ux0 + dxA, uy0 + dyA); }
+                    }
+                    if (vb & 0x10000u) {
+                        ++n_eval;
+                        if (cB < bc) { bc = cB; bu = pack_u(ux0 + dxB, uy0 + dyB); }
+                    }
+                }
+            }
+            if (lane == 0) {
+                if (have && (mc.refresh || bu != Ru || !(Rf & F_VALID))) {
+                    D.u[s] = bu;
+                    D.cost[s] = (unsigned long long)bc;
+                    D.flags[s] = (uint8_t)(Rf | F_VALID);
+                } else if (!have && Rf != R.f0) {
+                    D.flags[s] = (uint8_t)Rf;
+                }
+            }
+        }
+        if (lane == 0) {
+            if (n_eval) atomicAdd(B.evals[H.pair] + H.dir, (unsigned long long)n_eval);
+            if (n_cost) atomicAdd(B.evals[H.pair] + 2 + H.dir, (unsigned long long)n_cost);
+            if (n_glob) atomicAdd(B.evals[H.pair] + 6 + H.dir, (unsigned long long)n_glob);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty0 + 8u * b);
+    }
+}
+
+// the bit-plane kernel: its buffers are small, so more producer warps keep a
+// deeper ring of staged tiles
+constexpr int PB_PROD = 4, PB_CONS = 20, PB_NBUF = 8;
+
+template <int NCH, int PC>
+__global__ void __launch_bounds__(32 * (PB_PROD + PB_CONS), 1)
+k_pm_b(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_constant__ RowSched S,
+       const __grid_constant__ RowMaps TM, const int buf_words, const int nbuf,
+       const long long limit) {
+    extern __shared__ __align__(128) uint32_t sm[];
+    __shared__ RowRec s_rec[PB_NBUF][PR_NACT];
+    __shared__ RowHdr s_hdr[PB_NBUF];
+    __shared__ RowGeom s_geom[2];
+    __shared__ __align__(8) unsigned long long s_full[PB_NBUF], s_empty[PB_NBUF];
+    __shared__ int s_next[PB_NBUF];
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned a_sm = (unsigned)__cvta_generic_to_shared(sm);
+    const unsigned full0 = (unsigned)__cvta_generic_to_shared(&s_full[0]);
+    const unsigned empty0 = (unsigned)__cvta_generic_to_shared(&s_empty[0]);
+    if (threadIdx.x < 2)
+        s_geom[threadIdx.x] = rg_geom_bits(NCH, B.d[0][threadIdx.x].P, mc.sigma, mc.rs_W, mc.slack);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < nbuf; ++b) {
+            mbar_init(full0 + 8u * b, 1);
+            mbar_init(empty0 + 8u * b, PB_CONS);
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    volatile int* abort = &s_abort;
+    if (warp >= PB_CONS)
+        pr_produce<NCH, true, PB_PROD, PB_NBUF>(B, mc, S, TM, buf_words, nbuf, a_sm, s_rec, s_hdr,
+                                                s_next, s_geom, full0, empty0, abort, limit,
+                                                warp - PB_CONS, lane);
+    else
+        pr_consume_bits<NCH, PC>(B, mc, S, buf_words, nbuf, a_sm, s_rec, s_hdr, s_next, s_geom,
+                                 full0, empty0, abort, limit, lane);
 }
 
 }  // namespace
@@ -765,12 +1080,26 @@ static bool dir_maps(const DirLvl& D, int nch, const RowGeom& g, CUtensorMap* m)
            map2d(&m[2], D.sb2, D.sbp, D.th, 8ull * D.sbp, g.cwp, g.ch, 8);
 }
 
+// The two maps of the bit-plane form: the reference and the target planes,
+// each one array of 2 (H + 2 BORD) rows (nonzero rows, then sign rows).
+static bool dir_maps_bits(const DirLvl& D, const RowGeom& g, CUtensorMap* m) {
+    if (!D.ref_bits || !D.tgt_bits || D.rbit_row <= 0 || D.tbit_row <= 0) return false;
+    return map2d(&m[0], D.ref_bits, D.rbit_row, 2ull * (D.rh + 2 * BORD), 4ull * D.rbit_row,
+                 g.bwr, g.ref_h, 4) &&
+           map2d(&m[1], D.tgt_bits, D.tbit_row, 2ull * (D.th + 2 * BORD), 4ull * D.tbit_row,
+                 g.bww, g.win_h, 4);
+}
+
+// the search runs on the bit-planes (direction descriptor)
+static bool use_bits(const MatchConst& mc) { return mc.descriptor == PGM_DIR; }
+
 // Per-direction schedules S[0], S[1], the schedule of both directions
 // together S[2], and the layouts; false when a buffer ring would not fit in
 // shared memory, a slot would not fit its 16-bit fields, or a tensor map
 // cannot be made (each is encoded here, and cached for the launches).
 static bool pr_plan(const LvlBatch& B, const MatchConst& mc, int nch, RowSched* S, RowGeom* G) {
-    if (mc.norm != PGM_L2SQ || B.n > PR_MAPS) return false;
+    const bool bits = use_bits(mc);
+    if ((!bits && mc.norm != PGM_L2SQ) || B.n > PR_MAPS) return false;
     S[2].nk = 2 * B.n;
     S[2].total = 0;
     S[2].dir = 0;
@@ -780,7 +1109,8 @@ static bool pr_plan(const LvlBatch& B, const MatchConst& mc, int nch, RowSched* 
         S[d].total = 0;
         S[d].dir = d;
         S[d].ndir = 1;
-        G[d] = rg_geom(nch, B.d[0][d].P, mc.sigma, mc.rs_W, mc.slack);
+        G[d] = bits ? rg_geom_bits(nch, B.d[0][d].P, mc.sigma, mc.rs_W, mc.slack)
+                    : rg_geom(nch, B.d[0][d].P, mc.sigma, mc.rs_W, mc.slack);
         if (B.d[0][d].P > MAXP || 2L * G[d].words * 4 > 200L * 1024 ||
             (long)G[d].sp * G[d].win_h >= 65536L || (long)G[d].cwp * G[d].ch >= 32768L)
             return false;
@@ -794,7 +1124,8 @@ static bool pr_plan(const LvlBatch& B, const MatchConst& mc, int nch, RowSched* 
             S[d].total += tiles;
             S[2].cum[2 * k + d] = S[2].total;
             S[2].total += tiles;
-            if (D.P != B.d[0][d].P || !dir_maps(D, nch, G[d], m)) return false;
+            if (D.P != B.d[0][d].P || !(bits ? dir_maps_bits(D, G[d], m) : dir_maps(D, nch, G[d], m)))
+                return false;
         }
     S[0].cum[B.n] = S[0].total;
     S[1].cum[B.n] = S[1].total;
@@ -804,11 +1135,12 @@ static bool pr_plan(const LvlBatch& B, const MatchConst& mc, int nch, RowSched* 
 
 // The maps of every slot of schedule S (one thread's launch parameters;
 // cache hits after pr_plan).
-static RowMaps& pr_maps(const LvlBatch& B, int nch, const RowSched& S, const RowGeom* G) {
+static RowMaps& pr_maps(const LvlBatch& B, int nch, bool bits, const RowSched& S, const RowGeom* G) {
     static thread_local RowMaps TM;
     for (int k = 0; k < S.nk && k < PR_MAPS; ++k) {
         const int pair = S.ndir == 2 ? k >> 1 : k, dir = S.ndir == 2 ? (k & 1) : S.dir;
-        dir_maps(B.d[pair][dir], nch, G[dir], TM.m[k]);
+        if (bits) dir_maps_bits(B.d[pair][dir], G[dir], TM.m[k]);
+        else dir_maps(B.d[pair][dir], nch, G[dir], TM.m[k]);
     }
     return TM;
 }
@@ -816,17 +1148,21 @@ static RowMaps& pr_maps(const LvlBatch& B, int nch, const RowSched& S, const Row
 // wait limit of the kernel's mbarrier waits (cycles); set by pgm_set_wait_limit
 long long wait_limit();
 
-template <int NCH, int PC>
+template <int NCH, int PC, bool BITS = false>
 pgm_status launch_r(const LvlBatch& B, const MatchConst& mc, const RowSched& S, const RowMaps& TM,
                     int buf_words, cudaStream_t st) {
-    const int nbuf = 3L * buf_words * 4 <= 200L * 1024 ? 3 : 2;
+    const int most = BITS ? PB_NBUF : PR_NBUF;
+    int nbuf = 2;
+    while (nbuf < most && (nbuf + 1L) * buf_words * 4 <= 200L * 1024) ++nbuf;
     const int smem = nbuf * buf_words * 4;
     auto kern = k_pm_r<NCH, PC>;
+    if constexpr (BITS) kern = k_pm_b<NCH, PC>;
     if (pgm_status r = smem_opt_in((const void*)kern); r != PGM_OK) return r;
     const int sms = device_sms();
     if (sms <= 0) return cuda_fail("search: SM count", cudaErrorInvalidDevice);
     const int grid = S.total < sms ? S.total : sms;       // one CTA per SM (shared memory)
-    kern<<<grid, 32 * (PR_PROD + pr_cons(NCH, PC)), smem, st>>>(B, mc, S, TM, buf_words, nbuf, wait_limit());
+    const int threads = BITS ? 32 * (PB_PROD + PB_CONS) : 32 * (PR_PROD + pr_cons(NCH, PC));
+    kern<<<grid, threads, smem, st>>>(B, mc, S, TM, buf_words, nbuf, wait_limit());
     return launch_status("search: launch");
 }
 
@@ -871,19 +1207,28 @@ pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int 
     if (!pr_plan(B, mc, nch, S, G)) return PGM_OK;
     *handled = true;
     if (S[2].total == 0) return PGM_OK;
+    const bool bits = use_bits(mc);
     if (S[2].total <= device_sms() && 2 * B.n <= PR_MAPS) {
         const int words = G[0].words > G[1].words ? G[0].words : G[1].words;
         *nlaunch = 1;
-        RowMaps& TM = pr_maps(B, nch, S[2], G);
+        RowMaps& TM = pr_maps(B, nch, bits, S[2], G);
+        if (bits)
+            return nch == 2 ? launch_r<2, 0, true>(B, mc, S[2], TM, words, st)
+                            : launch_r<6, 0, true>(B, mc, S[2], TM, words, st);
         return nch == 2 ? launch_r<2, 0>(B, mc, S[2], TM, words, st)
                         : launch_r<6, 0>(B, mc, S[2], TM, words, st);
     }
     for (int d = 0; d < 2; ++d) {
         if (S[d].total == 0) continue;
-        RowMaps& TM = pr_maps(B, nch, S[d], G);
+        RowMaps& TM = pr_maps(B, nch, bits, S[d], G);
         const cudaStream_t sd = d == 1 && st2 ? st2 : st;
-        const pgm_status r = nch == 2 ? launch_dir<2>(B, mc, S[d], G[d].P, TM, G[d].words, sd)
-                                      : launch_dir<6>(B, mc, S[d], G[d].P, TM, G[d].words, sd);
+        pgm_status r;
+        if (bits)          // the bit-plane consumer's inner loops do not depend on P
+            r = nch == 2 ? launch_r<2, 0, true>(B, mc, S[d], TM, G[d].words, sd)
+                         : launch_r<6, 0, true>(B, mc, S[d], TM, G[d].words, sd);
+        else
+            r = nch == 2 ? launch_dir<2>(B, mc, S[d], G[d].P, TM, G[d].words, sd)
+                         : launch_dir<6>(B, mc, S[d], G[d].P, TM, G[d].words, sd);
         if (r != PGM_OK) return r;
         ++*nlaunch;
     }

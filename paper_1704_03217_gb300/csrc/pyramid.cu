@@ -294,6 +294,32 @@ __global__ void __launch_bounds__(SB_TW * SB_TY) k_sobel(const __grid_constant__
     }
 }
 
+// ------------------------------------------------- direction bit-planes
+// For the direction descriptor: word w of padded row yy of the nonzero and
+// the sign bit-plane from the padded descriptor (bit b = x nch + c holds
+// value c of padded pixel x; words past the row are zero).  One thread per
+// word of one image (blockIdx.z).
+__global__ void k_bits(const __grid_constant__ PyrBatch B, int nch, int pxe) {
+    const PyrItem& it = B.it[blockIdx.z];
+    const int w = blockIdx.x * blockDim.x + threadIdx.x, yy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int pw = it.sw + 2 * BORD, ph = it.sh + 2 * BORD;
+    if (w >= it.brow || yy >= ph) return;
+    // padded pixel x of row yy: it.dst points at pixel (0, 0), rows drow int16
+    const int16_t* row = reinterpret_cast<const int16_t*>(it.dst) + (ptrdiff_t)(yy - BORD) * it.drow -
+                         (ptrdiff_t)BORD * pxe;
+    uint32_t nz = 0, sg = 0;
+    const int b0 = 32 * w;
+    for (int k = 0; k < 32; ++k) {
+        const int b = b0 + k, x = b / nch, c = b - x * nch;
+        if (x >= pw) break;
+        const int v = row[(ptrdiff_t)x * pxe + c];
+        nz |= (uint32_t)(v != 0) << k;
+        sg |= (uint32_t)(v < 0) << k;
+    }
+    it.bits[(size_t)yy * it.brow + w] = nz;
+    it.bits[(size_t)(ph + yy) * it.brow + w] = sg;
+}
+
 }  // namespace
 
 // One launch per step of the pyramid for a whole batch of images (all with
@@ -309,7 +335,7 @@ pgm_status launch_pyramid_batch(const pgm_params* p, int n, const PyrPlan* plans
     const int dir_only = p->descriptor;      // 0 full, 1 signs, 2 sectors
     for (int base = 0; base < n; base += PYR_MAXB) {
         const int m = n - base < PYR_MAXB ? n - base : PYR_MAXB;
-        int nlaunch = L + nsch * L;
+        int nlaunch = L + nsch * L * (dir_only == 1 ? 2 : 1);
         for (int s = 0; s < nsch; ++s)
             for (int l = 0; l < L; ++l)
                 nlaunch += p0.space[s][l] == SP_LAB || p0.space[s][l] == SP_YCRCB;
@@ -378,6 +404,18 @@ pgm_status launch_pyramid_batch(const pgm_params* p, int n, const PyrPlan* plans
                 } else {
                     if (C == 1) k_sobel<3, 1><<<g, sblk, 0, st>>>(B, dir_only);
                     else k_sobel<3, 3><<<g, sblk, 0, st>>>(B, dir_only);
+                }
+                if (dir_only == 1) {                   // the sign codes as bit-planes
+                    int mb = 0;
+                    for (int k = 0; k < m; ++k) {
+                        const PyrPlan& pp = plans[base + k];
+                        PyrItem& it = B.it[k];
+                        it.bits = reinterpret_cast<uint32_t*>(pyrs[base + k] + pp.bits_off[s][l]);
+                        it.brow = pp.bit_row[l];
+                        mb = pp.bit_row[l] > mb ? pp.bit_row[l] : mb;
+                    }
+                    k_bits<<<dim3((mb + 31) / 32, (mh + 2 * BORD + 7) / 8, m), dim3(32, 8), 0, st>>>(
+                        B, 2 * C, 2 * px_words(2 * C));
                 }
             }
         if (pgm_status r = launch_status("pyramid: launch"); r != PGM_OK) return r;
