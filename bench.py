@@ -31,7 +31,10 @@ W_IMG, H_IMG = 1024, 436
 PARAMS = dict(levels=5, seed_stride=3, patch_fwd=15, patch_bwd=11, color=1, descriptor=0,
               iters_coarse=4, iters_fine=6, refine_rounds=2, rs_W=2)
 VARIANTS = {"PGM-CD": dict(color=1, descriptor=1), "PGM-G": dict(color=0, descriptor=0),
-            "PGM-GD": dict(color=0, descriptor=1)}
+            "PGM-GD": dict(color=0, descriptor=1),
+            # the checkerboard schedule at the iteration count above level 0
+            # that meets the scan order's accuracy margins on this workload
+            "PGM-C calibrated (iters_coarse 12)": dict(iters_coarse=12)}
 WORKLOAD = ("sintel-like 1024x436 RGB pairs (3-6 layered textured polygons, <=150 px motion), "
             "PGM-C: 6-ch Sobel-5 gradients, Table-2 colour schedule, L=5, seed stride 3, "
             "patch 15/11, iters 4/6, W=2, N=2")
@@ -46,60 +49,88 @@ def parse():
     ap.add_argument("--batch", type=int, default=16, help="pairs per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--cpu-pairs", type=int, default=0, help="oracle sample size (0: one per core)")
+    ap.add_argument("--cpu-pairs", type=int, default=0, help="oracle sample size in pairs (0: the step's pairs)")
     ap.add_argument("--tuning", default="",
                     help="fixed launch knobs 'SLACK,PAIRS' instead of autotuning them")
+    ap.add_argument("--variant", default="", choices=[""] + list(VARIANTS),
+                    help="time this variant's parameters instead of PGM-C (profiling runs)")
+    ap.add_argument("--traffic-record", default="",
+                    help="write the search kernel's DRAM traffic record from this ncu csv "
+                         "(made by bench.TRAFFIC_CMD) and exit")
     ap.add_argument("--serve", type=int, default=300,
                     help="requests of the serving run (Poisson, 200/s); 0 skips it")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------ CPU oracle
+def config_dict(batch, world):
+    """The workload description both arms print (same pairs, same params)."""
+    return {"workload": WORKLOAD, "pairs_per_step": batch, "image": "1024x436x3 uint8",
+            "pair_seeds": "sintel_like_pair seeds 10*rank*B + 0..B-1",
+            "l2": "GPU arm: flushed (256 MB write) before every timed step",
+            "parallelism": "replicas" if world > 1 else "1 GPU"}
+
+
 def _oracle_one(args):
-    seed, prm = args
+    seed, prm, schedule = args
     import oracle as O
     from paper_1704_03217_gb300 import synth
     f1, f2, _ = synth.sintel_like_pair(seed, W_IMG, H_IMG)
     t0 = time.perf_counter()
-    O.run_pair(prm, f1, f2, O.SCHED_CHECKERBOARD, seed)
+    O.run_pair(prm, f1, f2, schedule, seed)
     return time.perf_counter() - t0
 
 
-def oracle_rate(n_pairs, cores, seed0=1000):
-    """Pairs/s of the oracle, one pair per process, `cores` processes."""
+def oracle_rate(seeds, cores, schedule=0, prm=None):
+    """Pairs/s of the oracle on the pairs of `seeds`, one pair per process,
+    `cores` processes (schedule 0: checkerboard, 1: the paper's scan)."""
     from oracle import build as obuild
     obuild.build()
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
         t0 = time.perf_counter()
-        times = pool.map(_oracle_one, [(seed0 + k, PARAMS) for k in range(n_pairs)])
+        times = pool.map(_oracle_one, [(sd, prm or PARAMS, schedule) for sd in seeds])
         wall = time.perf_counter() - t0
     # pair generation runs inside the workers too: charge only the oracle time
     per_proc = max(sum(times[k::cores]) for k in range(cores))
-    return n_pairs / per_proc, per_proc, wall
+    return len(seeds) / per_proc, per_proc, wall
+
+
+def oracle_one_core(seed):
+    """Pairs/s of one process on one pair, in the checkerboard schedule and
+    in the paper's scan order (both run at once, one process each)."""
+    from oracle import build as obuild
+    obuild.build()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(2) as pool:
+        t_cb, t_seq = pool.map(_oracle_one, [(seed, PARAMS, 0), (seed, PARAMS, 1)])
+    return 1.0 / t_cb, 1.0 / t_seq
 
 
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     cores = os.cpu_count() or 1
-    n = a.cpu_pairs or cores
+    seeds = rank_seeds(0, a.batch)
+    procs = min(cores, len(seeds))
     for _ in range(a.warmup):
-        oracle_rate(n, cores)
-    rates, secs = [], []
+        oracle_rate(seeds[:procs], procs)
+    secs = []
     for _ in range(a.steps):
-        r, t, _ = oracle_rate(n, cores)
-        rates.append(r); secs.append(t)
+        _, t, _ = oracle_rate(seeds, procs)
+        secs.append(t)
     total = sum(secs)
-    value = n * a.steps / total
+    value = len(seeds) * a.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "pairs_per_step": n},
-            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-                             "sample": "%d sintel-like pairs per step, one per process" % n},
+            "config": config_dict(a.batch, world),
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": procs, "kind": "oracle",
+                             "sample": "the GPU arm's %d sintel-like pairs per step, one per "
+                                       "process, checkerboard schedule" % len(seeds)},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -107,26 +138,96 @@ def run_reference(a):
 
 
 # ------------------------------------------------------- ncu traffic record
-def pm_traffic_per_launch(pairs, launches):
-    """DRAM bytes per k_pm_t launch: the committed ncu record's bytes over all
-    search launches of one step, scaled to `pairs` per step and divided by
-    this step's `launches`; None when the device code of the search kernel
-    (pm_row.cu above its host-side section) changed since the capture."""
+TRAFFIC_REC = os.path.join(ROOT, "profiles", "k_pm_r_traffic.json")
+PM_SRC = os.path.join(ROOT, "paper_1704_03217_gb300", "csrc", "pm_row.cu")
+DEVICE_MARK = "// Host side: launch configuration.  No device code below this line.\n"
+# the capture the record is made from: DRAM counters of two level-0 search
+# launches (forward and backward of the second iteration's first colour phase)
+# of the first, eager step of an 8-pair run
+TRAFFIC_PAIRS = 8
+TRAFFIC_CMD = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+               "--clock-control none --nvtx --nvtx-include \"pgm_match/level 0/\" "
+               "-k regex:k_pm_r -s 4 -c 2 --csv --log-file gpurun_out/k_pm_r_traffic.csv "
+               "python bench.py --steps 1 --warmup 3 --batch %d --no-cpu-baseline --no-variants "
+               "--serve 0 --tuning 2,32" % TRAFFIC_PAIRS)
+
+
+def device_hash():
     import hashlib
-    rec = os.path.join(ROOT, "profiles", "k_pm_t_traffic.json")
-    src = os.path.join(ROOT, "paper_1704_03217_gb300", "csrc", "pm_row.cu")
-    mark = "// Host side: launch configuration.  No device code below this line.\n"
+    text = open(PM_SRC, encoding="utf-8").read()
+    if DEVICE_MARK not in text:
+        return None
+    return hashlib.sha256(text.split(DEVICE_MARK)[0].encode("utf-8")).hexdigest()
+
+
+def lattice_sizes(prm, w, h):
+    """Seeds per level of a w x h image (stride sigma, offset sigma // 2)."""
+    sig = prm["seed_stride"]
+    c = sig // 2
+    out = []
+    for _ in range(prm["levels"]):
+        out.append(((w - 1 - c) // sig + 1) * ((h - 1 - c) // sig + 1))
+        w, h = (w + 1) // 2, (h + 1) // 2
+    return out
+
+
+def search_units(prm, w, h, pairs):
+    """Seed-iterations of the search per step: every iteration of a visit at
+    level l covers each of the n_l seeds of both directions once."""
+    n = lattice_sizes(prm, w, h)
+    return pairs * sum(2 * n[l] * (prm["iters_fine"] if l == 0 else prm["iters_coarse"])
+                       for l in visit_levels(prm["levels"], prm.get("refine_rounds", 2)))
+
+
+def write_traffic_record(csv_path):
+    """profiles/k_pm_r_traffic.json from the capture TRAFFIC_CMD wrote."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    start = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[start]
+    ii, ki, mi, vi = (hdr.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Value"))
+    units_of = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9,
+                "ns": 1e-3, "nsecond": 1e-3, "us": 1, "usecond": 1, "ms": 1e3, "msecond": 1e3}
+    ui = hdr.index("Metric Unit")
+    per = {}
+    for r in rows[start + 1:]:
+        if len(r) <= vi or "k_pm_r" not in r[ki]:
+            continue
+        v = float(r[vi].replace(",", "")) * units_of.get(r[ui], 1)
+        per.setdefault(r[ii], {})[r[mi]] = v
+    launches = len(per)
+    rd = sum(x["dram__bytes_read.sum"] for x in per.values())
+    wr = sum(x["dram__bytes_write.sum"] for x in per.values())
+    us = sum(x["gpu__time_duration.sum"] for x in per.values())
+    n0 = lattice_sizes(PARAMS, W_IMG, H_IMG)[0]
+    units = launches * TRAFFIC_PAIRS * n0 / 2          # one colour of one direction each
+    rec = {"kernel": "k_pm_r", "workload": WORKLOAD, "pairs": TRAFFIC_PAIRS, "level": 0,
+           "launches": launches, "dram_read_bytes": rd, "dram_write_bytes": wr,
+           "ncu_time_us": us, "seed_units": units, "bytes_per_seed_unit": (rd + wr) / units,
+           "command": TRAFFIC_CMD,
+           "note": "DRAM bytes of level-0 search launches per seed and iteration; bench.py "
+                   "multiplies by its seed-iterations per step (all levels) and divides by its "
+                   "search launches per step (coarse levels assumed to move as many bytes per "
+                   "seed as level 0, an upper bound: their data sit in L2)",
+           "device_sha256": device_hash(),
+           "hash_note": "sha256 of pm_row.cu above the line " + json.dumps(DEVICE_MARK.strip())}
+    with open(TRAFFIC_REC, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    return rec
+
+
+def pm_traffic_per_launch(units, launches):
+    """DRAM bytes per search launch: the committed record's bytes per seed
+    unit times this step's `units` over its `launches`; None when the device
+    code of the search kernel changed since the capture."""
     try:
-        r = json.load(open(rec))
-        text = open(src, encoding="utf-8").read()
+        r = json.load(open(TRAFFIC_REC))
     except (OSError, ValueError):
         return None
-    if mark not in text:
+    if r.get("device_sha256") != device_hash() or launches <= 0:
         return None
-    h = hashlib.sha256(text.split(mark)[0].encode("utf-8")).hexdigest()
-    if r.get("pm_tile_device_sha256") != h or "dram_bytes_per_step" not in r or launches <= 0:
-        return None
-    return r["dram_bytes_per_step"] * pairs / r["pairs"] / launches
+    return r["bytes_per_seed_unit"] * units / launches
 
 
 # ------------------------------------------------- HBM-bound stages (a1-a3, a7-a9)
@@ -255,11 +356,16 @@ def run_ours(a):
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         # the oracle leg runs first, before this process touches the GPU
         cores = os.cpu_count() or 1
-        n = a.cpu_pairs or cores
-        r, t, _ = oracle_rate(n, cores)
-        cpu = {"value": r, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-               "sample": "%d sintel-like 1024x436 PGM-C pairs, one per process, %.1f s of "
-                         "oracle time per process" % (n, t)}
+        seeds = rank_seeds(0, a.cpu_pairs or a.batch)
+        procs = min(cores, len(seeds))
+        r, t, _ = oracle_rate(seeds, procs)
+        one_cb, one_seq = oracle_one_core(seeds[0])
+        cpu = {"value": r, "unit": "pairs/s", "cores": procs, "kind": "oracle",
+               "sample": "the timed step's %d sintel-like 1024x436 PGM-C pairs, one per "
+                         "process, %.1f s of oracle time per process" % (len(seeds), t),
+               "one_core_pairs_per_s": one_cb, "one_core_scan_order_pairs_per_s": one_seq,
+               "one_core_sample": "pair seed %d on one process, checkerboard schedule and the "
+                                  "paper's scan order" % seeds[0]}
 
     from paper_1704_03217_gb300 import build as pbuild
     pbuild.build()
@@ -270,7 +376,8 @@ def run_ours(a):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     B = a.batch
-    prm = api.Params(**PARAMS)
+    P = dict(PARAMS, **VARIANTS.get(a.variant, {}))
+    prm = api.Params(**P)
     pairs = [synth.sintel_like_pair(sd, W_IMG, H_IMG) for sd in rank_seeds(rank, B)]
     imgs1 = [torch.from_numpy(p[0]).to(dev) for p in pairs]
     imgs2 = [torch.from_numpy(p[1]).to(dev) for p in pairs]
@@ -376,11 +483,12 @@ def run_ours(a):
     d2h = out_rows[0].numel() * 4 + out_cnt[0].numel() * 4
     e2e = world * B * e2e_steps / max_over_ranks(e2e_t, world, dev)
 
-    # -------- per-kernel times (profiling pass, not the timed one)
+    # -------- per-kernel times (profiling pass: eager launches, each kernel
+    # class bracketed by events, both directions on one stream)
     import ctypes as C
     L.pgm_profile_enable(1)
     prof_steps = 2
-    for _ in range(prof_steps):                 # eager launches: events bracket each kernel
+    for _ in range(prof_steps):
         flush.fill_(1)
         m.enqueue(imgs1, imgs2, sids)
     torch.cuda.synchronize()
@@ -391,11 +499,20 @@ def run_ours(a):
     kernel_ms = {name: kms[i] / prof_steps for i, name in enumerate(_lib.K_CLASSES)}
     kernel_launches = {name: kn[i] // prof_steps for i, name in enumerate(_lib.K_CLASSES)}
     ev_counts = [w.evals() for w in m.ws]
-    nch = 6
-    el_pm = sum(e["pm"][0] * PARAMS["patch_fwd"] ** 2 * nch + e["pm"][1] * PARAMS["patch_bwd"] ** 2 * nch
+    nch = 6 if P["color"] == 1 else 2
+    el_pm = sum(e["pm"][0] * P["patch_fwd"] ** 2 * nch + e["pm"][1] * P["patch_bwd"] ** 2 * nch
                 for e in ev_counts)                     # per step
+    evals_step = {"pm": sum(sum(e["pm"]) for e in ev_counts),
+                  "cost": sum(sum(e["cost"]) for e in ev_counts),
+                  "init": sum(sum(e["init"]) for e in ev_counts),
+                  "pm_global": sum(sum(e["pm_global"]) for e in ev_counts)}
     pm_launch_ms = kernel_ms["pm"] / max(1, kernel_launches["pm"])
-    hb = hbm_stage_bytes(PARAMS, W_IMG, H_IMG, B, sum(counts))
+    # the search's share of the timed (graph, overlapped) step: its share of
+    # the serial kernel time applied to the timed step time
+    serial_ms = sum(kernel_ms.values())
+    pm_share = kernel_ms["pm"] / serial_ms if serial_ms > 0 else 0.0
+    pm_step_ms = pm_share * ms_max / a.steps
+    hb = hbm_stage_bytes(P, W_IMG, H_IMG, B, sum(counts))
     hpeak, hsrc = measured_hbm_peak()
     hbm_stages = {"peak_GBps": hpeak, "peak_source": hsrc + " (copy bandwidth)",
                   "note": "compulsory bytes per step over the stage's kernel time from the "
@@ -414,7 +531,9 @@ def run_ours(a):
     achieved_tmac = el_per_launch / (pm_launch_ms * 1e-3) / 1e12
     l1_gbs = 2 * el_per_launch / (pm_launch_ms * 1e-3) / 1e9
     l1_peak = sms * 128 * sm_mhz * 1e6 / 1e9
-    traffic = pm_traffic_per_launch(B, kernel_launches["pm"])
+    traffic = (pm_traffic_per_launch(search_units(P, W_IMG, H_IMG, B), kernel_launches["pm"])
+               if not a.variant else None)
+    overlap_tmac = el_pm / (pm_step_ms * 1e-3) / 1e12 if pm_step_ms > 0 else 0.0
 
     variants = {}
     if not a.no_variants:
@@ -438,6 +557,12 @@ def run_ours(a):
                               "gcand_evals_per_s": api.nominal_evals(pv, W_IMG, H_IMG, W_IMG, H_IMG)
                               * B * max(3, a.steps // 4) / (tot * 1e-3) / 1e9}
             del mv
+        variants["note"] = ("pairs/s of the same 16 pairs, whole step graph-replayed; "
+                            "gcand_evals_per_s nominal")
+
+    workloads = None
+    if not a.no_variants and rank == 0:
+        workloads = run_workloads(api, prm, dev, flush, a.steps)
 
     batched = None
     if not a.no_variants and rank == 0:
@@ -448,23 +573,30 @@ def run_ours(a):
         serving = run_serving(api, prm, a.serve, dev)
 
     if rank == 0:
+        cfg = config_dict(B, world)
+        if a.variant:
+            cfg["variant"] = dict(VARIANTS[a.variant], name=a.variant)
         line = {
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "pairs_per_step": B, "image": "1024x436x3 uint8",
-                       "l2": "flushed (256 MB write) before every timed step",
-                       "launch": "whole step captured once as a CUDA graph, replayed",
-                       "tuning": {"window_slack": tuned[0], "pairs_per_launch": tuned[1]},
-                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "config": cfg,
+            "launch": {"form": "whole step captured once as a CUDA graph, replayed",
+                       "tuning": {"window_slack": tuned[0], "pairs_per_launch": tuned[1]}},
             "gcand_evals_per_s": nominal * value / 1e9,
+            "gcand_evals_per_s_evaluated": (evals_step["pm"] + evals_step["cost"])
+            * a.steps / (ms_max * 1e-3) / 1e9,
+            "evals_note": "gcand_evals_per_s: nominal evaluations (every candidate of the "
+                          "method's schedule) x pairs/s; _evaluated: candidates the kernels "
+                          "scored (search + cost refresh), the rest being duplicates or "
+                          "outside the image, skipped without changing a result",
             "nominal_evals_per_pair": nominal,
             "matches_per_pair": sum(counts) / len(counts),
             "e2e": {"value": e2e, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "kernel": "k_pm_t (propagation + limited random search)",
+            "roofline": {"bound": "alu", "kernel": "k_pm_r (propagation + limited random search)",
                          "achieved": achieved_tmac, "peak": peak_tmac,
                          "unit": "Tmac/s (int16 x int16 element multiply-accumulates)",
                          "frac": achieved_tmac / peak_tmac, "traffic": traffic,
@@ -472,14 +604,18 @@ def run_ours(a):
                                         % (sms, sm_mhz),
                          "l1_GBps": l1_gbs, "l1_peak_GBps": l1_peak, "l1_frac": l1_gbs / l1_peak,
                          "pm_ms_per_launch": pm_launch_ms,
-                         "pm_launches_per_step": kernel_launches["pm"]},
+                         "pm_launches_per_step": kernel_launches["pm"],
+                         "pm_share_of_serial_kernel_time": pm_share,
+                         "pm_ms_in_timed_step": pm_step_ms,
+                         "frac_overlap_credited": overlap_tmac / peak_tmac,
+                         "note": "achieved from per-launch event times of the profiling pass "
+                                 "(directions serial); frac_overlap_credited divides by the "
+                                 "search's share of the timed, overlapped step instead"},
             "hbm_stages": hbm_stages,
             "kernel_ms_per_step": kernel_ms, "kernel_launches_per_step": kernel_launches,
-            "evals_per_step": {"pm": sum(sum(e["pm"]) for e in ev_counts),
-                               "cost": sum(sum(e["cost"]) for e in ev_counts),
-                               "init": sum(sum(e["init"]) for e in ev_counts),
-                               "pm_global": sum(sum(e["pm_global"]) for e in ev_counts)},
+            "evals_per_step": evals_step,
             "variants": variants,
+            "workloads": workloads,
             "batched": batched,
             "serving": serving,
             "clocks": clk,
@@ -489,6 +625,84 @@ def run_ours(a):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+# the other two single-pair workloads: method parameters as the oracle's
+# accuracy margins use them (Sec. IV defaults where the workload fixes none)
+C1_PARAMS = dict(levels=3, seed_stride=3, patch_fwd=8, patch_bwd=8, color=0, descriptor=0,
+                 iters_coarse=6, iters_fine=6, refine_rounds=2, rs_W=2)
+C3_PARAMS = dict(PARAMS)
+
+
+def _replay_rate(mv, flush, stream, reps, pairs):
+    """Pairs/s of a captured matcher: `reps` replays, L2 flushed before each."""
+    import torch
+    for _ in range(2):
+        mv.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for k in range(reps):
+        flush.fill_(k)
+        e0.record(stream)
+        mv.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return pairs * reps / (tot * 1e-3), tot / reps
+
+
+def run_workloads(api, prm, dev, flush, steps):
+    """Throughput lines of the 256x192 gray noise-affine pair and the KITTI-
+    shaped 1242x375 RGB pair, from resident device images, each whole batch
+    captured as one CUDA graph; the gray pair also one pair per replay (the
+    plain single-pair form)."""
+    import torch
+    from paper_1704_03217_gb300 import synth
+    stream = torch.cuda.current_stream(dev)
+    reps = max(3, steps // 4)
+    out = {}
+    # c1: 64 pairs per step, and one pair per graph replay
+    pc1 = api.Params(**C1_PARAMS)
+    pairs = [synth.config_pair("c1", sd) for sd in range(64)]
+    i1 = [torch.from_numpy(p[0]).to(dev) for p in pairs]
+    i2 = [torch.from_numpy(p[1]).to(dev) for p in pairs]
+    mv = api.PairMatcher(pc1, 256, 192, batch=64, device=dev)
+    mv.capture(i1, i2, list(range(64)))
+    rate, ms = _replay_rate(mv, flush, stream, reps, 64)
+    ms1 = api.PairMatcher(pc1, 256, 192, batch=1, device=dev)
+    a1, a2 = i1[0].clone(), i2[0].clone()
+    ms1.capture([a1], [a2], [0])
+    ms1.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(64):
+        a1.copy_(i1[k]); a2.copy_(i2[k])
+        ms1.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["c1 256x192 gray noise-affine"] = {
+        "params": C1_PARAMS, "pairs_per_step": 64, "ms_per_step": ms, "pairs_per_s": rate,
+        "single_pair_pairs_per_s": 64 / (e0.elapsed_time(e1) * 1e-3),
+        "gcand_evals_per_s": api.nominal_evals(pc1, 256, 192, 256, 192) * rate / 1e9}
+    del mv, ms1
+    # c3: 16 KITTI-shaped pairs, full-gradient and direction-only descriptors
+    pairs = [synth.config_pair("c3", sd) for sd in range(16)]
+    i1 = [torch.from_numpy(p[0]).to(dev) for p in pairs]
+    i2 = [torch.from_numpy(p[1]).to(dev) for p in pairs]
+    for name, kw in (("PGM-C", {}), ("PGM-CD", dict(descriptor=1))):
+        pv = api.Params(**dict(C3_PARAMS, **kw))
+        mv = api.PairMatcher(pv, 1242, 375, batch=16, device=dev)
+        mv.capture(i1, i2, list(range(16)))
+        rate, ms = _replay_rate(mv, flush, stream, reps, 16)
+        out["c3 1242x375 RGB kitti-like " + name] = {
+            "params": dict(C3_PARAMS, **kw), "pairs_per_step": 16, "ms_per_step": ms,
+            "pairs_per_s": rate,
+            "gcand_evals_per_s": api.nominal_evals(pv, 1242, 375, 1242, 375) * rate / 1e9}
+        del mv
+    out["note"] = "L2 flushed before every timed replay; gcand_evals_per_s nominal"
+    return out
 
 
 def run_batched(api, prm, dev, n=64, reps=3):
@@ -560,32 +774,45 @@ def run_batched(api, prm, dev, n=64, reps=3):
 
 def run_serving(api, prm, n, dev):
     """Continuous batching of Poisson arrivals (mean 200 pairs/s) of pairs of
-    640x480, 1280x720, 1920x1080 and 1024x436 under a 40 GB budget, next to
-    the plain form (one pair per launch, one at a time) on the same requests."""
+    640x480, 1280x720, 1920x1080 and 1024x436 (8 distinct pairs per size)
+    under a 40 GB budget, next to the plain form (one pair per launch, one at
+    a time) on the same requests; and the continuous form again under a
+    budget of three 1920x1080 requests, where admission waits for memory."""
     import torch
     from paper_1704_03217_gb300 import serve
     out = {"offered_pairs_per_s": 200.0, "budget_gb": 40, "requests": n,
-           "sizes": ["640x480", "1280x720", "1920x1080", "1024x436"]}
-    for name, max_batch, streams in (("continuous", 16, 3), ("plain", 1, 1)):
-        reqs = serve.poisson_requests(7, 200.0, n, pool=1)
+           "sizes": ["640x480", "1280x720", "1920x1080", "1024x436"], "distinct_pairs": 32}
+    reqs0 = serve.poisson_requests(7, 200.0, n, pool=8)
+    warm = serve.poisson_requests(8, 1e6, 4, pool=1)              # warm-up, not measured
+    big = None
+    for name, max_batch, streams, budget in (("continuous", 16, 3, 40 << 30), ("plain", 1, 1, 40 << 30),
+                                             ("continuous, budget-bound", 16, 3, None)):
+        reqs = [serve.Request(r.rid, r.arrival, r.img1, r.img2, stream_id=r.stream_id) for r in reqs0]
         ex = serve.GpuExecutor(prm, streams=streams, device=dev)
-        warm = serve.poisson_requests(8, 1e6, 4, pool=1)          # warm-up, not measured
-        serve.serve(warm, serve.Scheduler(40 << 30, max_batch, ex.bytes_of), ex)
+        if budget is None:
+            big = max(ex.bytes_of(r) for r in reqs)
+            budget = 3 * big
+        serve.serve(warm, serve.Scheduler(budget, max_batch, ex.bytes_of), ex)
         torch.cuda.synchronize()
-        sch = serve.Scheduler(40 << 30, max_batch, ex.bytes_of)
+        sch = serve.Scheduler(budget, max_batch, ex.bytes_of)
         t0 = time.perf_counter()
         done = serve.serve(reqs, sch, ex)
         wall = time.perf_counter() - t0
         r = serve.summary(done, wall)
         r["max_batch"], r["streams"] = max_batch, streams
+        r["budget_gb"] = budget / 2 ** 30
         r["peak_budget_gb"] = sch.peak / 2 ** 30
         out[name] = r
+        del ex
     out["p50_ms"], out["p99_ms"] = out["continuous"]["p50_ms"], out["continuous"]["p99_ms"]
     return out
 
 
 def main():
     a = parse()
+    if a.traffic_record:
+        print(json.dumps(write_traffic_record(a.traffic_record)))
+        return 0
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)

@@ -349,7 +349,8 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
     // reference patches.  The coarsest level's come first on the caller's
     // stream; the finer levels' are forked onto an auxiliary stream, where
     // they overlap the initialisation and the coarse visits, and each is
-    // joined back before the first visit at its level.
+    // joined back before the first visit at its level (the kernel time
+    // profile keeps them on the caller's stream).
     bool joined[MAXL];
     for (int l = 0; l < MAXL; ++l) joined[l] = true;
     Aux* aux = nullptr;
@@ -360,7 +361,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
         const int l0 = sch.level[0];
         for (int l = p->levels - 1; l >= 0; --l) {
             if (!needed[l]) continue;
-            if (l != l0 && !aux_tried) {
+            if (l != l0 && !aux_tried && !g_prof.on) {
                 aux_tried = true;
                 pgm_status r = aux_get(st, &aux);
                 if (r != PGM_OK) return r;
@@ -392,6 +393,9 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
     }
     for (int v = 0; v < sch.n; ++v) {
         const int l = sch.level[v];
+        char rname[16];
+        snprintf(rname, sizeof(rname), "level %d", l);
+        Range visit_range(rname);
         if (!joined[l]) {
             PGM_TRY(cudaStreamWaitEvent(st, aux->lvl[l], 0), "match: join box sums");
             joined[l] = true;
@@ -548,6 +552,7 @@ pgm_status pgm_build_pyramid(const pgm_params* p, const uint8_t* d_img, int w, i
     if (!make_pyr_plan(p, w, h, &pp)) return PGM_ERR_ARG;
     if (pyr_bytes < pp.bytes) return PGM_ERR_WORKSPACE;
     uint8_t* pyr = static_cast<uint8_t*>(d_pyr);
+    Range range("pgm_build_pyramid");
     return launch_pyramid_batch(p, 1, &pp, &d_img, &c, &pitch, &pyr,
                                 static_cast<cudaStream_t>(stream));
 }
@@ -576,6 +581,7 @@ pgm_status pgm_build_pyramid_batch(const pgm_params* p, int n, const uint8_t* co
             if (pyr_bytes[i] < plans[k].bytes) return PGM_ERR_WORKSPACE;
         }
     }
+    Range range("pgm_build_pyramid");
     for (int base = 0; base < n; base += PYR_MAXB) {
         const int m = n - base < PYR_MAXB ? n - base : PYR_MAXB;
         for (int k = 0; k < m; ++k) {
@@ -631,6 +637,7 @@ pgm_status pgm_match(const pgm_params* p, const void* d_pyr1, const void* d_pyr2
     static thread_local PairCtx c;
     r = prepare_pair(p, d_pyr1, d_pyr2, w1, h1, w2, h2, stream_id, d_ws, ws_bytes, &c);
     if (r != PGM_OK) return r;
+    Range range("pgm_match");
     return run_batch(p, &c, 1, static_cast<cudaStream_t>(stream));
 }
 
@@ -654,6 +661,7 @@ pgm_status pgm_match_batch(const pgm_params* p, int n, const void* const* d_pyr1
             if (r != PGM_OK) return r;
         }
     }
+    Range range("pgm_match");
     for (int base = 0; base < n; base += chunk) {
         int m = n - base < chunk ? n - base : chunk;
         for (int k = 0; k < m; ++k) {
@@ -690,6 +698,7 @@ pgm_status pgm_filter(const pgm_params* p, int w1, int h1, int w2, int h2, void*
     WsPlan wp;
     if (!make_ws_plan(p, w1, h1, w2, h2, &wp)) return PGM_ERR_ARG;
     if (ws_bytes < wp.bytes) return PGM_ERR_WORKSPACE;
+    Range range("pgm_filter");
     return launch_filter(p, wp, static_cast<uint8_t*>(d_ws), d_matches, max_matches, d_count,
                          d_keep, static_cast<cudaStream_t>(stream));
 }
@@ -713,6 +722,7 @@ pgm_status pgm_filter_batch(const pgm_params* p, int n, const int32_t* dims, voi
         if (ws_bytes[i] < wp.bytes) return PGM_ERR_WORKSPACE;
     }
     filter_consts(p, &F);
+    Range range("pgm_filter");
     for (int base = 0; base < n; base += MAXB) {
         const int m = n - base < MAXB ? n - base : MAXB;
         F.n = m;

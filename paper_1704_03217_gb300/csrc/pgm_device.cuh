@@ -2,6 +2,7 @@
 // units of libpgm (host plans, kernel argument blocks, launchers).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -161,6 +162,17 @@ struct MatchConst {              // scalars common to one launch
 // result-invariant tuning knobs (pgm_set_tuning)
 struct Tuning { int slack; int chunk; };
 Tuning tuning();
+
+// A host-side NVTX push/pop range: names the entry point and, inside
+// pgm_match, the visit's level on a profiler's timeline (and lets a profiler
+// select the kernels of one level).  Costs a pointer test when no tool is
+// attached.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 // Brackets the launches of one kernel class: counts them and, while
 // pgm_profile_enable(1) is on for this thread, records an event pair.

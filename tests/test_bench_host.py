@@ -46,3 +46,21 @@ def test_pyramid_bytes_match_the_abi_layout():
     want = 2 * pairs * (3 * w * h + 2 * desc)              # + the split copy, + the input
     got = bench.hbm_stage_bytes(bench.PARAMS, w, h, pairs, 0)["pyramid"]
     assert got == want
+
+
+def test_lattice_sizes_match_the_abi_field_layout():
+    """The seed counts bench.py scales the traffic record with are the
+    lattice sizes of the C ABI's field layout at every level."""
+    from paper_1704_03217_gb300 import api, build, _lib
+    build.build()
+    L = _lib.load()
+    for w, h in ((1024, 436), (1242, 375), (257, 193)):
+        prm = api.Params(**bench.PARAMS)
+        cp = prm.cstruct()
+        n = bench.lattice_sizes(bench.PARAMS, w, h)
+        for level in range(bench.PARAMS["levels"]):
+            nx, ny = C.c_int(), C.c_int()
+            o1, o2, o3 = C.c_size_t(), C.c_size_t(), C.c_size_t()
+            assert L.pgm_field_layout(C.byref(cp), w, h, w, h, level, 0, C.byref(nx), C.byref(ny),
+                                      C.byref(o1), C.byref(o2), C.byref(o3)) == 0
+            assert n[level] == nx.value * ny.value
