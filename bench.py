@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-pairs", type=int, default=0, help="oracle sample size in pairs (0: the step's pairs)")
     ap.add_argument("--tuning", default="",
-                    help="fixed launch knobs 'SLACK,PAIRS' instead of autotuning them")
+                    help="fixed launch knobs 'SLACK,PAIRS[,TILE_W]' instead of autotuning them")
     ap.add_argument("--variant", default="", choices=[""] + list(VARIANTS),
                     help="time this variant's parameters instead of PGM-C (profiling runs)")
     ap.add_argument("--traffic-record", default="",
@@ -390,10 +390,11 @@ def run_ours(a):
     # step is captured once as a CUDA graph and replayed
     from paper_1704_03217_gb300 import tune
     if a.tuning:
-        tuned = tuple(int(x) for x in a.tuning.split(","))
-        tune.set(*tuned)
+        tune.set(*(int(x) for x in a.tuning.split(",")))
+        tuned = tune.get()
     else:
-        tuned, _ = tune.autotune(m, imgs1, imgs2, reps=2, slacks=(2, 4, 6), chunks=(16, 32))
+        tuned, _ = tune.autotune(m, imgs1, imgs2, reps=2, slacks=(2, 4, 6), chunks=(16, 32),
+                                 tiles=(4, 8, 16))
     per_step_launches = m.capture(imgs1, imgs2, sids)
 
     def step():
@@ -583,7 +584,8 @@ def run_ours(a):
             "dtype": "int32", "data": "synthetic",
             "config": cfg,
             "launch": {"form": "whole step captured once as a CUDA graph, replayed",
-                       "tuning": {"window_slack": tuned[0], "pairs_per_launch": tuned[1]}},
+                       "tuning": {"window_slack": tuned[0], "pairs_per_launch": tuned[1],
+                                  "tile_w": tuned[2]}},
             "gcand_evals_per_s": nominal * value / 1e9,
             "gcand_evals_per_s_evaluated": (evals_step["pm"] + evals_step["cost"])
             * a.steps / (ms_max * 1e-3) / 1e9,
@@ -712,16 +714,19 @@ def run_batched(api, prm, dev, n=64, reps=3):
     pairs, batched filter) captured once as a CUDA graph and replayed, and
     (b) in the plain form: each pair's two pyramids, its match and its filter
     launched one pair after the other.  Pairs/s from CUDA events over `reps`
-    runs each; both forms must export the same matches."""
+    runs each; both forms must export the same matches.  The per-level
+    iteration schedule of the shared form is then autotuned on the batch
+    (tune.tune_schedule: fastest schedule whose accuracy against the pairs'
+    ground truth stays within tune.MARGINS of the paper's schedule)."""
     import numpy as np
     import torch
-    from paper_1704_03217_gb300 import synth
+    from paper_1704_03217_gb300 import evaluate, synth, tune
     rng = np.random.default_rng(77)
     pairs = []
     for _ in range(n):                       # RGB pairs for the colour descriptor
         w, h = synth.BATCH_SIZES[int(rng.integers(len(synth.BATCH_SIZES)))]
         pairs.append(synth.sintel_like_pair(int(rng.integers(1 << 30)), w, h,
-                                            t_max=min(150.0, w / 8))[:2])
+                                            t_max=min(150.0, w / 8)))
     i1 = [torch.from_numpy(np.ascontiguousarray(p[0])).to(dev) for p in pairs]
     i2 = [torch.from_numpy(np.ascontiguousarray(p[1])).to(dev) for p in pairs]
     P1 = [api.Pyramid(prm, x.shape[1], x.shape[0], dev) for x in i1]
@@ -732,17 +737,17 @@ def run_batched(api, prm, dev, n=64, reps=3):
     cnt = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(n)]
     sids = list(range(n))
 
-    def shared():
-        api.build_pyramids(prm, i1 + i2, P1 + P2)
-        api.match_batch(prm, P1, P2, sids, W)
-        api.filter_batch(prm, W, rows, cnt)
+    def shared(p):
+        api.build_pyramids(p, i1 + i2, P1 + P2)
+        api.match_batch(p, P1, P2, sids, W)
+        api.filter_batch(p, W, rows, cnt)
 
-    def plain():
+    def plain(p):
         for k in range(n):
             P1[k].build(i1[k])
             P2[k].build(i2[k])
-            api.match(prm, P1[k], P2[k], sids[k], W[k])
-            api.filter_into(prm, W[k], rows[k], cnt[k])
+            api.match(p, P1[k], P2[k], sids[k], W[k])
+            api.filter_into(p, W[k], rows[k], cnt[k])
 
     def timed(fn):
         fn()
@@ -755,21 +760,44 @@ def run_batched(api, prm, dev, n=64, reps=3):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    shared()
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        shared()
-    t_shared = timed(graph.replay)
+    def graph_ms(p):
+        shared(p)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            shared(p)
+        return timed(g.replay)
+
+    def accuracy(p):
+        shared(p)
+        torch.cuda.synchronize()
+        acc = [evaluate.match_accuracy(rows[k][:int(cnt[k].item())].cpu().numpy(), pairs[k][2],
+                                       caps[k]) for k in range(n)]
+        return {m: float(np.mean([a[m] for a in acc])) for m in ("epe", "outliers_3px", "density")}
+
+    t_shared = graph_ms(prm)
     got_shared = [int(c.item()) for c in cnt]
-    t_plain = timed(plain)
+    t_plain = timed(lambda: plain(prm))
     got_plain = [int(c.item()) for c in cnt]
     assert got_shared == got_plain, "batched and single-pair matches differ"
+    best, table = tune.tune_schedule(prm, graph_ms, accuracy)
     sizes = sorted({"%dx%d" % (p[0].shape[1], p[0].shape[0]) for p in pairs})
+    ref = tuple(tune.SCHEDULES_L5[0])
     return {"pairs": n, "sizes": sizes, "data": "synthetic Sintel-like RGB pairs",
             "batched_ms": t_shared, "batched_pairs_per_s": n / (t_shared * 1e-3),
             "plain_ms": t_plain, "plain_pairs_per_s": n / (t_plain * 1e-3),
-            "speedup": t_plain / t_shared}
+            "speedup": t_plain / t_shared,
+            "schedule_tuning": {
+                "paper_schedule": list(ref), "tuned_schedule": list(best),
+                "margins": tune.MARGINS,
+                "tuned_batched_pairs_per_s": n / (table[best]["ms"] * 1e-3),
+                "tuned_speedup_vs_plain": t_plain / table[best]["ms"],
+                "accuracy_paper": {k: table[ref][k] for k in ("epe", "outliers_3px", "density")},
+                "accuracy_tuned": {k: table[best][k] for k in ("epe", "outliers_3px", "density")},
+                "table": [dict(schedule=list(sch), **r) for sch, r in table.items()],
+                "note": "levels listed from 0 (full resolution); accuracy of the exported "
+                        "matches against the generator's flow; every schedule is bit-exact "
+                        "with the oracle run at the same counts"}}
 
 
 def run_serving(api, prm, n, dev):

@@ -94,6 +94,9 @@ typedef struct {
                               level 0 only at seeds whose pixel x and y are
                               both == g/2 (mod g) (PGM-C3/G3: g = 3)       */
     uint64_t philox_key;   /* key of the random-search stream              */
+    int32_t iters_level[12]; /* per-level iteration counts: entry l >= 0
+                              replaces iters_coarse / iters_fine at level l;
+                              -1 (the default) keeps them; at most 32767   */
 } pgm_params;
 
 /* Fill *p with the defaults above.  Never fails for a non-NULL p. */
@@ -316,10 +319,14 @@ pgm_status pgm_profile_read(double* ms, int64_t* launches);
  *                 around a tile's median match (default 2); candidates
  *                 outside it are scored from global memory.
  *   pairs_per_launch: pairs sharing one launch in pgm_match_batch (1..32,
- *                 default 32). */
+ *                 default 32).
+ *   tile_w:       seeds per row of a search tile: 4, 8 (default) or 16; a
+ *                 tile holds 64 lattice seeds (tile_w x 64 / tile_w) and
+ *                 stages one shared-memory window. */
 typedef struct {
     int32_t window_slack;
     int32_t pairs_per_launch;
+    int32_t tile_w;
 } pgm_tuning;
 /* NULL restores the defaults.  Errors: PGM_ERR_ARG (value out of range). */
 pgm_status pgm_set_tuning(const pgm_tuning* t);
@@ -339,6 +346,48 @@ pgm_status pgm_set_wait_limit(int64_t cycles);
  * random-search candidates per seed and iteration, one cost per seed and
  * visit, both directions; the exhaustive init is not counted). */
 int64_t pgm_nominal_evals(const pgm_params* p, int w1, int h1, int w2, int h2);
+
+/* ---- sparse-to-dense interpolation (Sec. III-G) ---------------------------
+ * The paper densifies its grid-3 matches with EpicFlow: an edge-aware
+ * geodesic distance, then a Nadaraya-Watson (NW) average or a locally
+ * weighted affine (LA) fit over a pixel's nearest matches, LA when the
+ * matches exceed 2.2 % of the image size.  Here every pixel of image 1 takes
+ * its k geodesically nearest matches, the geodesic step between 4-neighbours
+ * p, q costing c(p) + c(q) with c = 1 + (sum of |g| over the level-0
+ * descriptor channels of image 1) >> cost_shift, ties of distance going to
+ * the smaller match index; weights exp(-(d - d_nearest) / lambda); LA falls
+ * back to NW where its normal equations are degenerate.  The distances and
+ * neighbour lists are exact integers; the interpolation runs in double
+ * precision and is stored as float. */
+enum { PGM_INTERP_AUTO = 0, PGM_INTERP_NW = 1, PGM_INTERP_LA = 2 };
+typedef struct {
+    int32_t k;             /* neighbours per pixel, 1..16 (default 16)      */
+    int32_t mode;          /* PGM_INTERP_AUTO: LA iff n * 10^4 >
+                              la_permyriad * w * h (n = matches), else NW;
+                              PGM_INTERP_NW / PGM_INTERP_LA force one      */
+    int32_t cost_shift;    /* 0..31 (default 10)                           */
+    int32_t la_permyriad;  /* default 220 (2.2 %)                          */
+    double lambda;         /* > 0, distance scale of the weights (32)      */
+} pgm_interp_params;
+void pgm_interp_default_params(pgm_interp_params* ip);
+/* Workspace bytes for a w x h image (0: invalid size or k). */
+size_t pgm_interp_workspace_bytes(int w, int h, const pgm_interp_params* ip);
+/* Dense flow of image 1 (w x h, the size d_pyr1 was built for under p) from
+ * the exported matches: d_matches [max_matches][4] int32 (x1, y1, x2, y2),
+ * *d_count of them valid (the count pgm_filter wrote; at most max_matches
+ * are read; match positions outside the image are ignored, two at one pixel
+ * keep the first).  d_flow: [h][w][2] float (x, y displacement; 0 where no
+ * match is reachable).  d_ws: pgm_interp_workspace_bytes, 256-byte aligned;
+ * it holds, at offset 0, the k nearest matches of every pixel as
+ * [h][w][k] uint64 keys d << 32 | index in ascending order (all ones where
+ * fewer are reachable).  The call synchronises the stream (the relaxation
+ * repeats until nothing changes), so it cannot be captured in a graph.
+ * Errors: PGM_ERR_ARG, PGM_ERR_WORKSPACE, PGM_ERR_CUDA, PGM_ERR_UNSUPPORTED
+ * (the relaxation did not settle within its launch bound). */
+pgm_status pgm_interpolate(const pgm_params* p, const void* d_pyr1, int w, int h,
+                           const int32_t* d_matches, const int32_t* d_count, int64_t max_matches,
+                           const pgm_interp_params* ip, void* d_ws, size_t ws_bytes,
+                           float* d_flow, void* stream);
 
 #ifdef __cplusplus
 }

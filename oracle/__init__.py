@@ -28,7 +28,8 @@ FIELDS = [
 
 
 class _Params(C.Structure):
-    _fields_ = [(n, C.c_int32) for n, _ in FIELDS] + [("philox_key", C.c_uint64)]
+    _fields_ = ([(n, C.c_int32) for n, _ in FIELDS] + [("philox_key", C.c_uint64)]
+                + [("iters_level", C.c_int32 * 12)])
 
 
 def make_params(d=None) -> _Params:
@@ -37,6 +38,11 @@ def make_params(d=None) -> _Params:
     for n, default in FIELDS:
         setattr(p, n, int(d.pop(n, default)))
     p.philox_key = int(d.pop("philox_key", 0x5EED5EED1234ABCD))
+    lv = list(d.pop("iters_level", ()))
+    if len(lv) > 12:
+        raise ValueError("iters_level: at most 12 levels")
+    for l in range(12):
+        p.iters_level[l] = int(lv[l]) if l < len(lv) else -1
     if d:
         raise KeyError("unknown oracle parameters: %s" % sorted(d))
     return p
@@ -87,6 +93,11 @@ def lib():
         L.orc_filter_arrays.argtypes = [P, C.c_int, C.c_int, i32p, i32p, u8p, u8p, i32p,
                                         C.c_int64, u8p]
         L.orc_filter_arrays.restype = C.c_int64
+        L.orc_interp_cost.argtypes = [i16p, C.c_int, C.c_int, C.c_int, C.c_int, u32p]
+        L.orc_interp_knn.argtypes = [C.c_int, C.c_int, u32p, i32p, i32p, C.c_int64, C.c_int, u64p]
+        L.orc_interp_knn.restype = C.c_int
+        L.orc_interp_flow.argtypes = [C.c_int, C.c_int, C.c_int, u64p, i32p, i32p, i32p, i32p,
+                                      C.c_double, C.c_int, C.POINTER(C.c_double)]
         _lib = L
     return _lib
 
@@ -274,3 +285,56 @@ def run_pair(params, img1, img2, schedule=SCHED_CHECKERBOARD, stream_id=0):
     M = Match(p, P1, P2, schedule, stream_id)
     rows, _ = M.filter()
     return P1, P2, M, rows
+
+
+# ---- sparse-to-dense interpolation (Sec. III-G, readings R23-R25) ----------
+EMPTY_KEY = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def interp_cost(desc, shift=10):
+    """desc: (nch, h, w) int16 -> (h, w) uint32 step costs (R23)."""
+    d = np.ascontiguousarray(desc, dtype=np.int16)
+    nch, h, w = d.shape
+    out = np.zeros((h, w), np.uint32)
+    lib().orc_interp_cost(_ptr(d, C.c_int16), nch, w, h, shift, _ptr(out, C.c_uint32))
+    return out
+
+
+def interp_knn(cost, sx, sy, K):
+    """(h, w, K) uint64 keys d << 32 | match index of the K geodesically
+    nearest matches (R24)."""
+    c = np.ascontiguousarray(cost, dtype=np.uint32)
+    h, w = c.shape
+    sx = np.ascontiguousarray(sx, dtype=np.int32)
+    sy = np.ascontiguousarray(sy, dtype=np.int32)
+    keys = np.zeros((h, w, K), np.uint64)
+    if lib().orc_interp_knn(w, h, _ptr(c, C.c_uint32), _ptr(sx, C.c_int32), _ptr(sy, C.c_int32),
+                            len(sx), K, _ptr(keys, C.c_uint64)) != 0:
+        raise MemoryError("orc_interp_knn")
+    return keys
+
+
+def interp_flow(keys, sx, sy, fx, fy, lam, use_la):
+    """(h, w, 2) float64 flow from the K nearest matches (R25)."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    h, w, K = k.shape
+    a = [np.ascontiguousarray(v, dtype=np.int32) for v in (sx, sy, fx, fy)]
+    out = np.zeros((h, w, 2), np.float64)
+    lib().orc_interp_flow(w, h, K, _ptr(k, C.c_uint64), *[_ptr(v, C.c_int32) for v in a],
+                          float(lam), int(use_la), _ptr(out, C.c_double))
+    return out
+
+
+def interpolate(desc, rows, K=16, lam=32.0, shift=10, mode=0, la_permyriad=220):
+    """The whole interpolation of exported rows (x1, y1, x2, y2) over the
+    reference image of desc (nch, h, w): (keys, flow, use_la).  mode 0
+    chooses LA when the matches exceed la_permyriad / 10^4 of the pixels
+    (the paper's rule: 2.2 %), 1 forces NW, 2 forces LA."""
+    rows = np.asarray(rows, dtype=np.int32).reshape(-1, 4)
+    nch, h, w = np.asarray(desc).shape
+    use_la = (len(rows) * 10000 > la_permyriad * w * h) if mode == 0 else (mode == 2)
+    cost = interp_cost(desc, shift)
+    sx, sy = rows[:, 0], rows[:, 1]
+    keys = interp_knn(cost, sx, sy, K)
+    flow = interp_flow(keys, sx, sy, rows[:, 2] - rows[:, 0], rows[:, 3] - rows[:, 1], lam, use_la)
+    return keys, flow, bool(use_la)

@@ -18,6 +18,7 @@
  */
 #include "pgm_oracle.h"
 
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -677,7 +678,7 @@ orc_match* orc_match_run(const orc_params* p, const orc_pyr* p1, const orc_pyr* 
         if (v == 0) { init_exhaustive(m, l, 0); init_exhaustive(m, l, 1); }
         else transfer(m, lv[v - 1], l, xo[v]);
         cost_fill(m, l, 0); cost_fill(m, l, 1);
-        int T = l == 0 ? p->iters_fine : p->iters_coarse;
+        int T = p->iters_level[l] >= 0 ? p->iters_level[l] : l == 0 ? p->iters_fine : p->iters_coarse;
         basic_matching(m, l, v, T, schedule);
         consistency_update(m, l);
     }
@@ -771,4 +772,174 @@ int64_t orc_filter(const orc_params* p, const orc_match* m, int32_t* rows, int64
     const field_t* F = &m->f[0][0];
     return orc_filter_arrays(p, F->nx, F->ny, F->ux, F->uy, F->valid, F->outl, rows, max_rows,
                              keep_out);
+}
+
+/* ------------------------------------------------------------------------
+ * Sparse-to-dense interpolation (Sec. III-G).  The paper hands its grid-3
+ * matches to EpicFlow (edge-aware geodesic distance on a learned edge map,
+ * then Nadaraya-Watson (NW) or locally-weighted affine (LA) interpolation,
+ * LA when the matches exceed 2.2 % of the image).  Here the edge map is the
+ * L1 magnitude of the level-0 gradient descriptor (R23), the neighbours of a
+ * pixel are its K geodesically nearest matches (R24) and the weights are
+ * exp(-d / lambda) (R25).
+ * ---------------------------------------------------------------------- */
+
+/* R23: step cost of a pixel */
+void orc_interp_cost(const int16_t* desc, int nch, int w, int h, int shift, uint32_t* cost) {
+    for (int64_t p = 0; p < (int64_t)w * h; ++p) {
+        int64_t s = 0;
+        for (int c = 0; c < nch; ++c) {
+            int v = desc[(int64_t)c * w * h + p];
+            s += v < 0 ? -v : v;
+        }
+        cost[p] = 1u + (uint32_t)(s >> shift);
+    }
+}
+
+/* binary min-heap of (key, pixel) */
+typedef struct { uint64_t key; int64_t px; } orc_hent;
+typedef struct { orc_hent* a; int64_t n, cap; } orc_heap;
+
+static int heap_push(orc_heap* H, uint64_t key, int64_t px) {
+    if (H->n == H->cap) {
+        int64_t cap = H->cap ? 2 * H->cap : 1024;
+        orc_hent* a = (orc_hent*)realloc(H->a, (size_t)cap * sizeof(orc_hent));
+        if (!a) return -1;
+        H->a = a;
+        H->cap = cap;
+    }
+    int64_t i = H->n++;
+    while (i > 0) {
+        int64_t up = (i - 1) / 2;
+        if (H->a[up].key < key || (H->a[up].key == key && H->a[up].px <= px)) break;
+        H->a[i] = H->a[up];
+        i = up;
+    }
+    H->a[i].key = key;
+    H->a[i].px = px;
+    return 0;
+}
+
+static orc_hent heap_pop(orc_heap* H) {
+    orc_hent top = H->a[0], last = H->a[--H->n];
+    int64_t i = 0;
+    for (;;) {
+        int64_t c = 2 * i + 1;
+        if (c >= H->n) break;
+        if (c + 1 < H->n && (H->a[c + 1].key < H->a[c].key ||
+                             (H->a[c + 1].key == H->a[c].key && H->a[c + 1].px < H->a[c].px)))
+            ++c;
+        if (last.key < H->a[c].key || (last.key == H->a[c].key && last.px <= H->a[c].px)) break;
+        H->a[i] = H->a[c];
+        i = c;
+    }
+    H->a[i] = last;
+    return top;
+}
+
+/* R24: Dijkstra from every match at once, where a pixel is settled once per
+ * label, at most K times: entries leave the heap in (distance, label) order,
+ * so each pixel receives its labels in that order and keeps the first K
+ * distinct ones.  (If label i is among the K nearest of pixel p, it is among
+ * the K nearest of every pixel on a shortest path from match i to p, so the
+ * truncation loses nothing.) */
+int orc_interp_knn(int w, int h, const uint32_t* cost, const int32_t* sx, const int32_t* sy,
+                   int64_t n, int K, uint64_t* keys) {
+    const int64_t N = (int64_t)w * h;
+    int* cnt = (int*)calloc((size_t)N, sizeof(int));
+    orc_heap H = {NULL, 0, 0};
+    if (!cnt) return -1;
+    for (int64_t p = 0; p < N * K; ++p) keys[p] = UINT64_MAX;
+    int rc = 0;
+    for (int64_t i = 0; i < n && rc == 0; ++i)
+        if (sx[i] >= 0 && sy[i] >= 0 && sx[i] < w && sy[i] < h)
+            rc = heap_push(&H, (uint64_t)i, (int64_t)sy[i] * w + sx[i]);
+    int64_t* first = (int64_t*)malloc((size_t)N * sizeof(int64_t));  /* a position given twice */
+    if (!first) rc = -1;
+    for (int64_t p = 0; p < N && first; ++p) first[p] = -1;
+    for (int64_t i = 0; i < n && first; ++i)
+        if (sx[i] >= 0 && sy[i] >= 0 && sx[i] < w && sy[i] < h) {
+            const int64_t p = (int64_t)sy[i] * w + sx[i];
+            if (first[p] < 0) first[p] = i;
+        }
+    while (rc == 0 && H.n > 0) {
+        const orc_hent e = heap_pop(&H);
+        const uint64_t d = e.key >> 32;
+        const int64_t lab = (int64_t)(e.key & 0xffffffffu), p = e.px;
+        if (d == 0 && first[p] != lab) continue;           /* duplicate position */
+        if (cnt[p] >= K) continue;
+        int seen = 0;
+        for (int k = 0; k < cnt[p]; ++k)
+            if ((int64_t)(keys[p * K + k] & 0xffffffffu) == lab) seen = 1;
+        if (seen) continue;
+        keys[p * K + cnt[p]++] = e.key;
+        const int x = (int)(p % w), y = (int)(p / w);
+        const int nx[4] = {x - 1, x + 1, x, x}, ny[4] = {y, y, y - 1, y + 1};
+        for (int k = 0; k < 4 && rc == 0; ++k) {
+            if (nx[k] < 0 || ny[k] < 0 || nx[k] >= w || ny[k] >= h) continue;
+            const int64_t q = (int64_t)ny[k] * w + nx[k];
+            if (cnt[q] >= K) continue;
+            const uint64_t dq = d + cost[p] + cost[q];
+            if (dq >= 0xffffffffull) continue;               /* beyond the distance range */
+            rc = heap_push(&H, dq << 32 | (uint64_t)lab, q);
+        }
+    }
+    free(H.a);
+    free(cnt);
+    free(first);
+    return rc;
+}
+
+/* R25: NW average, or the weighted affine fit (Cramer's rule on the 3 x 3
+ * normal equations in coordinates relative to the pixel, whose constant
+ * term is the value at the pixel).  The weights are taken relative to the
+ * nearest match's (exp(-(d - d0) / lambda), the same fit and average); the
+ * fit counts as degenerate when det M <= 1e-6 (sum of weights)^3. */
+void orc_interp_flow(int w, int h, int K, const uint64_t* keys, const int32_t* sx,
+                     const int32_t* sy, const int32_t* fx, const int32_t* fy, double lambda,
+                     int use_la, double* flow) {
+    for (int64_t p = 0; p < (int64_t)w * h; ++p) {
+        const int x = (int)(p % w), y = (int)(p / w);
+        double sw = 0, nwx = 0, nwy = 0;
+        double M[3][3] = {{0}}, bx[3] = {0}, by[3] = {0};
+        const uint64_t d0 = keys[p * K] >> 32;          /* weights relative to the nearest */
+        for (int k = 0; k < K; ++k) {
+            const uint64_t key = keys[p * K + k];
+            if (key == UINT64_MAX) break;
+            const int64_t i = (int64_t)(key & 0xffffffffu);
+            const double wgt = exp(-(double)((key >> 32) - d0) / lambda);
+            const double v[3] = {(double)(sx[i] - x), (double)(sy[i] - y), 1.0};
+            sw += wgt;
+            nwx += wgt * fx[i];
+            nwy += wgt * fy[i];
+            for (int a = 0; a < 3; ++a) {
+                for (int b = 0; b < 3; ++b) M[a][b] += wgt * v[a] * v[b];
+                bx[a] += wgt * fx[i] * v[a];
+                by[a] += wgt * fy[i] * v[a];
+            }
+        }
+        double ox = 0, oy = 0;
+        if (sw > 0) {
+            ox = nwx / sw;
+            oy = nwy / sw;
+            if (use_la) {
+                const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                                   M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                                   M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+                if (det > 1e-6 * sw * sw * sw) {
+                    /* constant term: the determinant with column 3 replaced by b */
+                    const double dx = M[0][0] * (M[1][1] * bx[2] - bx[1] * M[2][1]) -
+                                      M[0][1] * (M[1][0] * bx[2] - bx[1] * M[2][0]) +
+                                      bx[0] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+                    const double dy = M[0][0] * (M[1][1] * by[2] - by[1] * M[2][1]) -
+                                      M[0][1] * (M[1][0] * by[2] - by[1] * M[2][0]) +
+                                      by[0] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+                    ox = dx / det;
+                    oy = dy / det;
+                }
+            }
+        }
+        flow[2 * p] = ox;
+        flow[2 * p + 1] = oy;
+    }
 }

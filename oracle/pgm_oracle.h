@@ -47,6 +47,8 @@ typedef struct {
     int32_t rs_grid;       /* 0: search at every seed; g > 0: at level 0 only
                               where x and y are both == g/2 (mod g)        */
     uint64_t philox_key;
+    int32_t iters_level[12]; /* entry l >= 0: iterations at level l in place
+                                of iters_coarse / iters_fine; -1: unset    */
 } orc_params;
 
 enum { ORC_SCHED_CHECKERBOARD = 0, ORC_SCHED_SEQUENTIAL = 1 };
@@ -108,6 +110,27 @@ int64_t orc_filter_arrays(const orc_params* p, int nx, int ny, const int32_t* ux
                           int32_t* rows, int64_t max_rows, uint8_t* keep_out);
 int64_t orc_filter(const orc_params* p, const orc_match* m, int32_t* rows, int64_t max_rows,
                    uint8_t* keep);
+
+/* ---- sparse-to-dense interpolation (Sec. III-G; readings R23-R25) -------- */
+/* Per-pixel step cost of the geodesic distance (R23): 1 + (sum over the
+ * descriptor channels of |g|) >> shift.  desc: nch planes of w x h int16. */
+void orc_interp_cost(const int16_t* desc, int nch, int w, int h, int shift, uint32_t* cost);
+/* The K geodesically nearest matches of every pixel (R24): 4-connected grid,
+ * a step between neighbours p, q costs cost[p] + cost[q]; match i sits at
+ * (sx[i], sy[i]) (a position given twice keeps the smaller index).  keys:
+ * w x h x K, ascending, key = d << 32 | i, UINT64_MAX where fewer than K
+ * matches are reachable.  Returns 0, or -1 when out of memory. */
+int orc_interp_knn(int w, int h, const uint32_t* cost, const int32_t* sx, const int32_t* sy,
+                   int64_t n, int K, uint64_t* keys);
+/* Flow of every pixel from its K nearest matches (R25): weights
+ * exp(-(d - d_nearest) / lambda); use_la = 0 Nadaraya-Watson average, 1
+ * weighted affine fit evaluated at the pixel (Nadaraya-Watson where the fit
+ * is degenerate).
+ * fx, fy: the matches' displacements.  flow: w x h x 2 (0 where no match is
+ * reachable). */
+void orc_interp_flow(int w, int h, int K, const uint64_t* keys, const int32_t* sx,
+                     const int32_t* sy, const int32_t* fx, const int32_t* fy, double lambda,
+                     int use_la, double* flow);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,8 @@ PARAM_FIELDS = [
 
 
 class CParams(C.Structure):
-    _fields_ = [(n, C.c_int32) for n, _ in PARAM_FIELDS] + [("philox_key", C.c_uint64)]
+    _fields_ = ([(n, C.c_int32) for n, _ in PARAM_FIELDS] + [("philox_key", C.c_uint64)]
+                + [("iters_level", C.c_int32 * 12)])
 
 
 STATUS = {0: "PGM_OK", 1: "PGM_ERR_ARG", 2: "PGM_ERR_SIZE", 3: "PGM_ERR_WORKSPACE",
@@ -32,12 +33,20 @@ EXPORTS = [
     "pgm_match", "pgm_match_batch", "pgm_field_layout", "pgm_filter", "pgm_sync_status",
     "pgm_nominal_evals", "pgm_launch_count", "pgm_profile_enable", "pgm_profile_read",
     "pgm_filter_noalloc", "pgm_build_pyramid_batch", "pgm_filter_batch", "pgm_set_tuning",
-    "pgm_get_tuning", "pgm_set_wait_limit", "pgm_error_detail",
+    "pgm_get_tuning", "pgm_set_wait_limit", "pgm_error_detail", "pgm_interp_default_params",
+    "pgm_interp_workspace_bytes", "pgm_interpolate",
 ]
 
 
 class CTuning(C.Structure):
-    _fields_ = [("window_slack", C.c_int32), ("pairs_per_launch", C.c_int32)]
+    _fields_ = [("window_slack", C.c_int32), ("pairs_per_launch", C.c_int32), ("tile_w", C.c_int32)]
+
+
+class CInterp(C.Structure):
+    _fields_ = [("k", C.c_int32), ("mode", C.c_int32), ("cost_shift", C.c_int32),
+                ("la_permyriad", C.c_int32), ("lambda_", C.c_double)]
+
+
 NOALLOC_MAX_SEEDS = 1 << 20
 K_CLASSES = ["pyramid", "init", "cost", "pm", "consist", "transfer", "filter"]
 WS_EVALS_OFFSET, WS_EVALS_COUNT = 8, 8   # pm, cost, init, pm-from-global: fwd/bwd each
@@ -88,6 +97,12 @@ def load(path: str = LIB_PATH):
     L.pgm_set_tuning.argtypes = [C.POINTER(CTuning)]; L.pgm_set_tuning.restype = C.c_int
     L.pgm_get_tuning.argtypes = [C.POINTER(CTuning)]; L.pgm_get_tuning.restype = C.c_int
     L.pgm_set_wait_limit.argtypes = [C.c_int64]; L.pgm_set_wait_limit.restype = C.c_int
+    L.pgm_interp_default_params.argtypes = [C.POINTER(CInterp)]; L.pgm_interp_default_params.restype = None
+    L.pgm_interp_workspace_bytes.argtypes = [i32, i32, C.POINTER(CInterp)]
+    L.pgm_interp_workspace_bytes.restype = C.c_size_t
+    L.pgm_interpolate.argtypes = [P, vp, i32, i32, vp, vp, i64, C.POINTER(CInterp), vp, C.c_size_t,
+                                  vp, vp]
+    L.pgm_interpolate.restype = C.c_int
     L.pgm_build_pyramid_batch.argtypes = [P, i32, C.POINTER(vp), C.POINTER(C.c_int32), psz,
                                           C.POINTER(vp), psz, vp]
     L.pgm_filter_batch.argtypes = [P, i32, C.POINTER(C.c_int32), C.POINTER(vp), psz,

@@ -40,11 +40,20 @@ class Params:
     ablation: int = 0
     rs_grid: int = 0
     philox_key: int = 0x5EED5EED1234ABCD
+    iters_level: tuple = ()       # per-level iteration counts (level 0 first); () keeps
+                                  # iters_coarse / iters_fine, -1 keeps them at one level
 
     def cstruct(self) -> _lib.CParams:
         p = _lib.CParams()
         for f in fields(self):
-            setattr(p, f.name, int(getattr(self, f.name)))
+            if f.name == "iters_level":
+                lv = tuple(self.iters_level)
+                if len(lv) > 12:
+                    raise ValueError("iters_level: at most 12 levels")
+                for l in range(12):
+                    p.iters_level[l] = int(lv[l]) if l < len(lv) else -1
+            else:
+                setattr(p, f.name, int(getattr(self, f.name)))
         return p
 
     def replace(self, **kw) -> "Params":
@@ -303,3 +312,47 @@ class PairMatcher:
     def results(self):
         counts = self.count[:, 0].tolist()
         return [self.rows[k, :min(c, self.cap)] for k, c in enumerate(counts)]
+
+
+@dataclass
+class InterpParams:
+    """Sparse-to-dense interpolation parameters (include/pgm.h,
+    pgm_interp_params): k nearest matches, mode 0 auto (LA above
+    la_permyriad / 10^4 matches per pixel, the paper's 2.2 %), 1 NW, 2 LA."""
+    k: int = 16
+    mode: int = 0
+    cost_shift: int = 10
+    la_permyriad: int = 220
+    lam: float = 32.0
+
+    def cstruct(self) -> _lib.CInterp:
+        return _lib.CInterp(int(self.k), int(self.mode), int(self.cost_shift),
+                            int(self.la_permyriad), float(self.lam))
+
+
+def interpolate(params: Params, pyr1: Pyramid, matches: torch.Tensor, count: torch.Tensor,
+                ip: InterpParams = None, ws: torch.Tensor = None, stream=None):
+    """Dense flow (h, w, 2) float32 of image 1 from exported matches
+    (n, 4) int32 and their device count (pgm_interpolate).  Returns (flow,
+    workspace); the workspace starts with the (h, w, k) uint64 neighbour keys."""
+    ip = ip or InterpParams()
+    cip = ip.cstruct()
+    L = _lib.load()
+    nbytes = L.pgm_interp_workspace_bytes(pyr1.w, pyr1.h, C.byref(cip))
+    if nbytes == 0:
+        raise ValueError("invalid interpolation parameters or image size")
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=pyr1.buf.device)
+    flow = torch.empty((pyr1.h, pyr1.w, 2), dtype=torch.float32, device=pyr1.buf.device)
+    m = matches.contiguous()
+    check(L.pgm_interpolate(C.byref(params.cstruct()), C.c_void_p(pyr1.buf.data_ptr()), pyr1.w,
+                            pyr1.h, C.c_void_p(m.data_ptr()), C.c_void_p(count.data_ptr()),
+                            int(m.shape[0]), C.byref(cip), C.c_void_p(ws.data_ptr()), ws.numel(),
+                            C.c_void_p(flow.data_ptr()), _stream(stream)), "pgm_interpolate")
+    return flow, ws
+
+
+def interp_keys(ws: torch.Tensor, w: int, h: int, k: int) -> torch.Tensor:
+    """(h, w, k) int64 view of the neighbour keys at the start of an
+    interpolation workspace (uint64 bits)."""
+    return ws[:8 * w * h * k].view(torch.int64).view(h, w, k)

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpgm.so")
 SOURCES = ["abi.cu", "pyramid.cu", "match.cu", "pm_row.cu", "init_tile.cu", "filter.cu",
-           "filter_noalloc.cu"]
+           "filter_noalloc.cu", "interp.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 if not os.path.exists(NVCC):

@@ -47,8 +47,8 @@ pgm_status cuda_fail(const char* site, cudaError_t e) {
 }
 
 // ------------------------------------------------------------ tuning knobs
-static std::atomic<int> g_slack{2}, g_chunk{MAXB};
-Tuning tuning() { return Tuning{g_slack.load(), g_chunk.load()}; }
+static std::atomic<int> g_slack{2}, g_chunk{MAXB}, g_tile_w{8};
+Tuning tuning() { return Tuning{g_slack.load(), g_chunk.load(), g_tile_w.load()}; }
 
 // bounded device waits (the search kernel's mbarrier waits), in SM cycles
 constexpr long long WAIT_DEFAULT = 1ll << 31;        // about 1 s at 2 GHz
@@ -109,6 +109,8 @@ pgm_status check_params(const pgm_params* p) {
     if (p->norm != PGM_L2SQ && p->norm != PGM_L1) return PGM_ERR_ARG;
     if (p->iters_coarse < 0 || p->iters_fine < 0 || p->iters_coarse > 32767 ||
         p->iters_fine > 32767) return PGM_ERR_ARG;
+    for (int l = 0; l < 12; ++l)
+        if (p->iters_level[l] < -1 || p->iters_level[l] > 32767) return PGM_ERR_ARG;
     if (p->refine_rounds < 0 || p->refine_rounds > 64) return PGM_ERR_ARG;
     if (p->rs_W < 1 || p->rs_W > (1 << 14)) return PGM_ERR_ARG;
     if (p->rs_mode != PGM_RS_SYMMETRIC && p->rs_mode != PGM_RS_PAPER_FLOOR) return PGM_ERR_ARG;
@@ -339,6 +341,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
     mc.tau2 = p->tau2;
     mc.rs_grid = p->rs_grid;
     mc.slack = tuning().slack;
+    mc.tile_w = tuning().tile_w;
     mc.descriptor = p->descriptor;
     static thread_local LvlBatch B;       // ~8 KB: kept off the stack
     static thread_local XferBatch X;
@@ -440,7 +443,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
         if (r != PGM_OK) return r;
         // the cost refresh of the visit: by the search kernel's first
         // iteration when the tile kernel takes the batch, else on its own
-        const int T = l == 0 ? p->iters_fine : p->iters_coarse;
+        const int T = iters_at(p, l);
         const bool fused = T > 0 && pm_tile_fits(B, mc, nch);
         if (!fused) {
             r = launch_cost_fill(B, mc, nch, maxP, max_seeds, st);
@@ -516,6 +519,7 @@ void pgm_default_params(pgm_params* p) {
     p->levels = 3; p->seed_stride = 3; p->patch_fwd = 15; p->patch_bwd = 11; p->sobel = 5;
     p->color = PGM_RGB; p->descriptor = PGM_FULL; p->cs_sched = PGM_CS_PAPER; p->norm = PGM_L2SQ;
     p->iters_coarse = 4; p->iters_fine = 6; p->refine_rounds = 2; p->rs_W = 2;
+    for (int l = 0; l < 12; ++l) p->iters_level[l] = -1;
     p->rs_mode = PGM_RS_SYMMETRIC; p->tau2 = 1; p->min_region = 9; p->region_dmax2 = 144;
     p->max_visits = 0; p->ablation = 0; p->rs_grid = 0;
     p->philox_key = 0x5EED5EED1234ABCDull;
@@ -762,11 +766,13 @@ pgm_status pgm_sync_status(const pgm_params* p, int w1, int h1, int w2, int h2, 
 }
 
 pgm_status pgm_set_tuning(const pgm_tuning* t) {
-    if (!t) { g_slack = 2; g_chunk = MAXB; return PGM_OK; }
+    if (!t) { g_slack = 2; g_chunk = MAXB; g_tile_w = 8; return PGM_OK; }
     if (t->window_slack < 0 || t->window_slack > 32 || t->pairs_per_launch < 1 ||
-        t->pairs_per_launch > MAXB) return PGM_ERR_ARG;
+        t->pairs_per_launch > MAXB || (t->tile_w != 4 && t->tile_w != 8 && t->tile_w != 16))
+        return PGM_ERR_ARG;
     g_slack = t->window_slack;
     g_chunk = t->pairs_per_launch;
+    g_tile_w = t->tile_w;
     return PGM_OK;
 }
 
@@ -780,6 +786,7 @@ pgm_status pgm_get_tuning(pgm_tuning* t) {
     if (!t) return PGM_ERR_ARG;
     t->window_slack = g_slack;
     t->pairs_per_launch = g_chunk;
+    t->tile_w = g_tile_w;
     return PGM_OK;
 }
 
@@ -827,7 +834,7 @@ int64_t pgm_nominal_evals(const pgm_params* p, int w1, int h1, int w2, int h2) {
     int64_t total = 0;
     for (int v = 0; v < sch.n; ++v) {
         const int l = sch.level[v];
-        const int64_t T = l == 0 ? p->iters_fine : p->iters_coarse;
+        const int64_t T = iters_at(p, l);
         for (int d = 0; d < 2; ++d) {
             const int64_t ns = (int64_t)wp.nx[l][d] * wp.ny[l][d];
             int64_t searching = ns;            // seeds that run the random search

@@ -102,6 +102,11 @@ inline int lattice_n(int W, int sigma) {
     int c = sigma / 2;
     return (W - 1 - c) >= 0 ? (W - 1 - c) / sigma + 1 : 0;
 }
+// iterations of a visit at level l: the per-level count when set, else
+// iters_fine at level 0 and iters_coarse above
+inline int iters_at(const pgm_params* p, int l) {
+    return p->iters_level[l] >= 0 ? p->iters_level[l] : l == 0 ? p->iters_fine : p->iters_coarse;
+}
 inline int rs_count(int W) { int K = 0; for (int w = W; w >= 1; w >>= 1) ++K; return K; }
 
 // ------------------------------------------------------- kernel blocks
@@ -157,10 +162,11 @@ struct MatchConst {              // scalars common to one launch
     int32_t refresh;                    // search phase also scores the current matches first
     int32_t cost_only;                  // score the current matches only (a visit without iterations)
     int32_t descriptor;                 // PGM_FULL, PGM_DIR (bit-plane search), PGM_SECTOR
+    int32_t tile_w;                     // tuning: seeds per search-tile row (64 per tile)
 };
 
 // result-invariant tuning knobs (pgm_set_tuning)
-struct Tuning { int slack; int chunk; };
+struct Tuning { int slack; int chunk; int tile_w; };
 Tuning tuning();
 
 // A host-side NVTX push/pop range: names the entry point and, inside

@@ -3,8 +3,9 @@
 // every seed's current match), squared-L2 cost (Eq. 3), on seed tiles staged
 // in shared memory.
 //
-// A tile is PR_TW x PR_TH lattice seeds; its PR_NACT seeds of the current
-// colour update.  A persistent CTA (one per SM) has PR_PROD producer warps and
+// A tile is tw x th lattice seeds (tw th = 64; tw = 4, 8 or 16, a result-
+// invariant tuning knob); its PR_NACT = 32 seeds of the current colour
+// update.  A persistent CTA (one per SM) has PR_PROD producer warps and
 // pr_cons consumer warps around a ring of tile buffers in shared memory, each
 // with a "full" and an "empty" mbarrier:
 //   - producer warp p stages the CTA's tiles p, p + PR_PROD, ...: it waits
@@ -49,8 +50,8 @@
 
 namespace pgm {
 
-constexpr int PR_TW = 8, PR_TH = 8;            // lattice seeds per tile
-constexpr int PR_NACT = PR_TW * PR_TH / 2;     // seeds of one colour per tile (one producer lane each)
+constexpr int PR_TILE = 64;                    // lattice seeds per tile (tw x th)
+constexpr int PR_NACT = PR_TILE / 2;           // seeds of one colour per tile (one producer lane each)
 constexpr int PR_PROD = 2;                     // producer warps
 // consumer warps: 18 (20 warps of at most 96 registers), 14 for the colour
 // layouts of 8 pixels per lane (P > 11), whose 24 reference words need more
@@ -63,6 +64,7 @@ constexpr long long PR_DRAIN_CYCLES = 1ll << 31;   // final wait for issued copi
 
 struct RowGeom {
     int P, pxw;
+    int tw, th;                       // tile shape in lattice seeds
     int ref_w, ref_h, win_w, win_h;   // staged regions (px)
     int sp;                           // words per shared row (reference region and window)
     int cw, ch, cwp;                  // window centres (cw x ch), row pitch of their sums (even)
@@ -73,12 +75,15 @@ struct RowGeom {
     int bwr, bww, off_rs, off_ws;
 };
 
-__host__ __device__ inline RowGeom rg_geom(int nch, int P, int sigma, int rs_W, int slack) {
+__host__ __device__ inline RowGeom rg_geom(int nch, int P, int sigma, int rs_W, int slack,
+                                           int tw) {
     RowGeom g;
     g.P = P;
     g.pxw = px_words(nch);
-    g.ref_w = sigma * (PR_TW - 1) + P;
-    g.ref_h = sigma * (PR_TH - 1) + P;
+    g.tw = tw;
+    g.th = PR_TILE / tw;
+    g.ref_w = sigma * (g.tw - 1) + P;
+    g.ref_h = sigma * (g.th - 1) + P;
     const int rho = rs_W > 1 ? rs_W : 1;
     g.win_w = g.ref_w + 2 * (rho + slack);
     g.win_h = g.ref_h + 2 * (rho + slack);
@@ -104,11 +109,12 @@ __host__ __device__ inline RowGeom rg_geom(int nch, int P, int sigma, int rs_W, 
 // is P nch bits, read as NW aligned words from a staged row that starts at a
 // 16-byte boundary (up to 127 bits before the first pixel); row pitches are 4
 // (mod 8) words, so the 16 rows a half-warp reads meet at most 2 to a bank.
-__host__ __device__ inline RowGeom rg_geom_bits(int nch, int P, int sigma, int rs_W, int slack) {
-    RowGeom g = rg_geom(nch, P, sigma, rs_W, slack);
+__host__ __device__ inline RowGeom rg_geom_bits(int nch, int P, int sigma, int rs_W, int slack,
+                                                int tw) {
+    RowGeom g = rg_geom(nch, P, sigma, rs_W, slack, tw);
     const int nw = nch == 6 ? 4 : 2;                      // words a lane reads per row
     auto pitch = [](int need) { while (need % 8 != 4) ++need; return need; };
-    g.bwr = pitch((127 + sigma * (PR_TW - 1) * nch) / 32 + nw);
+    g.bwr = pitch((127 + sigma * (g.tw - 1) * nch) / 32 + nw);
     g.bww = pitch((127 + (g.win_w - P) * nch) / 32 + nw);
     g.off_rs = (g.bwr * g.ref_h + 31) & ~31;
     g.off_win = (g.off_rs + g.bwr * g.ref_h + 31) & ~31;
@@ -272,8 +278,8 @@ __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSch
         const int k = lo, pair = S.ndir == 2 ? k >> 1 : k, dir = S.ndir == 2 ? (k & 1) : S.dir;
         const RowGeom& G = geom[dir];
         const DirLvl& D = B.d[pair][dir];
-        const int tiles_x = (D.nx + PR_TW - 1) / PR_TW, tt = t - S.cum[k];
-        const int i0 = (tt % tiles_x) * PR_TW, j0 = (tt / tiles_x) * PR_TH;
+        const int tiles_x = (D.nx + G.tw - 1) / G.tw, tt = t - S.cum[k];
+        const int i0 = (tt % tiles_x) * G.tw, j0 = (tt / tiles_x) * G.th;
         const int P = D.P, h = P / 2, sig = mc.sigma;
         const int rx0 = mc.c + sig * i0 - h, ry0 = mc.c + sig * j0 - h;
         // bit-plane form: first staged word (a multiple of 4) and bit shift
@@ -294,8 +300,8 @@ __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSch
         // the seed of this lane: active seed a = lane of the tile (Eq. 4 candidates, Eq. 5 draws)
         const int t4 = mc.t & 3;
         const int sx = (t4 == 0 || t4 == 3) ? 1 : -1, sy = (t4 == 0 || t4 == 2) ? 1 : -1;
-        const int a = lane, j = j0 + a / (PR_TW / 2);
-        const int i = i0 + 2 * (a % (PR_TW / 2)) + ((j + mc.colour) & 1);
+        const int a = lane, j = j0 + a / (G.tw / 2);
+        const int i = i0 + 2 * (a % (G.tw / 2)) + ((j + mc.colour) & 1);
         RowRec R;
         R.s = -1; R.px = 0; R.py = 0; R.f = 0; R.u = 0; R.nb0 = NO_CAND; R.nb1 = NO_CAND; R.K = 0;
         R.r0 = 0; R.r1 = 0; R.f0 = 0; R.wr0 = -2; R.wu = -1; R.w0 = -1; R.w1 = -1; R.wr1 = -2;
@@ -687,7 +693,8 @@ k_pm_r(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
     const unsigned full0 = (unsigned)__cvta_generic_to_shared(&s_full[0]);
     const unsigned empty0 = (unsigned)__cvta_generic_to_shared(&s_empty[0]);
     if (threadIdx.x < 2)
-        s_geom[threadIdx.x] = rg_geom(NCH, B.d[0][threadIdx.x].P, mc.sigma, mc.rs_W, mc.slack);
+        s_geom[threadIdx.x] = rg_geom(NCH, B.d[0][threadIdx.x].P, mc.sigma, mc.rs_W, mc.slack,
+                                      mc.tile_w);
     if (threadIdx.x == 0) {
         for (int b = 0; b < nbuf; ++b) {
             mbar_init(full0 + 8u * b, 1);
@@ -945,7 +952,8 @@ k_pm_b(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
     const unsigned full0 = (unsigned)__cvta_generic_to_shared(&s_full[0]);
     const unsigned empty0 = (unsigned)__cvta_generic_to_shared(&s_empty[0]);
     if (threadIdx.x < 2)
-        s_geom[threadIdx.x] = rg_geom_bits(NCH, B.d[0][threadIdx.x].P, mc.sigma, mc.rs_W, mc.slack);
+        s_geom[threadIdx.x] = rg_geom_bits(NCH, B.d[0][threadIdx.x].P, mc.sigma, mc.rs_W, mc.slack,
+                                           mc.tile_w);
     if (threadIdx.x == 0) {
         for (int b = 0; b < nbuf; ++b) {
             mbar_init(full0 + 8u * b, 1);
@@ -1109,8 +1117,8 @@ static bool pr_plan(const LvlBatch& B, const MatchConst& mc, int nch, RowSched* 
         S[d].total = 0;
         S[d].dir = d;
         S[d].ndir = 1;
-        G[d] = bits ? rg_geom_bits(nch, B.d[0][d].P, mc.sigma, mc.rs_W, mc.slack)
-                    : rg_geom(nch, B.d[0][d].P, mc.sigma, mc.rs_W, mc.slack);
+        G[d] = bits ? rg_geom_bits(nch, B.d[0][d].P, mc.sigma, mc.rs_W, mc.slack, mc.tile_w)
+                    : rg_geom(nch, B.d[0][d].P, mc.sigma, mc.rs_W, mc.slack, mc.tile_w);
         if (B.d[0][d].P > MAXP || 2L * G[d].words * 4 > 200L * 1024 ||
             (long)G[d].sp * G[d].win_h >= 65536L || (long)G[d].cwp * G[d].ch >= 32768L)
             return false;
@@ -1119,7 +1127,7 @@ static bool pr_plan(const LvlBatch& B, const MatchConst& mc, int nch, RowSched* 
     for (int k = 0; k < B.n; ++k)
         for (int d = 0; d < 2; ++d) {
             const DirLvl& D = B.d[k][d];
-            const int tiles = ((D.nx + PR_TW - 1) / PR_TW) * ((D.ny + PR_TH - 1) / PR_TH);
+            const int tiles = ((D.nx + G[d].tw - 1) / G[d].tw) * ((D.ny + G[d].th - 1) / G[d].th);
             S[d].cum[k] = S[d].total;
             S[d].total += tiles;
             S[2].cum[2 * k + d] = S[2].total;

@@ -46,6 +46,7 @@ def test_default_params_are_the_papers(lib):
     assert (p.levels, p.rs_W, p.sobel, p.refine_rounds, p.iters_coarse, p.iters_fine) == (3, 2, 5, 2, 4, 6)
     assert (p.patch_fwd, p.patch_bwd, p.min_region, p.region_dmax2) == (15, 11, 9, 144)
     assert p.philox_key == d.philox_key
+    assert list(p.iters_level) == [-1] * 12 == list(d.cstruct().iters_level)
 
 
 def test_status_strings(lib):
@@ -67,6 +68,10 @@ def test_size_queries_and_argument_checks(lib):
     big = Params(patch_fwd=17).cstruct()
     assert lib.pgm_match(C.byref(big), C.c_void_p(256), C.c_void_p(512), 64, 64, 64, 64, 0,
                          C.c_void_p(1024), 1 << 30, None) == 7
+    for lv in ((2, -2), (32768,)):              # per-level counts: -1 .. 32767
+        bad_it = Params(iters_level=lv).cstruct()
+        assert lib.pgm_match(C.byref(bad_it), C.c_void_p(256), C.c_void_p(512), 64, 64, 64, 64, 0,
+                             C.c_void_p(1024), 1 << 30, None) == 1
     # workspace too small is reported before any launch
     assert lib.pgm_match(C.byref(p), C.c_void_p(256), C.c_void_p(512), 1024, 436, 1024, 436, 0,
                          C.c_void_p(1024), 16, None) == 3

@@ -160,6 +160,30 @@ def test_cost_non_increasing_within_visit():
         prev = f
 
 
+def test_per_level_iterations_select_the_count():
+    """iters_level[l] replaces the iteration count of every visit at level l
+    and -1 keeps iters_coarse / iters_fine: the paper's schedule written per
+    level gives the same fields, and one level's count written per level
+    equals the same count given as iters_fine / iters_coarse."""
+    f1, f2, _ = synth.noise_affine_pair(4, w=128, h=96)
+    base = dict(levels=3, seed_stride=3, patch_fwd=8, patch_bwd=8)
+
+    def fields(extra):
+        p = O.make_params(dict(base, **extra))
+        M = O.Match(p, O.Pyramid(p, f1), O.Pyramid(p, f2))
+        return [M.field(l, d) for l in range(3) for d in (0, 1)]
+
+    def same(a, b):
+        return all((x[k] == y[k]).all() for x, y in zip(a, b) for k in ("ux", "uy", "valid", "cost"))
+
+    ref = fields({})
+    assert same(ref, fields(dict(iters_level=(6, 4, 4))))
+    assert same(ref, fields(dict(iters_level=(-1, 4, -1))))
+    assert same(fields(dict(iters_fine=2)), fields(dict(iters_level=(2,))))
+    assert same(fields(dict(iters_coarse=1, iters_fine=3)), fields(dict(iters_level=(3, 1, 1))))
+    assert not same(ref, fields(dict(iters_level=(6, 0, 4))))
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("name", ["c1", "c2", "c3"])
 def test_checkerboard_vs_sequential_margins(name):

@@ -107,6 +107,7 @@ def test_match_every_visit_c1(api):
     ("C3-dense", dict(levels=3, color=1, seed_stride=1, rs_grid=3, patch_fwd=7, patch_bwd=5),
      (160, 96)),
     ("G3", dict(levels=4, color=0, rs_grid=3), (301, 157)),
+    ("per-level-iters", dict(levels=4, color=1, iters_level=(3, 1, 5, 0)), (384, 164)),
 ])
 def test_pipeline_parity(api, name, prm, size):
     if size is None:
