@@ -976,6 +976,289 @@ k_pm_b(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
 }  // namespace
 
 // ===========================================================================
+// ------------------------------------------------------------------
+// Bit-plane search, one seed per lane.  A popcount cost is so cheap that a
+// warp cooperating on one seed spends most of its instructions on the seed's
+// bookkeeping; here a consumer warp takes a whole staged tile and every lane
+// one of its 32 seeds, so that bookkeeping is paid once per lane instead of
+// once per warp.  A lane first scores, row by row with its reference row
+// loaded once, every candidate known when the tile was staged: the current
+// match (cost refresh), the two propagated matches and the first two search
+// candidates around the current match; then it takes the decisions in the
+// paper's order.  Where a propagated match moved the search centre (or the
+// search has more than two candidates) the remaining search candidates are
+// scored afterwards, one per round, in order.  Results and evaluation counts
+// are those of the sequential order.
+constexpr int PS_PROD = 4, PS_CONS = 12, PS_NBUF = 16;
+constexpr int PS_NC = 5;                      // candidates scored in the first round
+
+// Cost rows [0, P) of NC candidates against the lane's reference patch.
+// ok[j]: candidate j is scored; slot[j]: window corner (y0 << 16 | x0) or -1
+// (read from the padded bit-planes in global memory, centre qx[j], qy[j]).
+template <int NCH, int NC>
+__device__ __forceinline__ void ps_rows(const RowGeom& G, const RowHdr& H, const DirLvl& D, int P,
+                                        unsigned a_rn, unsigned a_rs, unsigned a_wn, unsigned a_ws,
+                                        int rbit, int rrow, const bool (&ok)[NC],
+                                        const int (&slot)[NC], const int (&qx)[NC],
+                                        const int (&qy)[NC], unsigned fac, unsigned (&c)[NC]) {
+    constexpr int NR = NCH == 6 ? 3 : 1, NW = NR + 1;
+    const int h = P / 2;
+    const int tplane = D.tbit_row * (D.th + 2 * BORD);
+    unsigned msk[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int nb = P * NCH - 32 * k;
+        msk[k] = nb <= 0 ? 0u : nb >= 32 ? 0xffffffffu : (1u << nb) - 1u;
+    }
+    // per candidate: the first word of its row 0 and the bit shift
+    unsigned base[NC];
+    const uint32_t* gp[NC];
+    int sh[NC];
+    bool sm_[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        c[j] = 0;
+        sm_[j] = ok[j] && slot[j] >= 0;
+        base[j] = 0;
+        gp[j] = D.tgt_bits;
+        sh[j] = 0;
+        if (sm_[j]) {
+            const int bit = H.shw + (slot[j] & 0xffff) * NCH;
+            sh[j] = bit & 31;
+            base[j] = 4u * (unsigned)((slot[j] >> 16) * G.bww + (bit >> 5));
+        } else if (ok[j]) {
+            const int bit = (qx[j] - h + BORD) * NCH;
+            sh[j] = bit & 31;
+            gp[j] = D.tgt_bits + (size_t)(qy[j] - h + BORD) * D.tbit_row + (bit >> 5);
+        }
+    }
+    const int rsh = rbit & 31;
+    unsigned rb = 4u * (unsigned)(rrow * G.bwr + (rbit >> 5));
+    for (int r = 0; r < P; ++r) {
+        unsigned an[NR], as[NR];
+        {
+            unsigned vn[NW], vs[NW];
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                vn[k] = (unsigned)lds32(a_rn + rb + 4u * k);
+                vs[k] = (unsigned)lds32(a_rs + rb + 4u * k);
+            }
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                an[k] = __funnelshift_r(vn[k], vn[k + 1], rsh) & msk[k];
+                as[k] = __funnelshift_r(vs[k], vs[k + 1], rsh);
+            }
+        }
+        rb += 4u * (unsigned)G.bwr;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            if (!ok[j]) continue;
+            unsigned vn[NW], vs[NW];
+            if (sm_[j]) {
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    vn[k] = (unsigned)lds32(a_wn + base[j] + 4u * k);
+                    vs[k] = (unsigned)lds32(a_ws + base[j] + 4u * k);
+                }
+                base[j] += 4u * (unsigned)G.bww;
+            } else {
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    vn[k] = __ldg(gp[j] + k);
+                    vs[k] = __ldg(gp[j] + tplane + k);
+                }
+                gp[j] += D.tbit_row;
+            }
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                const unsigned tn = __funnelshift_r(vn[k], vn[k + 1], sh[j]);
+                const unsigned ts = __funnelshift_r(vs[k], vs[k + 1], sh[j]);
+                c[j] += (unsigned)__popc((an[k] ^ tn) & msk[k]) +
+                        ((unsigned)__popc(an[k] & tn & (as[k] ^ ts)) << fac);
+            }
+        }
+    }
+}
+
+template <int NCH, int PC>
+__device__ void ps_consume(const LvlBatch& B, const MatchConst& mc, const RowSched& S, int buf_words,
+                           int nbuf, unsigned a_sm, RowRec (*rec)[PR_NACT], const RowHdr* hdr,
+                           const RowGeom* geom, unsigned full0, unsigned empty0,
+                           volatile int* abort, long long limit, int cw, int lane) {
+    constexpr unsigned INF32 = 0xffffffffu;
+    const unsigned fac = mc.norm == PGM_L2SQ ? 2u : 1u;      // 4 = 1 << 2, 2 = 1 << 1
+    for (int n = cw;; n += PS_CONS) {
+        const int t = blockIdx.x + n * gridDim.x;
+        if (t >= S.total) break;
+        const int b = n % nbuf;
+        if (!__all_sync(FULL, mbar_wait(full0 + 8u * b, (unsigned)(n / nbuf) & 1u, limit, abort))) {
+            if (lane == 0 && !*abort) {
+                for (int k = 0; k < B.n; ++k) atomicOr(B.err[k], (unsigned)PGM_ERR_TIMEOUT);
+                *abort = 1;
+            }
+            break;
+        }
+        const RowHdr H = hdr[b];
+        const RowGeom& G = geom[H.dir];
+        const DirLvl& D = B.d[H.pair][H.dir];
+        const int P = PC > 0 ? PC : G.P, h = P / 2;
+        const unsigned buf = a_sm + 4u * (unsigned)(b * buf_words);
+        const unsigned a_rn = buf, a_rs = buf + 4u * (unsigned)G.off_rs;
+        const unsigned a_wn = buf + 4u * (unsigned)G.off_win, a_ws = buf + 4u * (unsigned)G.off_ws;
+        const RowRec R = rec[b][lane];
+        const int s = R.s, Rf = R.f, Ru = R.u, px = R.px, py = R.py;
+        bool have = s >= 0 && (Rf & F_VALID);
+        const bool idle = s < 0 || (!have && R.nb0 == NO_CAND && R.nb1 == NO_CAND);
+        // round 1: the candidates known at staging time
+        bool ok[PS_NC];
+        int slot[PS_NC], qx[PS_NC], qy[PS_NC];
+        ok[0] = !idle && mc.refresh && have;
+        slot[0] = R.wu;
+        qx[0] = px + lo16((uint32_t)Ru); qy[0] = py + hi16((uint32_t)Ru);
+        ok[1] = !idle && R.nb0 != NO_CAND;
+        slot[1] = R.w0;
+        qx[1] = px + lo16((uint32_t)R.nb0); qy[1] = py + hi16((uint32_t)R.nb0);
+        ok[2] = !idle && R.nb1 != NO_CAND;
+        slot[2] = R.w1;
+        qx[2] = px + lo16((uint32_t)R.nb1); qy[2] = py + hi16((uint32_t)R.nb1);
+        ok[3] = !idle && R.wr0 != -2;
+        slot[3] = R.wr0;
+        qx[3] = qx[0] + lo16((uint32_t)R.r0); qy[3] = qy[0] + hi16((uint32_t)R.r0);
+        ok[4] = !idle && R.wr1 != -2;
+        slot[4] = R.wr1;
+        qx[4] = qx[0] + lo16((uint32_t)R.r1); qy[4] = qy[0] + hi16((uint32_t)R.r1);
+        const int rbit = H.shr + (px - h - H.rx0) * NCH, rrow = py - h - H.ry0;
+        unsigned c[PS_NC];
+        ps_rows<NCH, PS_NC>(G, H, D, P, a_rn, a_rs, a_wn, a_ws, rbit, rrow, ok, slot, qx, qy, fac, c);
+        unsigned n_eval = 0, n_cost = 0, n_glob = 0;
+        // the decisions in the paper's order
+        unsigned bc = have && !mc.refresh ? (unsigned)R.cost : INF32;
+        int32_t bu = Ru;
+        if (ok[0]) { bc = c[0]; ++n_cost; n_glob += slot[0] < 0; }
+        if (ok[1]) {
+            ++n_eval; n_glob += slot[1] < 0;
+            if (c[1] < bc) { bc = c[1]; bu = R.nb0; have = true; }
+        }
+        if (ok[2]) {
+            ++n_eval; n_glob += slot[2] < 0;
+            if (c[2] < bc) { bc = c[2]; bu = R.nb1; have = true; }
+        }
+        const int K = idle ? 0 : R.K;
+        int k2 = K;                   // the first search candidate of round 2
+        const int cx0 = lo16((uint32_t)bu), cy0 = hi16((uint32_t)bu);
+        if (have && K > 0) {
+            if (bu == Ru && (Rf & F_VALID)) {        // centre = current match: round 1 scored them
+#pragma unroll
+                for (int j = 3; j < 5; ++j) {
+                    if (!ok[j]) continue;
+                    ++n_eval; n_glob += slot[j] < 0;
+                    if (c[j] < bc) {
+                        bc = c[j];
+                        bu = pack_u(qx[j] - px, qy[j] - py);
+                    }
+                }
+                k2 = 2;
+            } else {
+                k2 = 0;
+            }
+        }
+        // round 2: the rest of the limited random search, one candidate per step
+        const int rbit2 = rbit, rrow2 = rrow;
+        for (int k = k2;; ++k) {
+            const bool live = have && k < K;
+            if (!__any_sync(FULL, live)) break;
+            bool ok2[1] = {false};
+            int sl2[1] = {-1}, qx2[1] = {0}, qy2[1] = {0};
+            int dx = 0, dy = 0;
+            if (live) {
+                if (k < 2) {
+                    const uint32_t o = (uint32_t)(k ? R.r1 : R.r0);
+                    dx = lo16(o);
+                    dy = hi16(o);
+                } else {
+                    const uint4 rq = philox(
+                        make_uint4((uint32_t)s,
+                                   ((uint32_t)B.visit << 16) | ((uint32_t)H.dir << 15) | (uint32_t)mc.t,
+                                   ((uint32_t)B.level << 16) | (uint32_t)(k >> 1),
+                                   B.stream_id[H.pair]),
+                        mc.key0, mc.key1);
+                    dx = rs_off((k & 1) ? rq.z : rq.x, k, mc.rs_W, mc.rs_mode);
+                    dy = rs_off((k & 1) ? rq.w : rq.y, k, mc.rs_W, mc.rs_mode);
+                }
+                qx2[0] = px + cx0 + dx;
+                qy2[0] = py + cy0 + dy;
+                ok2[0] = !(dx == 0 && dy == 0) && inside(D, qx2[0], qy2[0]);
+                if (ok2[0]) sl2[0] = pr_slot<true>(G, H, P, qx2[0], qy2[0]);
+            }
+            unsigned c2[1];
+            ps_rows<NCH, 1>(G, H, D, P, a_rn, a_rs, a_wn, a_ws, rbit2, rrow2, ok2, sl2, qx2, qy2, fac, c2);
+            if (ok2[0]) {
+                ++n_eval; n_glob += sl2[0] < 0;
+                if (c2[0] < bc) { bc = c2[0]; bu = pack_u(cx0 + dx, cy0 + dy); }
+            }
+        }
+        if (!idle) {
+            if (have && (mc.refresh || bu != Ru || !(Rf & F_VALID))) {
+                D.u[s] = bu;
+                D.cost[s] = (unsigned long long)bc;
+                D.flags[s] = (uint8_t)(Rf | F_VALID);
+            } else if (!have && Rf != R.f0) {
+                D.flags[s] = (uint8_t)Rf;
+            }
+        } else if (s >= 0 && Rf != R.f0) {
+            D.flags[s] = (uint8_t)Rf;                 // the refresh dropped it
+        }
+        n_eval = __reduce_add_sync(FULL, n_eval);
+        n_cost = __reduce_add_sync(FULL, n_cost);
+        n_glob = __reduce_add_sync(FULL, n_glob);
+        if (lane == 0) {
+            if (n_eval) atomicAdd(B.evals[H.pair] + H.dir, (unsigned long long)n_eval);
+            if (n_cost) atomicAdd(B.evals[H.pair] + 2 + H.dir, (unsigned long long)n_cost);
+            if (n_glob) atomicAdd(B.evals[H.pair] + 6 + H.dir, (unsigned long long)n_glob);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty0 + 8u * b);          // the tile's buffer is free again
+    }
+}
+
+template <int NCH, int PC>
+__global__ void __launch_bounds__(32 * (PS_PROD + PS_CONS), 1)
+k_pm_s(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_constant__ RowSched S,
+       const __grid_constant__ RowMaps TM, const int buf_words, const int nbuf,
+       const long long limit) {
+    extern __shared__ __align__(128) uint32_t sm[];
+    __shared__ RowRec s_rec[PS_NBUF][PR_NACT];
+    __shared__ RowHdr s_hdr[PS_NBUF];
+    __shared__ RowGeom s_geom[2];
+    __shared__ __align__(8) unsigned long long s_full[PS_NBUF], s_empty[PS_NBUF];
+    __shared__ int s_next[PS_NBUF];
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned a_sm = (unsigned)__cvta_generic_to_shared(sm);
+    const unsigned full0 = (unsigned)__cvta_generic_to_shared(&s_full[0]);
+    const unsigned empty0 = (unsigned)__cvta_generic_to_shared(&s_empty[0]);
+    if (threadIdx.x < 2)
+        s_geom[threadIdx.x] = rg_geom_bits(NCH, B.d[0][threadIdx.x].P, mc.sigma, mc.rs_W, mc.slack,
+                                           mc.tile_w);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < nbuf; ++b) {
+            mbar_init(full0 + 8u * b, 1);
+            mbar_init(empty0 + 8u * b, 1);             // one consumer warp per tile
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    volatile int* abort = &s_abort;
+    if (warp >= PS_CONS)
+        pr_produce<NCH, true, PS_PROD, PS_NBUF>(B, mc, S, TM, buf_words, nbuf, a_sm, s_rec, s_hdr,
+                                                s_next, s_geom, full0, empty0, abort, limit,
+                                                warp - PS_CONS, lane);
+    else
+        ps_consume<NCH, PC>(B, mc, S, buf_words, nbuf, a_sm, s_rec, s_hdr, s_geom, full0, empty0,
+                            abort, limit, warp, lane);
+}
+
 // Host side: launch configuration.  No device code below this line.
 
 // The kernel's parameters (batch, constants, schedule, tensor maps, scalars)
@@ -1159,17 +1442,28 @@ long long wait_limit();
 template <int NCH, int PC, bool BITS = false>
 pgm_status launch_r(const LvlBatch& B, const MatchConst& mc, const RowSched& S, const RowMaps& TM,
                     int buf_words, cudaStream_t st) {
-    const int most = BITS ? PB_NBUF : PR_NBUF;
-    int nbuf = 2;
-    while (nbuf < most && (nbuf + 1L) * buf_words * 4 <= 200L * 1024) ++nbuf;
-    const int smem = nbuf * buf_words * 4;
-    auto kern = k_pm_r<NCH, PC>;
-    if constexpr (BITS) kern = k_pm_b<NCH, PC>;
-    if (pgm_status r = smem_opt_in((const void*)kern); r != PGM_OK) return r;
     const int sms = device_sms();
     if (sms <= 0) return cuda_fail("search: SM count", cudaErrorInvalidDevice);
+    // bit planes: one seed per lane once every consumer warp of a CTA has
+    // tiles of its own, else the warp-per-seed form (coarse levels)
+    const bool per_lane = BITS && S.total >= PS_CONS * sms;
+    auto kern = k_pm_r<NCH, PC>;
+    if constexpr (BITS) kern = per_lane ? k_pm_s<NCH, PC> : k_pm_b<NCH, PC>;
+    if (pgm_status r = smem_opt_in((const void*)kern); r != PGM_OK) return r;
+    // the ring: as many buffers as fit beside the kernel's static shared
+    // memory (the bit-plane kernel's tile records take about 33 KB)
+    cudaFuncAttributes fa;
+    PGM_TRY(cudaFuncGetAttributes(&fa, (const void*)kern), "search: kernel attributes");
+    const int most = BITS ? (per_lane ? PS_NBUF : PB_NBUF) : PR_NBUF;
+    const long cap = fa.maxDynamicSharedSizeBytes < 200 * 1024 ? fa.maxDynamicSharedSizeBytes
+                                                               : 200L * 1024;
+    if (2L * buf_words * 4 > cap) return PGM_ERR_UNSUPPORTED;
+    int nbuf = 2;
+    while (nbuf < most && (nbuf + 1L) * buf_words * 4 <= cap) ++nbuf;
+    const int smem = nbuf * buf_words * 4;
     const int grid = S.total < sms ? S.total : sms;       // one CTA per SM (shared memory)
-    const int threads = BITS ? 32 * (PB_PROD + PB_CONS) : 32 * (PR_PROD + pr_cons(NCH, PC));
+    const int threads = !BITS ? 32 * (PR_PROD + pr_cons(NCH, PC))
+                        : per_lane ? 32 * (PS_PROD + PS_CONS) : 32 * (PB_PROD + PB_CONS);
     kern<<<grid, threads, smem, st>>>(B, mc, S, TM, buf_words, nbuf, wait_limit());
     return launch_status("search: launch");
 }
