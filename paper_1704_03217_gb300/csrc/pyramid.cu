@@ -299,22 +299,36 @@ __global__ void __launch_bounds__(SB_TW * SB_TY) k_sobel(const __grid_constant__
 // the sign bit-plane from the padded descriptor (bit b = x nch + c holds
 // value c of padded pixel x; words past the row are zero).  One thread per
 // word of one image (blockIdx.z).
-__global__ void k_bits(const __grid_constant__ PyrBatch B, int nch, int pxe) {
+template <int NCH>
+__global__ void k_bits(const __grid_constant__ PyrBatch B) {
+    constexpr int PXE = 2 * px_words(NCH);       // int16 elements per padded pixel
     const PyrItem& it = B.it[blockIdx.z];
     const int w = blockIdx.x * blockDim.x + threadIdx.x, yy = blockIdx.y * blockDim.y + threadIdx.y;
     const int pw = it.sw + 2 * BORD, ph = it.sh + 2 * BORD;
     if (w >= it.brow || yy >= ph) return;
     // padded pixel x of row yy: it.dst points at pixel (0, 0), rows drow int16
     const int16_t* row = reinterpret_cast<const int16_t*>(it.dst) + (ptrdiff_t)(yy - BORD) * it.drow -
-                         (ptrdiff_t)BORD * pxe;
+                         (ptrdiff_t)BORD * PXE;
     uint32_t nz = 0, sg = 0;
-    const int b0 = 32 * w;
-    for (int k = 0; k < 32; ++k) {
-        const int b = b0 + k, x = b / nch, c = b - x * nch;
-        if (x >= pw) break;
-        const int v = row[(ptrdiff_t)x * pxe + c];
-        nz |= (uint32_t)(v != 0) << k;
-        sg |= (uint32_t)(v < 0) << k;
+    const int b0 = 32 * w, x0 = b0 / NCH, x1 = min((b0 + 31) / NCH, pw - 1);
+    for (int x = x0; x <= x1; ++x) {           // whole pixels, one vector load each
+        int v[NCH];
+        if constexpr (NCH == 6) {
+            const uint4 q = *reinterpret_cast<const uint4*>(row + (ptrdiff_t)x * PXE);
+            v[0] = (int16_t)(q.x & 0xffff); v[1] = (int16_t)(q.x >> 16);
+            v[2] = (int16_t)(q.y & 0xffff); v[3] = (int16_t)(q.y >> 16);
+            v[4] = (int16_t)(q.z & 0xffff); v[5] = (int16_t)(q.z >> 16);
+        } else {
+            const uint32_t q = *reinterpret_cast<const uint32_t*>(row + (ptrdiff_t)x * PXE);
+            v[0] = (int16_t)(q & 0xffff); v[1] = (int16_t)(q >> 16);
+        }
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int k = x * NCH + c - b0;
+            if (k < 0 || k >= 32) continue;
+            nz |= (uint32_t)(v[c] != 0) << k;
+            sg |= (uint32_t)(v[c] < 0) << k;
+        }
     }
     it.bits[(size_t)yy * it.brow + w] = nz;
     it.bits[(size_t)(ph + yy) * it.brow + w] = sg;
@@ -414,8 +428,9 @@ pgm_status launch_pyramid_batch(const pgm_params* p, int n, const PyrPlan* plans
                         it.brow = pp.bit_row[l];
                         mb = pp.bit_row[l] > mb ? pp.bit_row[l] : mb;
                     }
-                    k_bits<<<dim3((mb + 31) / 32, (mh + 2 * BORD + 7) / 8, m), dim3(32, 8), 0, st>>>(
-                        B, 2 * C, 2 * px_words(2 * C));
+                    const dim3 gb((mb + 31) / 32, (mh + 2 * BORD + 7) / 8, m);
+                    if (C == 3) k_bits<6><<<gb, dim3(32, 8), 0, st>>>(B);
+                    else k_bits<2><<<gb, dim3(32, 8), 0, st>>>(B);
                 }
             }
         if (pgm_status r = launch_status("pyramid: launch"); r != PGM_OK) return r;
