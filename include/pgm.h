@@ -342,6 +342,13 @@ pgm_status pgm_get_tuning(pgm_tuning* t);
  * makes the first wait run out).  Errors: PGM_ERR_ARG (cycles < 0). */
 pgm_status pgm_set_wait_limit(int64_t cycles);
 
+/* 1 in the checked build (libpgm_checked.so, compiled with -DPGM_CHECKED):
+ * the search, initialisation and consistency kernels check their shared-
+ * and global-memory indices; a failed check sets PGM_ERR_DEVICE_BOUNDS in the
+ * workspace status word (pgm_sync_status) and skips the access.  0 in the
+ * regular build, where the checks compile away. */
+int pgm_checked_build(void);
+
 /* Nominal candidate evaluations of one pair under params (2 propagation + K
  * random-search candidates per seed and iteration, one cost per seed and
  * visit, both directions; the exhaustive init is not counted). */

@@ -6,7 +6,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libpgm.so")
+# PGM_CHECKED=1: the build with device index checks (build(checked=True))
+LIB_PATH = os.path.join(HERE, "_build", "libpgm_checked.so" if os.environ.get("PGM_CHECKED") == "1"
+                        else "libpgm.so")
 
 PARAM_FIELDS = [
     ("levels", 3), ("seed_stride", 3), ("patch_fwd", 15), ("patch_bwd", 11), ("sobel", 5),
@@ -34,7 +36,7 @@ EXPORTS = [
     "pgm_nominal_evals", "pgm_launch_count", "pgm_profile_enable", "pgm_profile_read",
     "pgm_filter_noalloc", "pgm_build_pyramid_batch", "pgm_filter_batch", "pgm_set_tuning",
     "pgm_get_tuning", "pgm_set_wait_limit", "pgm_error_detail", "pgm_interp_default_params",
-    "pgm_interp_workspace_bytes", "pgm_interpolate",
+    "pgm_interp_workspace_bytes", "pgm_interpolate", "pgm_checked_build",
 ]
 
 
@@ -97,6 +99,7 @@ def load(path: str = LIB_PATH):
     L.pgm_set_tuning.argtypes = [C.POINTER(CTuning)]; L.pgm_set_tuning.restype = C.c_int
     L.pgm_get_tuning.argtypes = [C.POINTER(CTuning)]; L.pgm_get_tuning.restype = C.c_int
     L.pgm_set_wait_limit.argtypes = [C.c_int64]; L.pgm_set_wait_limit.restype = C.c_int
+    L.pgm_checked_build.argtypes = []; L.pgm_checked_build.restype = C.c_int
     L.pgm_interp_default_params.argtypes = [C.POINTER(CInterp)]; L.pgm_interp_default_params.restype = None
     L.pgm_interp_workspace_bytes.argtypes = [i32, i32, C.POINTER(CInterp)]
     L.pgm_interp_workspace_bytes.restype = C.c_size_t

@@ -385,6 +385,12 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
                     np = B.d[k][d].rw * B.d[k][d].rh;
                     if (np > max_px) max_px = np;
                 }
+            // the direction descriptor's bit-plane kernels need no box sums;
+            // only a level whose search (or, at the coarsest, initialisation)
+            // falls back to the int16 kernels does
+            if (p->descriptor == PGM_DIR && pm_tile_fits(B, mc, nch) &&
+                (l != l0 || init_bits_fits(B)))
+                continue;
             const bool on_aux = l != l0 && aux;
             pgm_status r = launch_box(B, nch, max_px, on_aux ? aux->s : st);
             if (r != PGM_OK) return r;
@@ -793,6 +799,14 @@ pgm_status pgm_get_tuning(pgm_tuning* t) {
 int64_t pgm_launch_count(void) { return (int64_t)g_launches.load(); }
 
 const char* pgm_error_detail(void) { return g_detail; }
+
+int pgm_checked_build(void) {
+#ifdef PGM_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 pgm_status pgm_profile_enable(int on) {
     if (on) {

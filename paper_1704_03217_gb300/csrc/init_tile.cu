@@ -231,10 +231,12 @@ __global__ void __launch_bounds__(IN_THREADS) k_init_b(const __grid_constant__ L
 #pragma unroll
             for (int p = 0; p < IN_PB; ++p) {
                 uint32_t vn[NW], vs[NW], tn[NR], ts[NR];
+                const bool in = PGM_CHECK(base[p] >= 0 && base[p] + r * trow + NW <= tplane,
+                                          B.err[pair]);
 #pragma unroll
                 for (int i = 0; i < NW; ++i) {
-                    vn[i] = sT[base[p] + r * trow + i];
-                    vs[i] = sT[tplane + base[p] + r * trow + i];
+                    vn[i] = in ? sT[base[p] + r * trow + i] : 0u;
+                    vs[i] = in ? sT[tplane + base[p] + r * trow + i] : 0u;
                 }
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
@@ -306,24 +308,38 @@ pgm_status launch_ib(const LvlBatch& B, const MatchConst& mc, int groups, int sm
 
 }  // namespace
 
+// shared words of the bit-plane initialisation: the target's two padded
+// planes and IB_SB seeds' reference rows
+static int ib_words(const DirLvl& D) {
+    return 2 * D.tbit_row * (D.th + 2 * BORD) + IB_SB * 2 * D.P * 3;
+}
+
+bool init_bits_fits(const LvlBatch& B) {
+    for (int k = 0; k < B.n; ++k)
+        for (int d = 0; d < 2; ++d) {
+            const DirLvl& D = B.d[k][d];
+            if (!D.ref_bits || !D.tgt_bits || D.rbit_row <= 0 || D.tbit_row <= 0 ||
+                D.P > 2 * BORD + 1 || 4L * ib_words(D) > 200L * 1024)
+                return false;
+        }
+    return true;
+}
+
 // *handled = false (nothing launched) when the cost is not squared L2 or a
 // target image with its border does not fit in shared memory.
 pgm_status launch_init_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
                             cudaStream_t st) {
     *handled = false;
-    if (mc.descriptor == PGM_DIR) {             // the bit-plane form, any norm
+    if (mc.descriptor == PGM_DIR && init_bits_fits(B)) {     // the bit-plane form, any norm
         int words = 0, seeds = 0;
-        bool planes = true;
         for (int k = 0; k < B.n; ++k)
             for (int d = 0; d < 2; ++d) {
                 const DirLvl& D = B.d[k][d];
-                planes = planes && D.ref_bits && D.tgt_bits && D.rbit_row > 0 && D.tbit_row > 0 &&
-                         D.P <= 2 * BORD + 1;
-                const int w = 2 * D.tbit_row * (D.th + 2 * BORD) + IB_SB * 2 * D.P * 3;
+                const int w = ib_words(D);
                 if (w > words) words = w;
                 if (D.nx * D.ny > seeds) seeds = D.nx * D.ny;
             }
-        if (planes && 4L * words <= 200L * 1024) {
+        {
             *handled = true;
             if (seeds == 0) return PGM_OK;
             const int groups = (seeds + IB_SB - 1) / IB_SB;

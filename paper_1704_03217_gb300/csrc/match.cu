@@ -563,7 +563,7 @@ __global__ void k_consist(const __grid_constant__ LvlBatch B, const MatchConst m
         a = (a >= 0 ? a : a - mc.sigma + 1) / mc.sigma;     // floor division
         b = (b >= 0 ? b : b - mc.sigma + 1) / mc.sigma;
         const int g = clampi(b, 0, D.ony - 1) * D.onx + clampi(a, 0, D.onx - 1);
-        if (D.oflags[g] & F_VALID) {
+        if (PGM_CHECK(g >= 0 && g < D.onx * D.ony, B.err[pair]) && (D.oflags[g] & F_VALID)) {
             const int32_t ou = D.ou[g];
             const int ex = ux + lo16(ou), ey = uy + hi16(ou);
             out = (long long)ex * ex + (long long)ey * ey > (long long)mc.tau2;

@@ -169,6 +169,17 @@ struct MatchConst {              // scalars common to one launch
 struct Tuning { int slack; int chunk; int tile_w; };
 Tuning tuning();
 
+// Device index checks of the checked build (-DPGM_CHECKED, libpgm_checked.so):
+// a check that fails records PGM_ERR_DEVICE_BOUNDS in the status word errp
+// and evaluates to false, so the caller skips the access.  In the regular
+// build a check is the constant true.
+#ifdef PGM_CHECKED
+#define PGM_CHECK(cond, errp) \
+    ((cond) ? true : (atomicOr((errp), (unsigned)PGM_ERR_DEVICE_BOUNDS), false))
+#else
+#define PGM_CHECK(cond, errp) true
+#endif
+
 // A host-side NVTX push/pop range: names the entry point and, inside
 // pgm_match, the visit's level on a profiler's timeline (and lets a profiler
 // select the kernels of one level).  Costs a pointer test when no tool is
@@ -231,6 +242,9 @@ pgm_status launch_init_tile(const LvlBatch& B, const MatchConst& mc, int nch, bo
 // true when the tile search kernel takes this batch (it then also does the
 // cost refresh of a visit's first iteration, MatchConst::refresh)
 bool pm_tile_fits(const LvlBatch& B, const MatchConst& mc, int nch);
+// init_tile.cu: the bit-plane initialisation takes this batch (planes present,
+// staged target fits in shared memory)
+bool init_bits_fits(const LvlBatch& B);
 // true when the tile search kernel takes this batch with one launch per
 // direction (phases larger than one tile per resident CTA)
 bool pm_tile_split(const LvlBatch& B, const MatchConst& mc, int nch);

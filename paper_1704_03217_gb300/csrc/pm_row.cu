@@ -562,8 +562,11 @@ __device__ void pr_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
             // this lane's reference words (zero for pixels past the patch)
             int ra[M][WPP];
             {
-                const unsigned rbase = buf + 4u * (unsigned)((py - h - H.ry0) * G.sp + H.shr +
-                                                             (px - h - H.rx0) * PXW);
+                const int roff = (py - h - H.ry0) * G.sp + H.shr + (px - h - H.rx0) * PXW;
+                const bool rok = PGM_CHECK(py - h - H.ry0 >= 0 && px - h - H.rx0 >= 0 &&
+                                           roff + (P - 1) * G.sp + P * PXW <= G.sp * G.ref_h,
+                                           B.err[H.pair]);
+                const unsigned rbase = buf + 4u * (unsigned)(rok ? roff : 0);
 #pragma unroll
                 for (int m = 0; m < M; ++m) {
                     const int keep = (vmask >> m) & 1u ? -1 : 0;
@@ -583,11 +586,21 @@ __device__ void pr_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
                 int l[3] = {0, 0, 0}, hh[3] = {0, 0, 0};
                 unsigned long long sb;
                 if (slot >= 0) {
-                    pr_acc_sh<NCH, M>(ra, off, a_win + 4u * (unsigned)(slot & 0xffff), l, hh);
-                    sb = lds64(a_sb + 8u * (unsigned)(slot >> 16));
+                    if (PGM_CHECK((slot & 0xffff) + (P - 1) * G.sp + P * PXW <= G.sp * G.win_h &&
+                                  (slot >> 16) < G.cwp * G.ch, B.err[H.pair])) {
+                        pr_acc_sh<NCH, M>(ra, off, a_win + 4u * (unsigned)(slot & 0xffff), l, hh);
+                        sb = lds64(a_sb + 8u * (unsigned)(slot >> 16));
+                    } else {
+                        sb = 0;
+                    }
                 } else {
-                    pr_acc_glob<NCH, M>(ra, t32, tpw, qx - h, qy - h, P, lane, l, hh);
-                    sb = D.sb2[(size_t)qy * D.sbp + qx];
+                    if (PGM_CHECK(qx >= 0 && qy >= 0 && qx < D.tw && qy < D.th && h <= BORD,
+                                  B.err[H.pair])) {
+                        pr_acc_glob<NCH, M>(ra, t32, tpw, qx - h, qy - h, P, lane, l, hh);
+                        sb = D.sb2[(size_t)qy * D.sbp + qx];
+                    } else {
+                        sb = 0;
+                    }
                     if (lane == 0) ++n_glob;
                 }
                 const int sl = __reduce_add_sync(FULL, l[0] + l[1] + l[2]);
@@ -1000,7 +1013,8 @@ __device__ __forceinline__ void ps_rows(const RowGeom& G, const RowHdr& H, const
                                         unsigned a_rn, unsigned a_rs, unsigned a_wn, unsigned a_ws,
                                         int rbit, int rrow, const bool (&ok)[NC],
                                         const int (&slot)[NC], const int (&qx)[NC],
-                                        const int (&qy)[NC], unsigned fac, unsigned (&c)[NC]) {
+                                        const int (&qy)[NC], unsigned fac, unsigned (&c)[NC],
+                                        uint32_t* errp) {
     constexpr int NR = NCH == 6 ? 3 : 1, NW = NR + 1;
     const int h = P / 2;
     const int tplane = D.tbit_row * (D.th + 2 * BORD);
@@ -1014,10 +1028,13 @@ __device__ __forceinline__ void ps_rows(const RowGeom& G, const RowHdr& H, const
     unsigned base[NC];
     const uint32_t* gp[NC];
     int sh[NC];
-    bool sm_[NC];
+    bool sm_[NC], rd[NC];
+    const bool rok = PGM_CHECK(rrow >= 0 && rrow + P <= G.ref_h && rbit >= 0 &&
+                               (rbit >> 5) + NW <= G.bwr, errp);
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         c[j] = 0;
+        rd[j] = ok[j] && rok;
         sm_[j] = ok[j] && slot[j] >= 0;
         base[j] = 0;
         gp[j] = D.tgt_bits;
@@ -1026,7 +1043,11 @@ __device__ __forceinline__ void ps_rows(const RowGeom& G, const RowHdr& H, const
             const int bit = H.shw + (slot[j] & 0xffff) * NCH;
             sh[j] = bit & 31;
             base[j] = 4u * (unsigned)((slot[j] >> 16) * G.bww + (bit >> 5));
+            rd[j] = rd[j] && PGM_CHECK((slot[j] >> 16) + P <= G.win_h && (bit >> 5) + NW <= G.bww,
+                                       errp);
         } else if (ok[j]) {
+            rd[j] = rd[j] && PGM_CHECK(qx[j] >= 0 && qy[j] >= 0 && qx[j] < D.tw && qy[j] < D.th &&
+                                       h <= BORD, errp);
             const int bit = (qx[j] - h + BORD) * NCH;
             sh[j] = bit & 31;
             gp[j] = D.tgt_bits + (size_t)(qy[j] - h + BORD) * D.tbit_row + (bit >> 5);
@@ -1052,7 +1073,7 @@ __device__ __forceinline__ void ps_rows(const RowGeom& G, const RowHdr& H, const
         rb += 4u * (unsigned)G.bwr;
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
-            if (!ok[j]) continue;
+            if (!rd[j]) continue;
             unsigned vn[NW], vs[NW];
             if (sm_[j]) {
 #pragma unroll
@@ -1127,9 +1148,13 @@ __device__ void ps_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
         ok[4] = !idle && R.wr1 != -2;
         slot[4] = R.wr1;
         qx[4] = qx[0] + lo16((uint32_t)R.r1); qy[4] = qy[0] + hi16((uint32_t)R.r1);
-        const int rbit = H.shr + (px - h - H.rx0) * NCH, rrow = py - h - H.ry0;
+        // a lane without a seed (a tile at the lattice edge) still walks the
+        // rows with its warp: its reference position is the region's corner
+        const int rbit = idle ? 0 : H.shr + (px - h - H.rx0) * NCH;
+        const int rrow = idle ? 0 : py - h - H.ry0;
         unsigned c[PS_NC];
-        ps_rows<NCH, PS_NC>(G, H, D, P, a_rn, a_rs, a_wn, a_ws, rbit, rrow, ok, slot, qx, qy, fac, c);
+        ps_rows<NCH, PS_NC>(G, H, D, P, a_rn, a_rs, a_wn, a_ws, rbit, rrow, ok, slot, qx, qy, fac, c,
+                            B.err[H.pair]);
         unsigned n_eval = 0, n_cost = 0, n_glob = 0;
         // the decisions in the paper's order
         unsigned bc = have && !mc.refresh ? (unsigned)R.cost : INF32;
@@ -1191,7 +1216,8 @@ __device__ void ps_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
                 if (ok2[0]) sl2[0] = pr_slot<true>(G, H, P, qx2[0], qy2[0]);
             }
             unsigned c2[1];
-            ps_rows<NCH, 1>(G, H, D, P, a_rn, a_rs, a_wn, a_ws, rbit2, rrow2, ok2, sl2, qx2, qy2, fac, c2);
+            ps_rows<NCH, 1>(G, H, D, P, a_rn, a_rs, a_wn, a_ws, rbit2, rrow2, ok2, sl2, qx2, qy2, fac, c2,
+                            B.err[H.pair]);
             if (ok2[0]) {
                 ++n_eval; n_glob += sl2[0] < 0;
                 if (c2[0] < bc) { bc = c2[0]; bu = pack_u(cx0 + dx, cy0 + dy); }
