@@ -25,53 +25,82 @@ __device__ __forceinline__ int gray_q14(int r, int g, int b) {
 // largest image and blocks outside an image's extent return.
 
 // ---------------------------------------------------------------- level 0
-// mode 0: gray input copied; mode 1: RGB -> gray; mode 2: RGB -> 3 planes
+// mode 0: gray input copied; mode 1: RGB -> gray; mode 2: RGB -> 3 planes.
+// A thread makes 4 consecutive pixels (one 32-bit store per output plane;
+// level rows are 16-byte aligned).
 __global__ void k_level0(const __grid_constant__ PyrBatch B) {
     const PyrItem& it = B.it[blockIdx.z];
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= it.sw || y >= it.sh) return;
     const uint8_t* src = it.src + (size_t)y * it.pitch;
     uint8_t* out = it.dst;
     const size_t o = (size_t)y * it.drow + x;
-    if (it.mode == 0) {
-        out[o] = src[x];
-    } else {
-        int r = src[3 * x], g = src[3 * x + 1], b = src[3 * x + 2];
-        if (it.mode == 1) {
-            out[o] = (uint8_t)gray_q14(r, g, b);
+    const int n = it.sw - x < 4 ? it.sw - x : 4;
+    uint32_t p0 = 0, p1 = 0, p2 = 0;
+    for (int k = 0; k < n; ++k) {
+        if (it.mode == 0) {
+            p0 |= (uint32_t)src[x + k] << (8 * k);
         } else {
-            out[o] = (uint8_t)r;
-            out[it.dplane + o] = (uint8_t)g;
-            out[2 * it.dplane + o] = (uint8_t)b;
+            const int r = src[3 * (x + k)], g = src[3 * (x + k) + 1], b = src[3 * (x + k) + 2];
+            if (it.mode == 1) {
+                p0 |= (uint32_t)gray_q14(r, g, b) << (8 * k);
+            } else {
+                p0 |= (uint32_t)r << (8 * k);
+                p1 |= (uint32_t)g << (8 * k);
+                p2 |= (uint32_t)b << (8 * k);
+            }
+        }
+    }
+    if (n == 4) {
+        *reinterpret_cast<uint32_t*>(out + o) = p0;
+        if (it.mode == 2) {
+            *reinterpret_cast<uint32_t*>(out + it.dplane + o) = p1;
+            *reinterpret_cast<uint32_t*>(out + 2 * it.dplane + o) = p2;
+        }
+    } else {
+        for (int k = 0; k < n; ++k) {
+            out[o + k] = (uint8_t)(p0 >> (8 * k));
+            if (it.mode == 2) {
+                out[it.dplane + o + k] = (uint8_t)(p1 >> (8 * k));
+                out[2 * it.dplane + o + k] = (uint8_t)(p2 >> (8 * k));
+            }
         }
     }
 }
 
 // ------------------------------------------------------- binomial down
-// One output pixel per thread; blockIdx.z = image * C + channel.  The
-// separable sums are exact integers, so summing rows first equals the 2D sum
-// of the definition.
-__global__ void k_down(const __grid_constant__ PyrBatch B, int C) {
+// A CTA of 32 x 8 threads makes a 32 x 8 block of one output channel
+// (blockIdx.z = image * C + channel): the 68 x 20 input pixels it needs
+// (border replicated) go to shared memory, then the horizontal 5-tap sums at
+// the even columns, then the vertical sums.  The separable sums are exact
+// integers, so summing rows first equals the 2D sum of the definition.
+__global__ void __launch_bounds__(256) k_down(const __grid_constant__ PyrBatch B, int C) {
+    constexpr int OW = 32, OH = 8, IW = 2 * OW + 4, IH = 2 * OH + 4;
+    __shared__ uint8_t sI[IH][IW];
+    __shared__ int sH[IH][OW];
     const PyrItem& it = B.it[blockIdx.z / C];
     const int ch = blockIdx.z % C;
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= it.dw || y >= it.dh) return;
+    const int ox0 = blockIdx.x * OW, oy0 = blockIdx.y * OH;
+    if (ox0 >= it.dw || oy0 >= it.dh) return;           // the whole block (uniform)
     const uint8_t* src = it.src + ch * it.splane;
-    const int k[5] = {1, 4, 6, 4, 1};
-    int xs[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) xs[i] = clampi(2 * x + i - 2, 0, it.sw - 1);
-    int acc = 0;
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-        const uint8_t* r = src + (size_t)clampi(2 * y + j - 2, 0, it.sh - 1) * it.srow;
-        int s = 0;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) s += k[i] * r[xs[i]];
-        acc += k[j] * s;
+    const int ix0 = 2 * ox0 - 2, iy0 = 2 * oy0 - 2;
+    const int tid = threadIdx.y * OW + threadIdx.x;
+    for (int e = tid; e < IH * IW; e += OW * OH) {
+        const int r = e / IW, c = e - r * IW;
+        sI[r][c] = src[(size_t)clampi(iy0 + r, 0, it.sh - 1) * it.srow + clampi(ix0 + c, 0, it.sw - 1)];
     }
+    __syncthreads();
+    for (int e = tid; e < IH * OW; e += OW * OH) {
+        const int r = e / OW, c = e - r * OW;
+        const uint8_t* q = &sI[r][2 * c];
+        sH[r][c] = q[0] + 4 * q[1] + 6 * q[2] + 4 * q[3] + q[4];
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y, x = ox0 + tx, y = oy0 + ty;
+    if (x >= it.dw || y >= it.dh) return;
+    const int acc = sH[2 * ty][tx] + 4 * sH[2 * ty + 1][tx] + 6 * sH[2 * ty + 2][tx] +
+                    4 * sH[2 * ty + 3][tx] + sH[2 * ty + 4][tx];
     it.dst[ch * it.dplane + (size_t)y * it.drow + x] = (uint8_t)((acc + 128) >> 8);
 }
 
@@ -283,13 +312,23 @@ __global__ void __launch_bounds__(SB_TW * SB_TY) k_sobel(const __grid_constant__
         }
     } else {
         // a border pixel takes the words of the nearest image pixel, which
-        // lies in this tile
-        const int nxw = (xb - xa) * PXW, nrow = yb - ya;
-        for (int e = tid; e < 2 * nrow * nxw; e += NT) {
-            const int a = e / (nrow * nxw), rem = e - a * (nrow * nxw), r = rem / nxw, cw = rem - r * nxw;
-            const int y = ya + r, x = xa + cw / PXW, q = cw - (cw / PXW) * PXW;
-            const int sy = clampi(y, 0, h - 1) - y0, sx = clampi(x, 0, w - 1) - x0;
-            (a ? dst1 : dst0)[(ptrdiff_t)y * rw + (ptrdiff_t)x * PXW + q] = sO[a][sy][sx * PXW + q];
+        // lies in this tile; a warp walks one output row, a pixel per lane
+        // (colour pixels as one 16-byte store)
+        const int nx = xb - xa, nrow = yb - ya;
+        for (int r = ty; r < 2 * nrow; r += SB_TY) {
+            const int a = r >= nrow, y = ya + (a ? r - nrow : r);
+            const int sy = clampi(y, 0, h - 1) - y0;
+            uint32_t* const orow = (a ? dst1 : dst0) + (ptrdiff_t)y * rw;
+            for (int i = tx; i < nx; i += SB_TW) {
+                const int x = xa + i, sx = clampi(x, 0, w - 1) - x0;
+                if constexpr (PXW == 4) {
+                    *reinterpret_cast<uint4*>(orow + (ptrdiff_t)x * 4) =
+                        *reinterpret_cast<const uint4*>(&sO[a][sy][sx * 4]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < PXW; ++q) orow[(ptrdiff_t)x * PXW + q] = sO[a][sy][sx * PXW + q];
+                }
+            }
         }
     }
 }
@@ -368,7 +407,7 @@ pgm_status launch_pyramid_batch(const pgm_params* p, int n, const PyrPlan* plans
             it.mode = cs[base + k] == 1 ? 0 : (C == 1 ? 1 : 2);
             mw = pp.W[0] > mw ? pp.W[0] : mw; mh = pp.H[0] > mh ? pp.H[0] : mh;
         }
-        k_level0<<<grid(mw, mh, m), blk, 0, st>>>(B);
+        k_level0<<<grid((mw + 3) / 4, mh, m), blk, 0, st>>>(B);
         for (int l = 1; l < L; ++l) {
             mw = mh = 0;
             for (int k = 0; k < m; ++k) {
