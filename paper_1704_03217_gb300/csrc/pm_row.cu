@@ -569,7 +569,8 @@ __device__ void pr_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
                 const unsigned rbase = buf + 4u * (unsigned)(rok ? roff : 0);
 #pragma unroll
                 for (int m = 0; m < M; ++m) {
-                    const int keep = (vmask >> m) & 1u ? -1 : 0;
+                    // (pixel m of every lane lies in the patch for m < P^2 / 32)
+                    const int keep = (PC > 0 && m < (PC * PC) / 32) || ((vmask >> m) & 1u) ? -1 : 0;
                     if constexpr (NCH == 6) {
                         const uint4 v = lds128(rbase + off[m]);
                         ra[m][0] = (int)v.x & keep;
