@@ -70,37 +70,29 @@ __global__ void k_level0(const __grid_constant__ PyrBatch B) {
 }
 
 // ------------------------------------------------------- binomial down
-// A CTA of 32 x 8 threads makes a 32 x 8 block of one output channel
-// (blockIdx.z = image * C + channel): the 68 x 20 input pixels it needs
-// (border replicated) go to shared memory, then the horizontal 5-tap sums at
-// the even columns, then the vertical sums.  The separable sums are exact
-// integers, so summing rows first equals the 2D sum of the definition.
-__global__ void __launch_bounds__(256) k_down(const __grid_constant__ PyrBatch B, int C) {
-    constexpr int OW = 32, OH = 8, IW = 2 * OW + 4, IH = 2 * OH + 4;
-    __shared__ uint8_t sI[IH][IW];
-    __shared__ int sH[IH][OW];
+// One output pixel per thread; blockIdx.z = image * C + channel.  The
+// separable sums are exact integers, so summing rows first equals the 2D sum
+// of the definition.
+__global__ void k_down(const __grid_constant__ PyrBatch B, int C) {
     const PyrItem& it = B.it[blockIdx.z / C];
     const int ch = blockIdx.z % C;
-    const int ox0 = blockIdx.x * OW, oy0 = blockIdx.y * OH;
-    if (ox0 >= it.dw || oy0 >= it.dh) return;           // the whole block (uniform)
-    const uint8_t* src = it.src + ch * it.splane;
-    const int ix0 = 2 * ox0 - 2, iy0 = 2 * oy0 - 2;
-    const int tid = threadIdx.y * OW + threadIdx.x;
-    for (int e = tid; e < IH * IW; e += OW * OH) {
-        const int r = e / IW, c = e - r * IW;
-        sI[r][c] = src[(size_t)clampi(iy0 + r, 0, it.sh - 1) * it.srow + clampi(ix0 + c, 0, it.sw - 1)];
-    }
-    __syncthreads();
-    for (int e = tid; e < IH * OW; e += OW * OH) {
-        const int r = e / OW, c = e - r * OW;
-        const uint8_t* q = &sI[r][2 * c];
-        sH[r][c] = q[0] + 4 * q[1] + 6 * q[2] + 4 * q[3] + q[4];
-    }
-    __syncthreads();
-    const int tx = threadIdx.x, ty = threadIdx.y, x = ox0 + tx, y = oy0 + ty;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= it.dw || y >= it.dh) return;
-    const int acc = sH[2 * ty][tx] + 4 * sH[2 * ty + 1][tx] + 6 * sH[2 * ty + 2][tx] +
-                    4 * sH[2 * ty + 3][tx] + sH[2 * ty + 4][tx];
+    const uint8_t* src = it.src + ch * it.splane;
+    const int k[5] = {1, 4, 6, 4, 1};
+    int xs[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) xs[i] = clampi(2 * x + i - 2, 0, it.sw - 1);
+    int acc = 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const uint8_t* r = src + (size_t)clampi(2 * y + j - 2, 0, it.sh - 1) * it.srow;
+        int s = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) s += k[i] * r[xs[i]];
+        acc += k[j] * s;
+    }
     it.dst[ch * it.dplane + (size_t)y * it.drow + x] = (uint8_t)((acc + 128) >> 8);
 }
 
