@@ -244,7 +244,15 @@ __device__ __forceinline__ int pr_slot(const RowGeom& G, const RowHdr& H, int P,
 
 // Producer warp p: stage the CTA's tiles n = p, p + PR_PROD, ... (launch tiles
 // blockIdx.x + n * gridDim.x) into buffer n mod nbuf.
-template <int NCH, bool BITS, int NPROD, int NBUFMAX>
+// NG = 0: one full and one empty mbarrier per buffer; every consumer warp
+// takes every tile, so waits see the phases of a buffer one after another.
+// NG > 0: consumer agent g takes the tiles n = g (mod NG) and a buffer
+// rotates among agents and producers, so a parity wait could otherwise
+// skip a phase; buffer b then has a full barrier per agent (b NG + g, the
+// phases of that agent's tiles in b) and an empty barrier per producer
+// (b NPROD + p, released by the consumers of the tile before producer p's
+// next tile in b), and every wait is for the next phase of its barrier.
+template <int NCH, bool BITS, int NPROD, int NBUFMAX, int NG = 0>
 __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSched& S,
                            const RowMaps& TM, int buf_words, int nbuf, unsigned a_sm,
                            RowRec (*rec)[PR_NACT], RowHdr* hdr, int* next, const RowGeom* geom,
@@ -252,15 +260,18 @@ __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSch
                            int pw, int lane) {
     constexpr int PXW = px_words(NCH);
     int lastn[NBUFMAX];                      // the tile this warp last armed in each buffer
+    int waits[NBUFMAX];                      // NG > 0: waits so far on this warp's empty barrier of b
 #pragma unroll
-    for (int b = 0; b < NBUFMAX; ++b) lastn[b] = -1;
+    for (int b = 0; b < NBUFMAX; ++b) { lastn[b] = -1; waits[b] = 0; }
     for (int n = pw;; n += NPROD) {
         const int t = blockIdx.x + n * gridDim.x;
         if (t >= S.total) break;
         const int b = n % nbuf;
-        const unsigned full = full0 + 8u * b, empty = empty0 + 8u * b;
-        if (n >= nbuf) {            // every consumer warp released the buffer's last tile
-            const bool ok = __all_sync(FULL, mbar_wait(empty, (unsigned)((n / nbuf) - 1) & 1u, limit, abort));
+        const unsigned full = full0 + 8u * (NG > 0 ? (unsigned)(b * NG + n % NG) : (unsigned)b);
+        const unsigned empty = empty0 + 8u * (NG > 0 ? (unsigned)(b * NPROD + pw) : (unsigned)b);
+        if (n >= nbuf) {            // the consumers released the buffer's last tile
+            const unsigned par = NG > 0 ? (unsigned)(waits[b]++) & 1u : (unsigned)((n / nbuf) - 1) & 1u;
+            const bool ok = __all_sync(FULL, mbar_wait(empty, par, limit, abort));
             if (!ok) {
                 if (lane == 0 && !*abort) {
                     for (int k = 0; k < B.n; ++k) atomicOr(B.err[k], (unsigned)PGM_ERR_TIMEOUT);
@@ -433,9 +444,16 @@ __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSch
     // after an abort: let the copies this warp issued land before the CTA exits
     if (*abort)
         for (int b = 0; b < nbuf; ++b)
-            if (lastn[b] >= 0)
-                (void)mbar_wait(full0 + 8u * (unsigned)b, (unsigned)(lastn[b] / nbuf) & 1u,
-                                PR_DRAIN_CYCLES, nullptr);
+            if (lastn[b] >= 0) {
+                const int m = lastn[b];
+                unsigned bar = (unsigned)b, ph = (unsigned)(m / nbuf);
+                if (NG > 0) {             // the phase of tile m on its agent's barrier of b
+                    bar = (unsigned)(b * NG + m % NG);
+                    ph = 0;
+                    for (int q = b; q < m; q += nbuf) ph += q % NG == m % NG;
+                }
+                (void)mbar_wait(full0 + 8u * bar, ph & 1u, PR_DRAIN_CYCLES, nullptr);
+            }
 }
 
 // Partial cross products of one lane's pixels with the candidate patch whose
@@ -1109,11 +1127,15 @@ __device__ void ps_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
                            volatile int* abort, long long limit, int cw, int lane) {
     constexpr unsigned INF32 = 0xffffffffu;
     const unsigned fac = mc.norm == PGM_L2SQ ? 2u : 1u;      // 4 = 1 << 2, 2 = 1 << 1
+    int seen[PS_NBUF];                    // waits so far on this warp's full barrier of each buffer
+#pragma unroll
+    for (int b = 0; b < PS_NBUF; ++b) seen[b] = 0;
     for (int n = cw;; n += PS_CONS) {
         const int t = blockIdx.x + n * gridDim.x;
         if (t >= S.total) break;
         const int b = n % nbuf;
-        if (!__all_sync(FULL, mbar_wait(full0 + 8u * b, (unsigned)(n / nbuf) & 1u, limit, abort))) {
+        const unsigned fb = full0 + 8u * (unsigned)(b * PS_CONS + cw);
+        if (!__all_sync(FULL, mbar_wait(fb, (unsigned)(seen[b]++) & 1u, limit, abort))) {
             if (lane == 0 && !*abort) {
                 for (int k = 0; k < B.n; ++k) atomicOr(B.err[k], (unsigned)PGM_ERR_TIMEOUT);
                 *abort = 1;
@@ -1244,7 +1266,8 @@ __device__ void ps_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
             if (n_glob) atomicAdd(B.evals[H.pair] + 6 + H.dir, (unsigned long long)n_glob);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(empty0 + 8u * b);          // the tile's buffer is free again
+        if (lane == 0)                                         // the tile's buffer is free again
+            mbar_arrive(empty0 + 8u * (unsigned)(b * PS_PROD + (n + nbuf) % PS_PROD));
     }
 }
 
@@ -1257,7 +1280,7 @@ k_pm_s(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
     __shared__ RowRec s_rec[PS_NBUF][PR_NACT];
     __shared__ RowHdr s_hdr[PS_NBUF];
     __shared__ RowGeom s_geom[2];
-    __shared__ __align__(8) unsigned long long s_full[PS_NBUF], s_empty[PS_NBUF];
+    __shared__ __align__(8) unsigned long long s_full[PS_NBUF * PS_CONS], s_empty[PS_NBUF * PS_PROD];
     __shared__ int s_next[PS_NBUF];
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1268,9 +1291,9 @@ k_pm_s(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
         s_geom[threadIdx.x] = rg_geom_bits(NCH, B.d[0][threadIdx.x].P, mc.sigma, mc.rs_W, mc.slack,
                                            mc.tile_w);
     if (threadIdx.x == 0) {
-        for (int b = 0; b < nbuf; ++b) {
-            mbar_init(full0 + 8u * b, 1);
-            mbar_init(empty0 + 8u * b, 1);             // one consumer warp per tile
+        for (int b = 0; b < nbuf; ++b) {                 // per consumer and per producer
+            for (int g = 0; g < PS_CONS; ++g) mbar_init(full0 + 8u * (b * PS_CONS + g), 1);
+            for (int q = 0; q < PS_PROD; ++q) mbar_init(empty0 + 8u * (b * PS_PROD + q), 1);
         }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -1278,7 +1301,7 @@ k_pm_s(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
     __syncthreads();
     volatile int* abort = &s_abort;
     if (warp >= PS_CONS)
-        pr_produce<NCH, true, PS_PROD, PS_NBUF>(B, mc, S, TM, buf_words, nbuf, a_sm, s_rec, s_hdr,
+        pr_produce<NCH, true, PS_PROD, PS_NBUF, PS_CONS>(B, mc, S, TM, buf_words, nbuf, a_sm, s_rec, s_hdr,
                                                 s_next, s_geom, full0, empty0, abort, limit,
                                                 warp - PS_CONS, lane);
     else
