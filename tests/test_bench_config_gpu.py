@@ -2,7 +2,9 @@
 1024x436 PGM-C pairs (the benchmark's seeds and stream ids) in one
 PairMatcher, matched by one CUDA graph replay with the launch knobs the
 autotuner picks on GB300; the exported matches of sampled pairs equal the
-oracle's exactly.  (The method is a heuristic with more than one valid
+oracle's exactly.  The same for its direction-only variant PGM-CD, whose
+levels 0 and 1 run the one-seed-per-lane bit-plane kernel at this size, over
+several replays and every tile shape.  (The method is a heuristic with more than one valid
 outcome; the checkerboard order and the Philox stream fix one, and the
 GPU path reproduces it.)"""
 import pytest
@@ -19,28 +21,34 @@ PRM = dict(levels=5, seed_stride=3, patch_fwd=15, patch_bwd=11, color=1, descrip
            iters_coarse=4, iters_fine=6, refine_rounds=2, rs_W=2)
 
 
-def test_bench_configuration_matches_oracle():
+@pytest.mark.parametrize("name,extra,tiles", [("PGM-C", {}, (8,)),
+                                               ("PGM-CD", dict(descriptor=1), (8, 4, 16))])
+def test_bench_configuration_matches_oracle(name, extra, tiles):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1704_03217_gb300 import build
     build.build()
     from paper_1704_03217_gb300 import api, tune
+    prm = dict(PRM, **extra)
     pairs = [synth.sintel_like_pair(sd, W, H) for sd in range(B)]
     imgs1 = [torch.from_numpy(p[0]).cuda() for p in pairs]
     imgs2 = [torch.from_numpy(p[1]).cuda() for p in pairs]
-    m = api.PairMatcher(api.Params(**PRM), W, H, batch=B)
-    try:
-        tune.set(2, 16)
-        m.capture(imgs1, imgs2, list(range(B)))
-        for _ in range(2):                    # replays repeat the same step
-            m.replay()
-        torch.cuda.synchronize()
-    finally:
-        tune.set()
-    got = [r.cpu().numpy() for r in m.results()]
-    for ws in m.ws:
-        ws.sync_status()
+    m = api.PairMatcher(api.Params(**prm), W, H, batch=B)
+    want = {}
     for k in (0, 9, 15):
-        _, _, _, rows = O.run_pair(PRM, pairs[k][0], pairs[k][1], O.SCHED_CHECKERBOARD, k)
-        assert got[k].shape == rows.shape, (k, got[k].shape, rows.shape)
-        assert (got[k] == rows).all(), k
+        _, _, _, want[k] = O.run_pair(prm, pairs[k][0], pairs[k][1], O.SCHED_CHECKERBOARD, k)
+    for tw in tiles:
+        try:
+            tune.set(2, 16, tw)
+            m.capture(imgs1, imgs2, list(range(B)))
+            for _ in range(3):                # replays repeat the same step
+                m.replay()
+            torch.cuda.synchronize()
+        finally:
+            tune.set()
+        got = [r.cpu().numpy() for r in m.results()]
+        for ws in m.ws:
+            ws.sync_status()
+        for k, rows in want.items():
+            assert got[k].shape == rows.shape, (name, tw, k, got[k].shape, rows.shape)
+            assert (got[k] == rows).all(), (name, tw, k)
