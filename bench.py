@@ -569,6 +569,10 @@ def run_ours(a):
     if not a.no_variants and rank == 0:
         batched = run_batched(api, prm, dev)
 
+    interp = None
+    if not a.no_variants and rank == 0:
+        interp = run_interp(api, prm, m, dev, [p[2] for p in pairs])
+
     serving = None
     if a.serve > 0 and rank == 0:
         serving = run_serving(api, prm, a.serve, dev)
@@ -619,6 +623,7 @@ def run_ours(a):
             "variants": variants,
             "workloads": workloads,
             "batched": batched,
+            "interpolation": interp,
             "serving": serving,
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -798,6 +803,39 @@ def run_batched(api, prm, dev, n=64, reps=3):
                 "note": "levels listed from 0 (full resolution); accuracy of the exported "
                         "matches against the generator's flow; every schedule is bit-exact "
                         "with the oracle run at the same counts"}}
+
+
+def run_interp(api, prm, m, dev, flows, reps=3):
+    """Sparse-to-dense interpolation (pgm_interpolate) of the timed step's
+    exported matches, pair by pair on the device: ms per 1024x436 pair from
+    CUDA events (each call synchronises its stream while the relaxation runs)
+    and the dense flow's end-point error against the generator's flow."""
+    import numpy as np
+    import torch
+    ip = api.InterpParams()
+    n = min(4, m.batch)
+    ws = None
+    for k in range(n):                         # warm-up, and the workspace
+        _, ws = api.interpolate(prm, m.p1[k], m.rows[k], m.count[k], ip, ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        for k in range(n):
+            flow, ws = api.interpolate(prm, m.p1[k], m.rows[k], m.count[k], ip, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (reps * n)
+    epe = []
+    for k in range(n):
+        flow, ws = api.interpolate(prm, m.p1[k], m.rows[k], m.count[k], ip, ws)
+        epe.append(np.hypot(*(flow.cpu().numpy() - flows[k]).transpose(2, 0, 1)))
+    e = np.concatenate([x.ravel() for x in epe])
+    return {"pairs": n, "k": ip.k, "ms_per_pair": ms, "mpix_per_s": W_IMG * H_IMG / (ms * 1e3),
+            "epe_mean": float(e.mean()), "epe_median": float(np.median(e)),
+            "outliers_3px": float((e > 3).mean()),
+            "note": "k geodesic nearest matches, LA (matches above 2.2 % of the pixels); "
+                    "median EPE is the typical pixel, the mean carries occluded regions"}
 
 
 def run_serving(api, prm, n, dev):

@@ -100,10 +100,15 @@ __global__ void k_iseed(const int32_t* rows, const int32_t* count, int64_t max_r
     }
 }
 
-__global__ void __launch_bounds__(IT_W * IT_W) k_irelax(const uint32_t* cost, int w, int h, int k,
+// KT > 0: k fixed at compile time (the default 16), which keeps the list in
+// registers; KT = 0: any k
+template <int KT>
+__global__ void __launch_bounds__(IT_W * IT_W) k_irelax(const uint32_t* cost, int w, int h, int k_,
                                                         unsigned long long* keys, unsigned* changed) {
+    const int k = KT > 0 ? KT : k_;
     __shared__ unsigned long long sl[IT_H * IT_H][IK_MAX];
     __shared__ uint32_t sc[IT_H * IT_H];
+    __shared__ uint8_t dirty[2][IT_H * IT_H];     // the list changed in the last round
     const int tx = threadIdx.x % IT_W, ty = threadIdx.x / IT_W;
     const int x0 = blockIdx.x * IT_W - 1, y0 = blockIdx.y * IT_W - 1;
     for (int t = threadIdx.x; t < IT_H * IT_H; t += IT_W * IT_W) {
@@ -112,6 +117,8 @@ __global__ void __launch_bounds__(IT_W * IT_W) k_irelax(const uint32_t* cost, in
         const int64_t p = (int64_t)y * w + x;
         sc[t] = in ? cost[p] : 0u;
         for (int e = 0; e < IK_MAX; ++e) sl[t][e] = in && e < k ? keys[p * k + e] : EMPTY;
+        dirty[0][t] = 1;                         // round 0 looks at every neighbour
+        dirty[1][t] = 0;
     }
     __syncthreads();
     const int x = x0 + 1 + tx, y = y0 + 1 + ty, me = (ty + 1) * IT_H + tx + 1;
@@ -122,12 +129,14 @@ __global__ void __launch_bounds__(IT_W * IT_W) k_irelax(const uint32_t* cost, in
     bool any = false;
     for (int it = 0; it < IT_INNER; ++it) {
         bool ch = false;
+        const int cur = it & 1;
         if (live) {
             const int nb[4] = {me - 1, me + 1, me - IT_H, me + IT_H};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int t = nb[q];
                 if (sc[t] == 0u) continue;                       // outside the image
+                if (!dirty[cur][t]) continue;                    // nothing new there
                 const unsigned long long step = (unsigned long long)(sc[me] + sc[t]) << 32;
                 for (int e = 0; e < k; ++e) {
                     const unsigned long long key = sl[t][e];
@@ -149,6 +158,13 @@ __global__ void __launch_bounds__(IT_W * IT_W) k_irelax(const uint32_t* cost, in
         if (ch) {
 #pragma unroll
             for (int e = 0; e < IK_MAX; ++e) sl[me][e] = L[e];
+        }
+        dirty[cur ^ 1][me] = ch;                                 // read in the next round
+        if (threadIdx.x < 4 * IT_H) {                            // the halo does not change
+            const int e = threadIdx.x, t = e < IT_H ? e : e < 2 * IT_H ? (IT_H - 1) * IT_H + e - IT_H
+                                              : e < 3 * IT_H ? (e - 2 * IT_H) * IT_H
+                                                             : (e - 3 * IT_H) * IT_H + IT_H - 1;
+            dirty[cur ^ 1][t] = 0;
         }
         any |= ch;
         if (!__syncthreads_or(ch)) break;                        // the tile is stable
@@ -298,7 +314,8 @@ pgm_status pgm_interpolate(const pgm_params* p, const void* d_pyr1, int w, int h
     while (host_flag) {
         if (launches++ > most) return PGM_ERR_UNSUPPORTED;
         PGM_TRY(cudaMemsetAsync(flag, 0, 4, st), "interpolate: clear the flag");
-        k_irelax<<<grid, IT_W * IT_W, 0, st>>>(cost, w, h, ip->k, keys, flag);
+        if (ip->k == IK_MAX) k_irelax<IK_MAX><<<grid, IT_W * IT_W, 0, st>>>(cost, w, h, ip->k, keys, flag);
+        else k_irelax<0><<<grid, IT_W * IT_W, 0, st>>>(cost, w, h, ip->k, keys, flag);
         if ((r = launch_status("interpolate: relax")) != PGM_OK) return r;
         PGM_TRY(cudaMemcpyAsync(&host_flag, flag, 4, cudaMemcpyDeviceToHost, st),
                 "interpolate: read the flag");
