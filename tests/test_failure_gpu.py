@@ -47,3 +47,37 @@ def test_wait_limit_timeout_is_reported_and_recovered(api):
     got = again.field(0, 0)
     for k in want:
         assert torch.equal(got[k], want[k]), k
+
+
+@pytest.mark.parametrize("name,extra,pairs", [("PGM-C", {}, 2), ("PGM-CD", dict(descriptor=1), 3)])
+def test_wait_limit_timeout_in_large_phases(api, name, extra, pairs):
+    """The same at full size, where the search runs its per-direction
+    launches (and, for the direction descriptor, the one-seed-per-lane
+    kernel with its per-consumer barriers): every workspace reports the
+    timeout, and afterwards the batch matches exactly as before."""
+    from paper_1704_03217_gb300 import _lib, synth
+    L = _lib.load()
+    prm = api.Params(levels=5, color=1, **extra)
+    data = [synth.sintel_like_pair(60 + k) for k in range(pairs)]
+    i1 = [torch.from_numpy(d[0]).cuda() for d in data]
+    i2 = [torch.from_numpy(d[1]).cuda() for d in data]
+    m = api.PairMatcher(prm, 1024, 436, batch=pairs)
+    m.enqueue(i1, i2)
+    torch.cuda.synchronize()
+    want = [r.clone() for r in m.results()]
+    try:
+        assert L.pgm_set_wait_limit(2) == 0
+        m.enqueue(i1, i2)
+        torch.cuda.synchronize()
+        for ws in m.ws:
+            with pytest.raises(_lib.PGMError) as e:
+                ws.sync_status()
+            assert e.value.code == 5
+    finally:
+        assert L.pgm_set_wait_limit(0) == 0
+    m.enqueue(i1, i2)
+    torch.cuda.synchronize()
+    for ws in m.ws:
+        ws.sync_status()
+    for a, b in zip(m.results(), want):
+        assert torch.equal(a, b), name
