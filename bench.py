@@ -557,6 +557,9 @@ def run_ours(a):
             variants[name] = {"pairs_per_s": B * max(3, a.steps // 4) / (tot * 1e-3),
                               "gcand_evals_per_s": api.nominal_evals(pv, W_IMG, H_IMG, W_IMG, H_IMG)
                               * B * max(3, a.steps // 4) / (tot * 1e-3) / 1e9}
+            if kw.get("descriptor") == 1:
+                variants[name]["roofline"] = bit_search_roofline(api, _lib, pv, mv, imgs1, imgs2,
+                                                                 sids, flush, l1_peak)
             del mv
         variants["note"] = ("pairs/s of the same 16 pairs, whole step graph-replayed; "
                             "gcand_evals_per_s nominal")
@@ -710,6 +713,36 @@ def run_workloads(api, prm, dev, flush, steps):
         del mv
     out["note"] = "L2 flushed before every timed replay; gcand_evals_per_s nominal"
     return out
+
+
+def bit_search_roofline(api, lib, pv, mv, imgs1, imgs2, sids, flush, l1_peak):
+    """The bit-plane search kernels (direction descriptor) against the
+    L1/shared roofline: per evaluated candidate the target patch's two
+    bit-planes, P^2 2C / 4 bytes (P^2 2C values of 2 bits), over the search
+    time per step from a profiling pass (CUDA events around every launch)."""
+    import ctypes as C
+    import torch
+    L = lib.load()
+    L.pgm_profile_enable(1)
+    for _ in range(2):
+        flush.fill_(2)
+        mv.enqueue(imgs1, imgs2, sids)
+    torch.cuda.synchronize()
+    kms = (C.c_double * 7)()
+    kn = (C.c_int64 * 7)()
+    L.pgm_profile_read(kms, kn)
+    L.pgm_profile_enable(0)
+    ms = kms[lib.K_CLASSES.index("pm")] / 2
+    nch = 6 if pv.color == 1 else 2
+    ev = [w.evals() for w in mv.ws]
+    nbytes = sum(e["pm"][0] * pv.patch_fwd ** 2 * nch / 4 + e["pm"][1] * pv.patch_bwd ** 2 * nch / 4
+                 for e in ev)
+    gbs = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    return {"bound": "l1", "kernel": "k_pm_s / k_pm_b (bit-plane search)", "achieved": gbs,
+            "peak": l1_peak, "unit": "GB/s (2-bit target-patch values read per evaluation)",
+            "frac": gbs / l1_peak, "pm_ms_per_step": ms,
+            "bytes_per_eval_fwd": pv.patch_fwd ** 2 * nch / 4,
+            "bytes_per_eval_bwd": pv.patch_bwd ** 2 * nch / 4}
 
 
 def run_batched(api, prm, dev, n=64, reps=3):
