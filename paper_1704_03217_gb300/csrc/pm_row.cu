@@ -321,7 +321,8 @@ __device__ void pr_produce(const LvlBatch& B, const MatchConst& mc, const RowSch
             const int s = j * D.nx + i;
             const int px = mc.c + sig * i, py = mc.c + sig * j;
             const int f = D.flags[s], u = D.u[s];
-            const unsigned long long cst = D.cost[s], sa = D.sa2img[(size_t)py * D.rw + px];
+            // (the bit-plane cost needs no sum |a|^2, and no box sums are made for it)
+            const unsigned long long cst = D.cost[s], sa = BITS ? 0ull : D.sa2img[(size_t)py * D.rw + px];
             bool have = f & F_VALID;
             // the refresh (first iteration of a visit) drops a match whose centre
             // left the target, here and at the neighbours
