@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpgm.so")
 LIB_CHECKED = os.path.join(OUT, "libpgm_checked.so")
-SOURCES = ["abi.cu", "pyramid.cu", "match.cu", "pm_row.cu", "init_tile.cu", "filter.cu",
+SOURCES = ["abi.cu", "pyramid.cu", "match.cu", "pm_row.cu", "init_tile.cu", "init_tc.cu", "filter.cu",
            "filter_noalloc.cu", "interp.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

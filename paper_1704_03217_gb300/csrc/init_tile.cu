@@ -348,6 +348,7 @@ pgm_status launch_init_tile(const LvlBatch& B, const MatchConst& mc, int nch, bo
         }
     }
     if (mc.norm != PGM_L2SQ) return PGM_OK;
+    if (pgm_status r = launch_init_tc(B, mc, nch, handled, st); r != PGM_OK || *handled) return r;
     int words = 0, seeds = 0;
     for (int k = 0; k < B.n; ++k)
         for (int d = 0; d < 2; ++d) {

@@ -239,6 +239,10 @@ pgm_status launch_box(const LvlBatch& B, int nch, int max_pixels, cudaStream_t s
 // *handled = false when it does not apply (the caller uses the direct kernel)
 pgm_status launch_init_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
                             cudaStream_t st);
+// init_tc.cu: the same initialisation on the tensor cores (six channels,
+// squared L2, patches up to 15 x 15); *handled = false when it does not apply
+pgm_status launch_init_tc(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
+                          cudaStream_t st);
 // true when the tile search kernel takes this batch (it then also does the
 // cost refresh of a visit's first iteration, MatchConst::refresh)
 bool pm_tile_fits(const LvlBatch& B, const MatchConst& mc, int nch);
