@@ -425,7 +425,7 @@ int tc_pairs(int P, int sigma, uint16_t* out) {
 // *handled = false (nothing launched) unless the batch is six-channel, squared
 // L2, patches up to 15 x 15, and a CTA's staging fits in shared memory.
 pgm_status launch_init_tc(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
-                          cudaStream_t st) {
+                          cudaStream_t st, int* nlaunch) {
     *handled = false;
     if (nch != 6 || mc.norm != PGM_L2SQ || mc.sigma < 1 || B.n < 1) return PGM_OK;
     int P[2] = {0, 0}, units = 0, ctas = 0, seeds = 0;
@@ -451,6 +451,7 @@ pgm_status launch_init_tc(const LvlBatch& B, const MatchConst& mc, int nch, bool
     k_init_tc_clear<<<gs, 256, 0, st>>>(B);
     k_init_tc<<<dim3(ctas, B.n, 2), TC_THREADS, 16 * units, st>>>(B, mc, T, wait_limit());
     k_init_tc_fin<<<gs, 256, 0, st>>>(B, mc);
+    *nlaunch = 3;
     return launch_status("init (tensor cores): launch");
 }
 

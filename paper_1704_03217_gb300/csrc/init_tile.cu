@@ -328,8 +328,9 @@ bool init_bits_fits(const LvlBatch& B) {
 // *handled = false (nothing launched) when the cost is not squared L2 or a
 // target image with its border does not fit in shared memory.
 pgm_status launch_init_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
-                            cudaStream_t st) {
+                            cudaStream_t st, int* nlaunch) {
     *handled = false;
+    *nlaunch = 1;
     if (mc.descriptor == PGM_DIR && init_bits_fits(B)) {     // the bit-plane form, any norm
         int words = 0, seeds = 0;
         for (int k = 0; k < B.n; ++k)
@@ -348,7 +349,7 @@ pgm_status launch_init_tile(const LvlBatch& B, const MatchConst& mc, int nch, bo
         }
     }
     if (mc.norm != PGM_L2SQ) return PGM_OK;
-    if (pgm_status r = launch_init_tc(B, mc, nch, handled, st); r != PGM_OK || *handled) return r;
+    if (pgm_status r = launch_init_tc(B, mc, nch, handled, st, nlaunch); r != PGM_OK || *handled) return r;
     int words = 0, seeds = 0;
     for (int k = 0; k < B.n; ++k)
         for (int d = 0; d < 2; ++d) {

@@ -673,7 +673,7 @@ pgm_status launch_init(const LvlBatch& B, const MatchConst& mc, int nch, int max
     if (max_seeds <= 0) return PGM_OK;
     KScope ks(PGM_K_INIT, st);
     bool handled = false;
-    const pgm_status r = launch_init_tile(B, mc, nch, &handled, st);
+    const pgm_status r = launch_init_tile(B, mc, nch, &handled, st, &ks.n);
     if (r != PGM_OK || handled) return r;
     dim3 g(max_seeds, 2, B.n);
     if (nch == 2) {

@@ -237,12 +237,13 @@ pgm_status launch_box(const LvlBatch& B, int nch, int max_pixels, cudaStream_t s
 // pm_row.cu (search and cost refresh on staged tiles) and init_tile.cu:
 // exhaustive init, squared L2, target image staged in shared memory;
 // *handled = false when it does not apply (the caller uses the direct kernel)
+// (*nlaunch: the kernels launched)
 pgm_status launch_init_tile(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
-                            cudaStream_t st);
+                            cudaStream_t st, int* nlaunch);
 // init_tc.cu: the same initialisation on the tensor cores (six channels,
 // squared L2, patches up to 15 x 15); *handled = false when it does not apply
 pgm_status launch_init_tc(const LvlBatch& B, const MatchConst& mc, int nch, bool* handled,
-                          cudaStream_t st);
+                          cudaStream_t st, int* nlaunch);
 // true when the tile search kernel takes this batch (it then also does the
 // cost refresh of a visit's first iteration, MatchConst::refresh)
 bool pm_tile_fits(const LvlBatch& B, const MatchConst& mc, int nch);
