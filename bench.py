@@ -273,6 +273,55 @@ def hbm_stage_bytes(prm, w, h, pairs, matches_total):
     return {"pyramid": pyr, "fields": pairs * f + 16 * matches_total}
 
 
+def tc_steps(P, sigma):
+    """K steps (pixel pairs) of the tensor-core initialisation for a P x P
+    patch: the library's pairing (raster order, first later pixel also later
+    in phase order, else a zero partner), restated to count MMAs."""
+    used = [False] * (P * P)
+    key = lambda i: ((((i // P) % sigma) * sigma + (i % P) % sigma), (i // P) // sigma,
+                     (i % P) // sigma)
+    n = 0
+    for i in range(P * P):
+        if used[i]:
+            continue
+        used[i] = True
+        n += 1
+        for j in range(i + 1, P * P):
+            if not used[j] and key(j) > key(i):
+                used[j] = True
+                break
+    return n
+
+
+def init_tc_flops(prm, w, h, pairs):
+    """Tensor-core initialisation per step: (executed, useful) fp16 FLOPs.
+    Executed: every MMA issued (tiles of 128 flattened seeds x 160 flattened
+    centres x 16, four split products per K step); useful: the four split
+    products of the real (seed, centre) pairs over the six channels."""
+    L, sig = prm["levels"], prm["seed_stride"]
+    for _ in range(L - 1):
+        w, h = (w + 1) // 2, (h + 1) // 2
+    c = sig // 2
+    nx, ny = (w - 1 - c) // sig + 1, (h - 1 - c) // sig + 1
+    ex = us = 0
+    for P in (prm["patch_fwd"], prm["patch_bwd"]):
+        Wu = nx + (P - 1) // sig
+        mt = -(-ny * Wu // 128)
+        nt = -(-h * (w + P - 1) // 160)
+        ex += mt * nt * tc_steps(P, sig) * 4 * 2 * 128 * 160 * 16
+        us += nx * ny * w * h * P * P * 6 * 4 * 2
+    return pairs * ex, pairs * us
+
+
+def measured_tensor_peak():
+    """Dense bf16 TFLOP/s, sustained (the fp16 rate is the same)."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+                     ["bf16_tflops_sustained"]), "measured (cuBLAS bf16, sustained)"
+    except (OSError, ValueError, KeyError):
+        return 1700.0, "fallback"
+
+
 def measured_hbm_peak():
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
@@ -535,6 +584,24 @@ def run_ours(a):
     traffic = (pm_traffic_per_launch(search_units(P, W_IMG, H_IMG, B), kernel_launches["pm"])
                if not a.variant else None)
     overlap_tmac = el_pm / (pm_step_ms * 1e-3) / 1e12 if pm_step_ms > 0 else 0.0
+    init_roof = None
+    if P["color"] == 1 and P["descriptor"] != 1 and kernel_ms["init"] > 0:
+        ex, us = init_tc_flops(P, W_IMG, H_IMG, B)
+        tpk, tsrc = measured_tensor_peak()
+        sec = kernel_ms["init"] * 1e-3
+        init_roof = {"kernel": "k_init_tc (exhaustive coarsest-level initialisation, tcgen05)",
+                     "bound": "tensor", "achieved": ex / sec / 1e12, "peak": tpk,
+                     "unit": "TFLOP/s (fp16 MMA)", "frac": ex / sec / 1e12 / tpk,
+                     "peak_source": tsrc, "useful_TFLOPs": us / sec / 1e12,
+                     "useful_frac": us / sec / 1e12 / tpk,
+                     "element_Tmac_per_s": us / 8 / sec / 1e12,
+                     "ms_per_step": kernel_ms["init"],
+                     "launches_per_step": kernel_launches["init"],
+                     "note": "achieved: every MMA issued (128 x 160 x 16 tiles, 8-channel "
+                             "pixels, four split products per element); useful: the split "
+                             "products of the real seed-centre pairs; element_Tmac_per_s: "
+                             "int16 element MACs of Eq. 3's cross term per second; time of "
+                             "the init class (clear, MMA and unpack launches)"}
 
     variants = {}
     if not a.no_variants:
@@ -620,6 +687,7 @@ def run_ours(a):
                          "note": "achieved from per-launch event times of the profiling pass "
                                  "(directions serial); frac_overlap_credited divides by the "
                                  "search's share of the timed, overlapped step instead"},
+            "init_roofline": init_roof,
             "hbm_stages": hbm_stages,
             "kernel_ms_per_step": kernel_ms, "kernel_launches_per_step": kernel_launches,
             "evals_per_step": evals_step,
