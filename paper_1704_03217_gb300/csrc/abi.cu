@@ -1,6 +1,7 @@
 // abi.cu -- the extern "C" entry points of libpgm: argument checks, buffer
 // layouts (plans), the visit schedule of Fig. 5 and the launch sequence.
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
@@ -54,6 +55,13 @@ Tuning tuning() { return Tuning{g_slack.load(), g_chunk.load(), g_tile_w.load()}
 constexpr long long WAIT_DEFAULT = 1ll << 31;        // about 1 s at 2 GHz
 static std::atomic<long long> g_wait{WAIT_DEFAULT};
 long long wait_limit() { return g_wait.load(); }
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("PGM_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 
 namespace {
 struct ProfEvent { int cls; int n; cudaEvent_t a, b; };

@@ -548,6 +548,8 @@ __global__ void __launch_bounds__(256) k_pm(const __grid_constant__ LvlBatch B, 
 // Only the other direction's VALID bit and u are read; this kernel writes
 // only OUTL bits, so the two directions can be updated in one launch.
 __global__ void k_consist(const __grid_constant__ LvlBatch B, const MatchConst mc) {
+    pdl_trigger();
+    pdl_wait();
     const int pair = blockIdx.z, dir = blockIdx.y;
     const DirLvl& D = B.d[pair][dir];
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -575,6 +577,8 @@ __global__ void k_consist(const __grid_constant__ LvlBatch B, const MatchConst m
 
 // ------------------------------------------------------------ transfer
 __global__ void k_transfer(const __grid_constant__ XferBatch X) {
+    pdl_trigger();
+    pdl_wait();
     const int pair = blockIdx.z, dir = blockIdx.y;
     const XferDir& T = X.d[pair][dir];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -768,14 +772,16 @@ pgm_status launch_consist(const LvlBatch& B, const MatchConst& mc, int max_seeds
                           cudaStream_t st) {
     if (max_seeds <= 0) return PGM_OK;
     KScope ks(PGM_K_CONSIST, st);
-    k_consist<<<dim3((max_seeds + 255) / 256, 2, B.n), 256, 0, st>>>(B, mc);
+    PGM_TRY(launch_pdl(k_consist, dim3((max_seeds + 255) / 256, 2, B.n), dim3(256), 0, st, B, mc),
+            "consistency: launch");
     return last_status();
 }
 
 pgm_status launch_transfer(const XferBatch& X, int max_seeds, cudaStream_t st) {
     if (max_seeds <= 0) return PGM_OK;
     KScope ks(PGM_K_TRANSFER, st);
-    k_transfer<<<dim3((max_seeds + 255) / 256, 2, X.n), 256, 0, st>>>(X);
+    PGM_TRY(launch_pdl(k_transfer, dim3((max_seeds + 255) / 256, 2, X.n), dim3(256), 0, st, X),
+            "transfer: launch");
     return last_status();
 }
 

@@ -74,6 +74,37 @@ struct Schedule {
     int with_o[MAXVIS];          // transfer into this visit carries O (Eq. 8)
 };
 
+// Programmatic dependent launch along the matching loop (search phases,
+// consistency, transfer): a kernel launched with launch_pdl may start while
+// the previous kernel of its stream is still running; it runs its prologue
+// (shared memory and barrier set-up), then pdl_wait() blocks until that kernel
+// has completed and its writes are visible, before any global memory access.
+// pdl_trigger() lets the next kernel start early.  Without the launch
+// attribute both are no-ops.  PGM_PDL=0 in the environment turns the
+// attribute off (same results).
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+#endif
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
+
 // Record, for this host thread, which CUDA call failed and how
 // (pgm_error_detail), and return PGM_ERR_CUDA.
 pgm_status cuda_fail(const char* site, cudaError_t e);

@@ -721,6 +721,7 @@ k_pm_r(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
     __shared__ __align__(8) unsigned long long s_full[PR_NBUF], s_empty[PR_NBUF];
     __shared__ int s_next[PR_NBUF];
     __shared__ int s_abort;
+    pdl_trigger();                  // the next phase may start its prologue
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned a_sm = (unsigned)__cvta_generic_to_shared(sm);
     const unsigned full0 = (unsigned)__cvta_generic_to_shared(&s_full[0]);
@@ -737,6 +738,7 @@ k_pm_r(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
+    pdl_wait();                     // the previous phase is complete and visible
     volatile int* abort = &s_abort;
     if (warp >= pr_cons(NCH, PC))
         pr_produce<NCH, false, PR_PROD, PR_NBUF>(B, mc, S, TM, buf_words, nbuf, a_sm, s_rec, s_hdr, s_next, s_geom, full0,
@@ -980,6 +982,7 @@ k_pm_b(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
     __shared__ __align__(8) unsigned long long s_full[PB_NBUF], s_empty[PB_NBUF];
     __shared__ int s_next[PB_NBUF];
     __shared__ int s_abort;
+    pdl_trigger();                  // the next phase may start its prologue
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned a_sm = (unsigned)__cvta_generic_to_shared(sm);
     const unsigned full0 = (unsigned)__cvta_generic_to_shared(&s_full[0]);
@@ -996,6 +999,7 @@ k_pm_b(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
+    pdl_wait();                     // the previous phase is complete and visible
     volatile int* abort = &s_abort;
     if (warp >= PB_CONS)
         pr_produce<NCH, true, PB_PROD, PB_NBUF>(B, mc, S, TM, buf_words, nbuf, a_sm, s_rec, s_hdr,
@@ -1284,6 +1288,7 @@ k_pm_s(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
     __shared__ __align__(8) unsigned long long s_full[PS_NBUF * PS_CONS], s_empty[PS_NBUF * PS_PROD];
     __shared__ int s_next[PS_NBUF];
     __shared__ int s_abort;
+    pdl_trigger();                  // the next phase may start its prologue
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned a_sm = (unsigned)__cvta_generic_to_shared(sm);
     const unsigned full0 = (unsigned)__cvta_generic_to_shared(&s_full[0]);
@@ -1300,6 +1305,7 @@ k_pm_s(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
+    pdl_wait();                     // the previous phase is complete and visible
     volatile int* abort = &s_abort;
     if (warp >= PS_CONS)
         pr_produce<NCH, true, PS_PROD, PS_NBUF, PS_CONS>(B, mc, S, TM, buf_words, nbuf, a_sm, s_rec, s_hdr,
@@ -1515,7 +1521,9 @@ pgm_status launch_r(const LvlBatch& B, const MatchConst& mc, const RowSched& S, 
     const int grid = S.total < sms ? S.total : sms;       // one CTA per SM (shared memory)
     const int threads = !BITS ? 32 * (PR_PROD + pr_cons(NCH, PC))
                         : per_lane ? 32 * (PS_PROD + PS_CONS) : 32 * (PB_PROD + PB_CONS);
-    kern<<<grid, threads, smem, st>>>(B, mc, S, TM, buf_words, nbuf, wait_limit());
+    PGM_TRY(launch_pdl(kern, dim3(grid), dim3(threads), smem, st, B, mc, S, TM, buf_words, nbuf,
+                       wait_limit()),
+            "search: launch");
     return launch_status("search: launch");
 }
 
