@@ -97,22 +97,18 @@ __global__ void k_down(const __grid_constant__ PyrBatch B, int C) {
 }
 
 // ------------------------------------------------------- colour spaces
-// Integer cube root of v <= 2^48: float estimate, then exact correction.  The
-// estimate is within a few hundredths of the real root (v rounded to float,
-// then a cube root of documented 1-ulp accuracy, for roots below 2^17), so
-// its integer part is off by at most one; two steps each way leave margin.
+// Integer cube root of v <= 2^48: the floor of a float estimate, then one
+// exact correction step each way.  The estimate 2^(log2(v) / 3) from the
+// fast base-2 logarithm and exponential (each documented within 2 units in
+// the last place here; log2(v) < 49) is within about 2e-6 of the root
+// relatively, so for roots below 2^17 its integer part is off by at most
+// one.  All 2^24 colours are checked against the oracle on the GPU.
 __device__ __forceinline__ uint32_t icbrt48(unsigned long long v) {
-    int c = (int)cbrtf((float)v);
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const unsigned long long cc = (unsigned long long)(unsigned)c * (unsigned)c;
-        if (c > 0 && cc * (unsigned)c > v) --c;
-    }
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const unsigned n = (unsigned)c + 1u;
-        if ((unsigned long long)n * n * n <= v) ++c;
-    }
+    int c = v ? (int)__exp2f(__log2f((float)v) * (1.0f / 3.0f)) : 0;
+    const unsigned long long cc = (unsigned long long)(unsigned)c * (unsigned)c;
+    if (c > 0 && cc * (unsigned)c > v) --c;
+    const unsigned n = (unsigned)c + 1u;
+    if ((unsigned long long)n * n * n <= v) ++c;
     return (uint32_t)c;
 }
 
