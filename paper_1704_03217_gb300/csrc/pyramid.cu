@@ -104,7 +104,7 @@ __global__ void k_down(const __grid_constant__ PyrBatch B, int C) {
 // relatively, so for roots below 2^17 its integer part is off by at most
 // one.  All 2^24 colours are checked against the oracle on the GPU.
 __device__ __forceinline__ uint32_t icbrt48(unsigned long long v) {
-    int c = v ? (int)__exp2f(__log2f((float)v) * (1.0f / 3.0f)) : 0;
+    int c = v ? (int)exp2f(__log2f((float)v) * (1.0f / 3.0f)) : 0;
     const unsigned long long cc = (unsigned long long)(unsigned)c * (unsigned)c;
     if (c > 0 && cc * (unsigned)c > v) --c;
     const unsigned n = (unsigned)c + 1u;
