@@ -513,10 +513,71 @@ __device__ __forceinline__ void pr_acc_glob(const int (&ra)[M][NCH / 2], const u
     }
 }
 
+// Six-channel pixels, P = 15, staged rows of a compile-time pitch SP words:
+// lane l < 30 holds column l mod 15 of patch rows 2m + l div 15 (m = 0 .. 7,
+// row 15 counting zero); lanes 30 and 31 read columns 15 and 16 of the odd
+// rows and count zero.  Every load of pixel m then sits 8 SP m bytes from the
+// lane's own base, an immediate offset.  The extra row and columns stay in
+// the staged buffer: a region's last row is followed by the next region (the
+// window after the reference rows, the sums after the window), and a row's
+// pitch exceeds the window width by more than two pixels.
+constexpr int PR_ROWS_SP = 188;                // the pitch of the default tiles (8 x 8, margin 2)
+template <int OFF>
+__device__ __forceinline__ uint4 lds128_at(unsigned addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4+%5];\n"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr), "n"(OFF));
+    return v;
+}
+template <int SP, int m = 0>
+__device__ __forceinline__ void pr_ref_rows(int (&ra)[8][3], unsigned base, unsigned vmask) {
+    if constexpr (m < 8) {
+        const uint4 v = lds128_at<8 * SP * m>(base);
+        const int keep = ((vmask >> m) & 1u) ? -1 : 0;
+        ra[m][0] = (int)v.x & keep;
+        ra[m][1] = (int)v.y & keep;
+        ra[m][2] = (int)v.z & keep;
+        pr_ref_rows<SP, m + 1>(ra, base, vmask);
+    }
+}
+template <int SP, int m = 0>
+__device__ __forceinline__ void pr_acc_rows(const int (&ra)[8][3], unsigned base, int (&l)[3],
+                                            int (&h)[3]) {
+    if constexpr (m < 8) {
+        const uint4 v = lds128_at<8 * SP * m>(base);
+        l[0] = __dp2a_lo((int)v.x, ra[m][0], l[0]);
+        h[0] = __dp2a_hi((int)v.x, ra[m][0], h[0]);
+        l[1] = __dp2a_lo((int)v.y, ra[m][1], l[1]);
+        h[1] = __dp2a_hi((int)v.y, ra[m][1], h[1]);
+        l[2] = __dp2a_lo((int)v.z, ra[m][2], l[2]);
+        h[2] = __dp2a_hi((int)v.z, ra[m][2], h[2]);
+        pr_acc_rows<SP, m + 1>(ra, base, l, h);
+    }
+}
+// the same lanes' pixels from the padded target image in global memory
+// (pixels a lane does not hold read the patch corner)
+__device__ __forceinline__ void pr_acc_glob_rows(const int (&ra)[8][3], const uint32_t* img,
+                                                 int pitch, int x0, int y0, int r0, int col,
+                                                 unsigned vmask, int (&l)[3], int (&h)[3]) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const bool in = (vmask >> m) & 1u;
+        const uint32_t* p = img + (ptrdiff_t)(y0 + (in ? 2 * m + r0 : 0)) * pitch +
+                            (ptrdiff_t)(x0 + (in ? col : 0)) * 4;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+        l[0] = __dp2a_lo((int)v.x, ra[m][0], l[0]);
+        h[0] = __dp2a_hi((int)v.x, ra[m][0], h[0]);
+        l[1] = __dp2a_lo((int)v.y, ra[m][1], l[1]);
+        h[1] = __dp2a_hi((int)v.y, ra[m][1], h[1]);
+        l[2] = __dp2a_lo((int)v.z, ra[m][2], l[2]);
+        h[2] = __dp2a_hi((int)v.z, ra[m][2], h[2]);
+    }
+}
+
 // Consumer warps: for every tile of the CTA, the active seeds taken one at a
 // time from the buffer's counter.  PC > 0: the patch side of every pair of the
 // launch (compile time), else at most MAXP (run time).
-template <int NCH, int PC>
+template <int NCH, int PC, int SP = 0>
 __device__ void pr_consume(const LvlBatch& B, const MatchConst& mc, const RowSched& S,
                            int buf_words, int nbuf, unsigned a_sm, const uint32_t* sm_gen,
                            RowRec (*rec)[PR_NACT], const RowHdr* hdr, int* next,
@@ -524,9 +585,12 @@ __device__ void pr_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
                            volatile int* abort, long long limit, int lane) {
     constexpr int PXW = px_words(NCH), WPP = NCH / 2;
     constexpr int M = PC > 0 ? (PC * PC + 31) / 32 : (MAXP * MAXP) / 32;   // pixels per lane
+    static_assert(SP == 0 || (NCH == 6 && PC == 15), "fixed-pitch rows: six channels, P = 15");
     int cur_dir = -1, P = 0, h = 0;
     unsigned off[M];                 // byte offset of lane pixel m from a patch corner
     unsigned vmask = 0;              // bit m: lane pixel m lies in the patch
+    unsigned lane_off = 0;           // SP > 0: byte offset of the lane's first pixel
+    int r0 = 0, lcol = 0;            //         its patch row (0, 1) and column
     for (int n = 0;; ++n) {
         const int t = blockIdx.x + n * gridDim.x;
         if (t >= S.total) break;
@@ -541,6 +605,15 @@ __device__ void pr_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
         const RowHdr H = hdr[b];
         const RowGeom& G = geom[H.dir];
         const DirLvl& D = B.d[H.pair][H.dir];
+        if (H.dir != cur_dir && SP > 0) {   // rows 2 m + r0 of column lcol
+            cur_dir = H.dir;
+            P = PC;
+            h = P / 2;
+            r0 = lane < 15 ? 0 : 1;
+            lcol = lane < 30 ? lane % 15 : lane - 15;
+            lane_off = 4u * (unsigned)(r0 * SP + lcol * 4);
+            vmask = lane < 30 ? (lane < 15 ? 0xffu : 0x7fu) : 0u;
+        }
         if (H.dir != cur_dir) {      // the lane's pixels k = lane + 32 m of a P x P patch
             cur_dir = H.dir;
             P = PC > 0 ? PC : G.P;
@@ -586,6 +659,8 @@ __device__ void pr_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
                                            roff + (P - 1) * G.sp + P * PXW <= G.sp * G.ref_h,
                                            B.err[H.pair]);
                 const unsigned rbase = buf + 4u * (unsigned)(rok ? roff : 0);
+                if constexpr (SP > 0) pr_ref_rows<SP>(ra, rbase + lane_off, vmask);
+                else
 #pragma unroll
                 for (int m = 0; m < M; ++m) {
                     // (pixel m of every lane lies in the patch for m < P^2 / 32)
@@ -608,7 +683,10 @@ __device__ void pr_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
                 if (slot >= 0) {
                     if (PGM_CHECK((slot & 0xffff) + (P - 1) * G.sp + P * PXW <= G.sp * G.win_h &&
                                   (slot >> 16) < G.cwp * G.ch, B.err[H.pair])) {
-                        pr_acc_sh<NCH, M>(ra, off, a_win + 4u * (unsigned)(slot & 0xffff), l, hh);
+                        if constexpr (SP > 0)
+                            pr_acc_rows<SP>(ra, a_win + 4u * (unsigned)(slot & 0xffff) + lane_off, l, hh);
+                        else
+                            pr_acc_sh<NCH, M>(ra, off, a_win + 4u * (unsigned)(slot & 0xffff), l, hh);
                         sb = lds64(a_sb + 8u * (unsigned)(slot >> 16));
                     } else {
                         sb = 0;
@@ -616,7 +694,10 @@ __device__ void pr_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
                 } else {
                     if (PGM_CHECK(qx >= 0 && qy >= 0 && qx < D.tw && qy < D.th && h <= BORD,
                                   B.err[H.pair])) {
-                        pr_acc_glob<NCH, M>(ra, t32, tpw, qx - h, qy - h, P, lane, l, hh);
+                        if constexpr (SP > 0)
+                            pr_acc_glob_rows(ra, t32, tpw, qx - h, qy - h, r0, lcol, vmask, l, hh);
+                        else
+                            pr_acc_glob<NCH, M>(ra, t32, tpw, qx - h, qy - h, P, lane, l, hh);
                         sb = D.sb2[(size_t)qy * D.sbp + qx];
                     } else {
                         sb = 0;
@@ -709,7 +790,7 @@ __device__ void pr_consume(const LvlBatch& B, const MatchConst& mc, const RowSch
 
 // One colour phase (or the cost refresh alone, mc.cost_only) of one or both
 // directions for all pairs of the launch.
-template <int NCH, int PC>
+template <int NCH, int PC, int SP = 0>
 __global__ void __launch_bounds__(32 * (PR_PROD + pr_cons(NCH, PC)), 1)
 k_pm_r(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_constant__ RowSched S,
        const __grid_constant__ RowMaps TM, const int buf_words, const int nbuf,
@@ -744,7 +825,7 @@ k_pm_r(const __grid_constant__ LvlBatch B, const MatchConst mc, const __grid_con
         pr_produce<NCH, false, PR_PROD, PR_NBUF>(B, mc, S, TM, buf_words, nbuf, a_sm, s_rec, s_hdr, s_next, s_geom, full0,
                         empty0, abort, limit, warp - pr_cons(NCH, PC), lane);
     else
-        pr_consume<NCH, PC>(B, mc, S, buf_words, nbuf, a_sm, sm, s_rec, s_hdr, s_next, s_geom,
+        pr_consume<NCH, PC, SP>(B, mc, S, buf_words, nbuf, a_sm, sm, s_rec, s_hdr, s_next, s_geom,
                             full0, empty0, abort, limit, lane);
 }
 
@@ -1496,7 +1577,7 @@ static RowMaps& pr_maps(const LvlBatch& B, int nch, bool bits, const RowSched& S
 // wait limit of the kernel's mbarrier waits (cycles); set by pgm_set_wait_limit
 long long wait_limit();
 
-template <int NCH, int PC, bool BITS = false>
+template <int NCH, int PC, bool BITS = false, int SP = 0>
 pgm_status launch_r(const LvlBatch& B, const MatchConst& mc, const RowSched& S, const RowMaps& TM,
                     int buf_words, cudaStream_t st) {
     const int sms = device_sms();
@@ -1504,7 +1585,7 @@ pgm_status launch_r(const LvlBatch& B, const MatchConst& mc, const RowSched& S, 
     // bit planes: one seed per lane once every consumer warp of a CTA has
     // tiles of its own, else the warp-per-seed form (coarse levels)
     const bool per_lane = BITS && S.total >= PS_CONS * sms;
-    auto kern = k_pm_r<NCH, PC>;
+    auto kern = k_pm_r<NCH, PC, SP>;
     if constexpr (BITS) kern = per_lane ? k_pm_s<NCH, PC> : k_pm_b<NCH, PC>;
     if (pgm_status r = smem_opt_in((const void*)kern); r != PGM_OK) return r;
     // the ring: as many buffers as fit beside the kernel's static shared
@@ -1531,8 +1612,15 @@ pgm_status launch_r(const LvlBatch& B, const MatchConst& mc, const RowSched& S, 
 // for the common 6-channel patches (15, 11) and 2-channel ones (15, 11, 8),
 // else the run-time form.
 template <int NCH>
-pgm_status launch_dir(const LvlBatch& B, const MatchConst& mc, const RowSched& S, int P,
+pgm_status launch_dir(const LvlBatch& B, const MatchConst& mc, const RowSched& S, const RowGeom& G,
                       const RowMaps& TM, int buf_words, cudaStream_t st) {
+    const int P = G.P;
+    // fixed-pitch rows: their one-past reads must land in the next region
+    if constexpr (NCH == 6)
+        if (P == 15 && G.sp == PR_ROWS_SP && G.pxw == 4 && G.off_win >= G.sp * G.ref_h &&
+            G.off_sb - G.off_win >= G.sp * G.win_h && G.words - G.off_sb >= G.sp + 4 * (P + 2) &&
+            G.sp / 4 >= G.win_w + 2)
+            return launch_r<NCH, 15, false, PR_ROWS_SP>(B, mc, S, TM, buf_words, st);
     if (P == 15) return launch_r<NCH, 15>(B, mc, S, TM, buf_words, st);
     if (P == 11) return launch_r<NCH, 11>(B, mc, S, TM, buf_words, st);
     if (NCH == 2 && P == 8) return launch_r<NCH, 8>(B, mc, S, TM, buf_words, st);
@@ -1588,8 +1676,8 @@ pgm_status launch_pm_tile(const LvlBatch& B, const MatchConst& mc, int nch, int 
             r = nch == 2 ? launch_r<2, 0, true>(B, mc, S[d], TM, G[d].words, sd)
                          : launch_r<6, 0, true>(B, mc, S[d], TM, G[d].words, sd);
         else
-            r = nch == 2 ? launch_dir<2>(B, mc, S[d], G[d].P, TM, G[d].words, sd)
-                         : launch_dir<6>(B, mc, S[d], G[d].P, TM, G[d].words, sd);
+            r = nch == 2 ? launch_dir<2>(B, mc, S[d], G[d], TM, G[d].words, sd)
+                         : launch_dir<6>(B, mc, S[d], G[d], TM, G[d].words, sd);
         if (r != PGM_OK) return r;
         ++*nlaunch;
     }
