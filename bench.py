@@ -147,7 +147,7 @@ DEVICE_MARK = "// Host side: launch configuration.  No device code below this li
 TRAFFIC_PAIRS = 8
 TRAFFIC_CMD = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                "--clock-control none --nvtx --nvtx-include \"pgm_match/level 0/\" "
-               "-k regex:k_pm_r -s 4 -c 2 --csv --log-file gpurun_out/k_pm_r_traffic.csv "
+               "-k regex:k_pm_r -s 4 -c 2 --csv --log-file k_pm_r_traffic.csv "
                "python bench.py --steps 1 --warmup 3 --batch %d --no-cpu-baseline --no-variants "
                "--serve 0 --tuning 2,32" % TRAFFIC_PAIRS)
 
