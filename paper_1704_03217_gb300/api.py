@@ -176,6 +176,44 @@ class Workspace:
                                           C.c_void_p(self.buf.data_ptr()), self.buf.numel(),
                                           _stream(stream)), "device status")
 
+    def dump(self, path):
+        """Write the fields of every level and direction to an .npz file, for
+        debugging: arrays ``l<level>_d<dir>_ux / _uy`` (int16), ``_cost``
+        (uint64) and ``_flags`` (uint8: bit 0 initialised, bit 1 outlier, bit 2
+        outlier record initialised), the pair's dims and the parameters as
+        JSON.  Reads the buffer (a device synchronisation on CUDA)."""
+        import json
+        import numpy as np
+        out = {"dims": np.array(self.dims, dtype=np.int32),
+               "params": np.array(json.dumps(asdict(self.params)))}
+        for level in range(self.params.levels):
+            for d in (0, 1):
+                nx, ny, ou, oc, of = self.layout(level, d)
+                n = nx * ny
+                u = self.buf[ou:ou + 4 * n].view(torch.int16).view(ny, nx, 2).cpu().numpy()
+                k = "l%d_d%d_" % (level, d)
+                out[k + "ux"], out[k + "uy"] = u[..., 0].copy(), u[..., 1].copy()
+                out[k + "cost"] = self.buf[oc:oc + 8 * n].view(torch.int64).view(ny, nx) \
+                    .cpu().numpy().view(np.uint64)
+                out[k + "flags"] = self.buf[of:of + n].view(ny, nx).cpu().numpy()
+        np.savez_compressed(path, **out)
+
+
+def load_fields(path):
+    """Read a ``Workspace.dump`` file: (params dict, dims tuple, {(level, dir):
+    {"ux", "uy", "cost", "flags"}})."""
+    import json
+    import numpy as np
+    with np.load(path) as z:
+        params = json.loads(str(z["params"]))
+        dims = tuple(int(v) for v in z["dims"])
+        fields_ = {}
+        for key in z.files:
+            if key.startswith("l") and "_d" in key:
+                lv, d, name = key[1:].split("_", 2)
+                fields_.setdefault((int(lv), int(d[1:])), {})[name] = z[key]
+    return params, dims, fields_
+
 
 def nominal_evals(params: Params, w1, h1, w2, h2) -> int:
     return int(_lib.load().pgm_nominal_evals(C.byref(params.cstruct()), w1, h1, w2, h2))

@@ -18,7 +18,11 @@ Failures are contained to the request that caused them:
   - a request whose device-side status reports an error (a bounded wait that
     ran out, a failed bounds check) is evicted when its batch completes,
     without its matches; the others of the batch deliver theirs.
-``Faults`` injects the first two kinds on the host, for tests.
+``Faults`` injects failures of each kind on the host, for tests: from code,
+or from the environment as ``PGM_FAULT=alloc@5,admit@7,timeout@9`` (a failed
+slot allocation for request 5, request 7 refused at admission, request 9
+reported as if a bounded device wait had run out).  No injected fault touches
+the GPU: each one is decided on the host, between launches.
 
 The admission policy (``Scheduler``) is plain Python with no GPU dependency,
 so it is tested on the CPU with a fake clock; ``GpuExecutor`` runs batches
@@ -26,6 +30,7 @@ through the library's batched entry points, on buffers kept resident in a
 pool of slots (pyramids, workspace, match rows) reused across batches.
 """
 import collections
+import os
 import time
 from dataclasses import dataclass, field
 
@@ -52,11 +57,56 @@ class Request:
 
 @dataclass
 class Faults:
-    """Host-side fault injection: request ids whose launch fails as if an
-    allocation failed, and request ids reported with a device-side error when
-    their batch completes."""
+    """Host-side fault injection, by request id:
+      alloc_fail:   the launch of the request's batch fails as if a slot
+                    allocation failed (the batch is retried singly, the
+                    request evicted);
+      device_error: the request completes with a device-side error reported;
+      admit_reject: the request is refused when it arrives;
+      timeout:      the request completes as if a bounded wait of the search
+                    kernel had run out (PGM_ERR_TIMEOUT in its status word)."""
     alloc_fail: set = field(default_factory=set)
     device_error: set = field(default_factory=set)
+    admit_reject: set = field(default_factory=set)
+    timeout: set = field(default_factory=set)
+
+    KINDS = {"alloc": "alloc_fail", "admit": "admit_reject", "timeout": "timeout",
+             "device": "device_error"}
+
+    @classmethod
+    def parse(cls, spec):
+        """Faults from a spec such as ``alloc@5,admit@7,timeout@9+12``: comma-
+        separated ``kind@ids`` items, ids joined by ``+``; kinds alloc, admit,
+        timeout and device.  An empty spec injects nothing; anything else
+        malformed raises ValueError."""
+        f = cls()
+        for item in (spec or "").replace(" ", "").split(","):
+            if not item:
+                continue
+            kind, sep, ids = item.partition("@")
+            if not sep or kind not in cls.KINDS or not ids:
+                raise ValueError("PGM_FAULT item %r: expected kind@id with kind in %s"
+                                 % (item, "/".join(sorted(cls.KINDS))))
+            try:
+                rids = {int(x) for x in ids.split("+")}
+            except ValueError:
+                raise ValueError("PGM_FAULT item %r: request ids must be integers" % item) from None
+            getattr(f, cls.KINDS[kind]).update(rids)
+        return f
+
+    @classmethod
+    def from_env(cls, environ=None):
+        """Faults named by the PGM_FAULT environment variable (none if unset)."""
+        env = os.environ if environ is None else environ
+        return cls.parse(env.get("PGM_FAULT", ""))
+
+    def device_failure(self, rid):
+        """The device-side failure injected for request `rid`, or None."""
+        if rid in self.timeout:
+            return "PGM_ERR_TIMEOUT (injected: a bounded device wait ran out)"
+        if rid in self.device_error:
+            return "injected device error"
+        return None
 
 
 class LaunchError(RuntimeError):
@@ -69,10 +119,12 @@ class LaunchError(RuntimeError):
 
 class Scheduler:
     """FIFO admission under a byte budget.  ``bytes_of(req)`` is the device
-    memory a request holds while it is in flight."""
+    memory a request holds while it is in flight.  ``faults.admit_reject``
+    (default: from PGM_FAULT) names requests refused on arrival."""
 
-    def __init__(self, budget_bytes, max_batch, bytes_of):
+    def __init__(self, budget_bytes, max_batch, bytes_of, faults=None):
         self.budget, self.max_batch, self.bytes_of = int(budget_bytes), int(max_batch), bytes_of
+        self.faults = faults if faults is not None else Faults.from_env()
         self.waiting = collections.deque()
         self.in_use = 0
         self.peak = 0
@@ -80,11 +132,16 @@ class Scheduler:
         self.single = 0              # requests to admit one at a time (retries)
 
     def arrive(self, req, now=0.0):
-        """Queue a request; one larger than the whole budget is rejected
-        (returns False, req.error set)."""
+        """Queue a request; one larger than the whole budget, or named by
+        faults.admit_reject, is rejected (returns False, req.error set)."""
         req.nbytes = int(self.bytes_of(req))
-        if req.nbytes > self.budget:
-            req.error = "rejected: needs %d bytes, over the %d-byte budget" % (req.nbytes, self.budget)
+        err = None
+        if req.rid in self.faults.admit_reject:
+            err = "rejected: injected admission failure"
+        elif req.nbytes > self.budget:
+            err = "rejected: needs %d bytes, over the %d-byte budget" % (req.nbytes, self.budget)
+        if err is not None:
+            req.error = err
             req.done = now
             self.rejected.append(req)
             return False
@@ -157,15 +214,18 @@ def serve(requests, scheduler, executor, clock=time.perf_counter, idle_sleep=0.0
 
 
 def summary(done, wall=None):
-    """Latency and throughput of the matched requests; failed ones counted."""
+    """Latency and throughput of the matched requests; failed ones counted
+    (latencies are NaN when no request was matched)."""
     ok = [r for r in done if r.error is None]
-    lat = np.array([r.latency for r in ok]) * 1e3
+    lat = np.array([r.latency for r in ok], dtype=np.float64) * 1e3
     first = min(r.arrival for r in done)
     last = max(r.done for r in done)
     span = wall if wall is not None else (last - first)
+    pct = (lambda q: float(np.percentile(lat, q))) if ok else (lambda q: float("nan"))
     return {"requests": len(done), "failed": len(done) - len(ok),
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "pairs_per_s": len(ok) / span}
+            "p50_ms": pct(50), "p99_ms": pct(99),
+            "mean_ms": float(lat.mean()) if ok else float("nan"),
+            "pairs_per_s": len(ok) / span if span > 0 else float("nan")}
 
 
 class GpuExecutor:
@@ -180,7 +240,7 @@ class GpuExecutor:
         from . import api
         self.torch, self.api = torch, api
         self.params, self.device = params, device
-        self.faults = faults or Faults()
+        self.faults = faults if faults is not None else Faults.from_env()
         self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
         self.next = 0
         self.inflight = []            # (event, batch, slots)
@@ -267,7 +327,7 @@ class GpuExecutor:
                 for r, sl in zip(batch, slots):
                     try:
                         sl["ws"].sync_status()          # device-side status word of the pair
-                        failed = "injected device error" if r.rid in self.faults.device_error else None
+                        failed = self.faults.device_failure(r.rid)
                     except RuntimeError as e:
                         failed = str(e)
                     if failed:

@@ -21,8 +21,8 @@ class FakeClock:
 class FakeExecutor:
     """A batch of n requests finishes `base + per * n` seconds after launch.
     Faults as in the GPU executor: a launch containing a request of
-    faults.alloc_fail raises; a request of faults.device_error completes
-    without matches."""
+    faults.alloc_fail raises; a request of faults.device_error or
+    faults.timeout completes without matches."""
 
     def __init__(self, clock, base=0.02, per=0.005, faults=None):
         self.clock, self.base, self.per = clock, base, per
@@ -42,8 +42,9 @@ class FakeExecutor:
         self.inflight = [(t, b) for t, b in self.inflight if t > self.clock.t]
         for b in done:
             for r in b:
-                if r.rid in self.faults.device_error:
-                    r.error, r.matches = "evicted: injected device error", None
+                failed = self.faults.device_failure(r.rid)
+                if failed:
+                    r.error, r.matches = "evicted: %s" % failed, None
                 else:
                     r.matches = np.array([[r.rid]])
         return done
@@ -97,7 +98,7 @@ def test_request_over_budget_is_rejected_and_the_loop_goes_on():
 def _run(faults, n=30, max_batch=4):
     clock = FakeClock()
     ex = FakeExecutor(clock, faults=faults)
-    sch = Scheduler(budget_bytes=12, max_batch=max_batch, bytes_of=lambda r: 3)
+    sch = Scheduler(budget_bytes=12, max_batch=max_batch, bytes_of=lambda r: 3, faults=faults)
     return serve(_reqs(n, 0.002), sch, ex, clock=clock, idle_sleep=0), sch, ex
 
 
@@ -127,3 +128,54 @@ def test_device_error_evicts_only_that_request():
             assert b.error is None and (a.matches == b.matches).all()
     s = summary(reqs)
     assert s["failed"] == 3 and s["requests"] == 30 and sch.in_use == 0
+
+
+def test_fault_spec():
+    f = Faults.parse("alloc@5,admit@7, timeout@9+12,device@3")
+    assert (f.alloc_fail, f.admit_reject, f.timeout, f.device_error) == ({5}, {7}, {9, 12}, {3})
+    assert Faults.parse("") == Faults() == Faults.from_env({})
+    assert Faults.from_env({"PGM_FAULT": "admit@1+2"}).admit_reject == {1, 2}
+    assert "PGM_ERR_TIMEOUT" in f.device_failure(9) and f.device_failure(4) is None
+    for bad in ("alloc", "alloc@", "oom@3", "alloc@x", "@4"):
+        with pytest.raises(ValueError):
+            Faults.parse(bad)
+
+
+def test_admission_fault_rejects_only_that_request():
+    clean, _, _ = _run(Faults())
+    reqs, sch, ex = _run(Faults(admit_reject={7, 8}))
+    assert [r.rid for r in sch.rejected] == [7, 8]
+    assert all(reqs[k].error == "rejected: injected admission failure" for k in (7, 8))
+    assert all(rid not in (7, 8) for b in ex.launched for rid in b)
+    for a, b in zip(clean, reqs):
+        if b.rid not in (7, 8):
+            assert b.error is None and (a.matches == b.matches).all()
+    assert sch.in_use == 0 and summary(reqs)["failed"] == 2
+
+
+def test_pgm_fault_environment_drives_every_kind(monkeypatch):
+    """PGM_FAULT alone (no Faults passed) injects all three host-side kinds
+    into one run: the named requests fail with their own reasons, the others
+    get exactly the matches of a run without faults."""
+    clean, _, _ = _run(Faults())
+    monkeypatch.setenv("PGM_FAULT", "alloc@5,admit@11,timeout@20")
+    clock = FakeClock()
+    ex = FakeExecutor(clock, faults=Faults.from_env())
+    sch = Scheduler(budget_bytes=12, max_batch=4, bytes_of=lambda r: 3)     # reads PGM_FAULT
+    reqs = serve(_reqs(30, 0.002), sch, ex, clock=clock, idle_sleep=0)
+    err = {r.rid: r.error for r in reqs if r.error}
+    assert sorted(err) == [5, 11, 20]
+    assert "allocation" in err[5] and err[11].startswith("rejected") and "PGM_ERR_TIMEOUT" in err[20]
+    for a, b in zip(clean, reqs):
+        if b.rid not in err:
+            assert b.error is None and (a.matches == b.matches).all()
+    assert sch.in_use == 0 and sch.peak <= 12
+
+
+def test_summary_when_every_request_failed():
+    reqs = _reqs(3, 0.01)
+    for r in reqs:
+        r.error, r.done = "evicted: x", r.arrival + 0.5
+    s = summary(reqs)
+    assert s["failed"] == 3 and s["pairs_per_s"] == 0.0
+    assert np.isnan(s["p50_ms"]) and np.isnan(s["p99_ms"]) and np.isnan(s["mean_ms"])
