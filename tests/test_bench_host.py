@@ -64,3 +64,17 @@ def test_lattice_sizes_match_the_abi_field_layout():
             assert L.pgm_field_layout(C.byref(cp), w, h, w, h, level, 0, C.byref(nx), C.byref(ny),
                                       C.byref(o1), C.byref(o2), C.byref(o3)) == 0
             assert n[level] == nx.value * ny.value
+
+
+def test_paper_timings_are_the_table_3_figures():
+    """The paper's per-pair times quoted beside the measurements: each variant
+    on both datasets, the direction-only variants faster than their
+    full-gradient twins as Table 3 has them."""
+    t = bench.PAPER_TIMINGS["s_per_pair"]
+    assert set(t) == {"PGM-C", "PGM-G", "PGM-CD", "PGM-GD", "PGM-C3", "PGM-G3"}
+    assert t["PGM-C"] == {"sintel": 3.49, "kitti2012": 4.55}
+    for full, fast in (("PGM-C", "PGM-CD"), ("PGM-G", "PGM-GD"), ("PGM-C", "PGM-C3"),
+                       ("PGM-G", "PGM-G3")):
+        assert all(t[fast][d] < t[full][d] for d in ("sintel", "kitti2012"))
+    import json
+    json.dumps(bench.PAPER_TIMINGS)
