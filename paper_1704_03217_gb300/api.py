@@ -215,6 +215,28 @@ def load_fields(path):
     return params, dims, fields_
 
 
+# the pgm_params fields that fix a pyramid buffer's layout and contents
+PYRAMID_FIELDS = ("levels", "sobel", "color", "descriptor", "cs_sched")
+
+
+def check_pyramids(params: Params, *pyrs) -> None:
+    """pgm_match and pgm_interpolate take pyramid buffers without their sizes
+    and read them with the layout `params` implies.  Refuse, before the call,
+    a pyramid built under other layout parameters (it would be read with the
+    wrong layout, possibly past its end) or a buffer smaller than the layout."""
+    L = _lib.load()
+    cp = params.cstruct()
+    for p in pyrs:
+        diff = [f for f in PYRAMID_FIELDS if getattr(p.params, f) != getattr(params, f)]
+        if diff:
+            raise ValueError("pyramid built with other %s than the call's parameters"
+                             % ", ".join(diff))
+        need = L.pgm_pyramid_bytes(C.byref(cp), p.w, p.h)
+        if need == 0 or p.buf.numel() < need:
+            raise ValueError("pyramid buffer of %d bytes, the layout needs %d"
+                             % (p.buf.numel(), need))
+
+
 def nominal_evals(params: Params, w1, h1, w2, h2) -> int:
     return int(_lib.load().pgm_nominal_evals(C.byref(params.cstruct()), w1, h1, w2, h2))
 
@@ -225,6 +247,7 @@ def build_pyramid(params: Params, img: torch.Tensor, stream=None) -> Pyramid:
 
 def match(params: Params, pyr1: Pyramid, pyr2: Pyramid, stream_id: int = 0,
           ws: Workspace = None, stream=None) -> Workspace:
+    check_pyramids(params, pyr1, pyr2)
     if ws is None:
         ws = Workspace(params, pyr1.w, pyr1.h, pyr2.w, pyr2.h, pyr1.buf.device)
     cp = params.cstruct()
@@ -237,6 +260,9 @@ def match(params: Params, pyr1: Pyramid, pyr2: Pyramid, stream_id: int = 0,
 
 def match_batch(params: Params, pyrs1, pyrs2, stream_ids, wss, stream=None):
     n = len(pyrs1)
+    if not (len(pyrs2) == len(stream_ids) == len(wss) == n):
+        raise ValueError("match_batch: pyrs1, pyrs2, stream_ids and wss differ in length")
+    check_pyramids(params, *pyrs1, *pyrs2)
     cp = params.cstruct()
     P1 = (C.c_void_p * n)(*[p.buf.data_ptr() for p in pyrs1])
     P2 = (C.c_void_p * n)(*[p.buf.data_ptr() for p in pyrs2])
@@ -373,6 +399,7 @@ def interpolate(params: Params, pyr1: Pyramid, matches: torch.Tensor, count: tor
     """Dense flow (h, w, 2) float32 of image 1 from exported matches
     (n, 4) int32 and their device count (pgm_interpolate).  Returns (flow,
     workspace); the workspace starts with the (h, w, k) uint64 neighbour keys."""
+    check_pyramids(params, pyr1)
     ip = ip or InterpParams()
     cip = ip.cstruct()
     L = _lib.load()

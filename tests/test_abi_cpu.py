@@ -111,3 +111,34 @@ def test_noalloc_rejects_misaligned_pointers():
         code = L.pgm_filter_noalloc(C.byref(cp), 8, 8, C.c_void_p(a["u"]), C.c_void_p(a["f"]),
                                     C.c_void_p(a["m"]), 64, C.c_void_p(a["c"]), None)
         assert code == 1, (bad, code)
+
+
+def test_binding_refuses_pyramids_of_another_layout():
+    """pgm_match and pgm_interpolate take pyramid buffers without their sizes,
+    so the binding refuses, before calling the library, a pyramid built under
+    other layout parameters or a buffer smaller than the layout (buffers in
+    host memory here: nothing reaches the library's compute calls)."""
+    import torch
+    from paper_1704_03217_gb300 import api, build
+    build.build()
+    p = api.Params(levels=4, color=1)
+    P1 = api.Pyramid(p, 64, 48, device="cpu")
+    P2 = api.Pyramid(p, 64, 48, device="cpu")
+    for other in (dict(levels=3), dict(color=0), dict(descriptor=1), dict(sobel=3),
+                  dict(cs_sched=1)):
+        q = p.replace(**other)
+        with pytest.raises(ValueError, match=next(iter(other))):
+            api.match(q, P1, P2)
+        with pytest.raises(ValueError):
+            api.match_batch(q, [P1], [P2], [0], [None])
+        with pytest.raises(ValueError):
+            api.interpolate(q, P1, torch.zeros((1, 4), dtype=torch.int32),
+                            torch.zeros(1, dtype=torch.int32))
+    # parameters that do not change the pyramid pass the check
+    api.check_pyramids(p.replace(iters_fine=2, philox_key=7, patch_fwd=9, seed_stride=2), P1, P2)
+    short = api.Pyramid(p, 64, 48, device="cpu")
+    short.buf = short.buf[:-1]
+    with pytest.raises(ValueError, match="needs"):
+        api.match(p, P1, short)
+    with pytest.raises(ValueError, match="length"):
+        api.match_batch(p, [P1, P1], [P2], [0, 1], [None, None])
