@@ -342,6 +342,18 @@ pgm_status pgm_get_tuning(pgm_tuning* t);
  * makes the first wait run out).  Errors: PGM_ERR_ARG (cycles < 0). */
 pgm_status pgm_set_wait_limit(int64_t cycles);
 
+/* Host-side fault injection, for failure-handling tests (no counterpart in
+ * the paper).  Counting from this call, over the following pgm_match and
+ * pgm_match_batch calls of every thread, the `steps`-th launch step of the
+ * matching schedule (the box sums of a level, the initialisation or a
+ * transfer, a cost refresh, a colour phase, a consistency check) is not
+ * enqueued: that call returns PGM_ERR_CUDA at once, pgm_error_detail names
+ * the step, and the work the call had already enqueued -- including what it
+ * forked onto its auxiliary streams -- is joined back to its stream, as on
+ * any failure part-way through a call.  The failure fires once; 0 disarms.
+ * Nothing reaches the GPU.  Errors: PGM_ERR_ARG (steps < 0). */
+pgm_status pgm_inject_launch_failure(int steps);
+
 /* 1 in the checked build (libpgm_checked.so, compiled with -DPGM_CHECKED):
  * the search, initialisation and consistency kernels check their shared-
  * and global-memory indices; a failed check sets PGM_ERR_DEVICE_BOUNDS in the

@@ -37,6 +37,7 @@ EXPORTS = [
     "pgm_filter_noalloc", "pgm_build_pyramid_batch", "pgm_filter_batch", "pgm_set_tuning",
     "pgm_get_tuning", "pgm_set_wait_limit", "pgm_error_detail", "pgm_interp_default_params",
     "pgm_interp_workspace_bytes", "pgm_interpolate", "pgm_checked_build",
+    "pgm_inject_launch_failure",
 ]
 
 
@@ -99,6 +100,7 @@ def load(path: str = LIB_PATH):
     L.pgm_set_tuning.argtypes = [C.POINTER(CTuning)]; L.pgm_set_tuning.restype = C.c_int
     L.pgm_get_tuning.argtypes = [C.POINTER(CTuning)]; L.pgm_get_tuning.restype = C.c_int
     L.pgm_set_wait_limit.argtypes = [C.c_int64]; L.pgm_set_wait_limit.restype = C.c_int
+    L.pgm_inject_launch_failure.argtypes = [C.c_int]; L.pgm_inject_launch_failure.restype = C.c_int
     L.pgm_checked_build.argtypes = []; L.pgm_checked_build.restype = C.c_int
     L.pgm_interp_default_params.argtypes = [C.POINTER(CInterp)]; L.pgm_interp_default_params.restype = None
     L.pgm_interp_workspace_bytes.argtypes = [i32, i32, C.POINTER(CInterp)]

@@ -47,6 +47,21 @@ pgm_status cuda_fail(const char* site, cudaError_t e) {
     return PGM_ERR_CUDA;
 }
 
+// ------------------------------------------- host-side fault injection
+// pgm_inject_launch_failure: a countdown over the launch steps of the
+// matching schedule, process-wide; the step that takes it from 1 to 0 fails.
+static std::atomic<int> g_fail_step{0};
+static bool fault_due() {
+    int v = g_fail_step.load(std::memory_order_relaxed);
+    while (v > 0 && !g_fail_step.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) {
+    }
+    return v == 1;
+}
+static pgm_status injected_fail(const char* site) {
+    snprintf(g_detail, sizeof(g_detail), "%s: injected launch failure", site);
+    return PGM_ERR_CUDA;
+}
+
 // ------------------------------------------------------------ tuning knobs
 static std::atomic<int> g_slack{2}, g_chunk{MAXB}, g_tile_w{8};
 Tuning tuning() { return Tuning{g_slack.load(), g_chunk.load(), g_tile_w.load()}; }
@@ -336,7 +351,17 @@ static pgm_status aux_get(cudaStream_t st, Aux** out) {
     return PGM_OK;
 }
 
-pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) {
+// What a call has forked onto its auxiliary streams and not yet joined back
+// to the caller's stream.
+struct Forks {
+    Aux* aux = nullptr;
+    bool s_forked = false;       // aux->s waits on this call's work
+    bool box_open[MAXL] = {};    // box sums of level l pending on aux->s
+    bool s2_open = false;        // backward search phases pending on aux->s2
+};
+
+pgm_status run_batch_forked(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st,
+                            Forks& fk) {
     Schedule sch;
     make_schedule(p, &sch);
     const int nch = ctx[0].a.nch;
@@ -362,9 +387,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
     // they overlap the initialisation and the coarse visits, and each is
     // joined back before the first visit at its level (the kernel time
     // profile keeps them on the caller's stream).
-    bool joined[MAXL];
-    for (int l = 0; l < MAXL; ++l) joined[l] = true;
-    Aux* aux = nullptr;
+    Aux*& aux = fk.aux;
     bool aux_tried = false, forked = false;
     if (p->norm == PGM_L2SQ) {
         bool needed[MAXL] = {false};
@@ -381,6 +404,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
                 PGM_TRY(cudaEventRecord(aux->fork, st), "match: fork box sums");
                 PGM_TRY(cudaStreamWaitEvent(aux->s, aux->fork, 0), "match: fork box sums");
                 forked = true;
+                fk.s_forked = true;
             }
             memset(&B, 0, sizeof(B));
             B.n = n; B.level = l;
@@ -400,11 +424,12 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
                 (l != l0 || init_bits_fits(B)))
                 continue;
             const bool on_aux = l != l0 && aux;
+            if (fault_due()) return injected_fail("match: box sums");
             pgm_status r = launch_box(B, nch, max_px, on_aux ? aux->s : st);
             if (r != PGM_OK) return r;
             if (on_aux) {
                 PGM_TRY(cudaEventRecord(aux->lvl[l], aux->s), "match: box sums done");
-                joined[l] = false;
+                fk.box_open[l] = true;
             }
         }
     }
@@ -413,9 +438,9 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
         char rname[16];
         snprintf(rname, sizeof(rname), "level %d", l);
         Range visit_range(rname);
-        if (!joined[l]) {
+        if (fk.box_open[l]) {
             PGM_TRY(cudaStreamWaitEvent(st, aux->lvl[l], 0), "match: join box sums");
-            joined[l] = true;
+            fk.box_open[l] = false;
         }
         memset(&B, 0, sizeof(B));
         B.n = n; B.level = l; B.visit = v;
@@ -433,6 +458,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
             B.err[k] = reinterpret_cast<uint32_t*>(ctx[k].ws + ctx[k].w.off_err);
         }
         pgm_status r;
+        if (fault_due()) return injected_fail(v == 0 ? "match: initialisation" : "match: transfer");
         if (v == 0) {
             r = launch_init(B, mc, nch, maxP, max_seeds, st);
         } else {
@@ -460,6 +486,7 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
         const int T = iters_at(p, l);
         const bool fused = T > 0 && pm_tile_fits(B, mc, nch);
         if (!fused) {
+            if (fault_due()) return injected_fail("match: cost refresh");
             r = launch_cost_fill(B, mc, nch, maxP, max_seeds, st);
             if (r != PGM_OK) return r;
         }
@@ -478,23 +505,50 @@ pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) 
                 PGM_TRY(cudaEventRecord(aux->sfork, st), "match: fork backward search");
                 PGM_TRY(cudaStreamWaitEvent(aux->s2, aux->sfork, 0), "match: fork backward search");
                 st2 = aux->s2;
+                fk.s2_open = true;
             }
         }
         for (int t = 0; t < T; ++t)
             for (int col = 0; col < 2; ++col) {
                 mc.t = t; mc.colour = col; mc.refresh = fused && t == 0;
+                if (fault_due()) return injected_fail("match: search phase");
                 r = launch_pm_phase(B, mc, nch, maxP, max_half, st, st2);
                 if (r != PGM_OK) return r;
             }
         if (st2) {
             PGM_TRY(cudaEventRecord(aux->sjoin, st2), "match: join backward search");
             PGM_TRY(cudaStreamWaitEvent(st, aux->sjoin, 0), "match: join backward search");
+            fk.s2_open = false;
         }
         mc.t = 0; mc.colour = 0; mc.refresh = 0;
+        if (fault_due()) return injected_fail("match: consistency");
         r = launch_consist(B, mc, max_seeds, st);
         if (r != PGM_OK) return r;
     }
     return PGM_OK;
+}
+
+// The whole schedule on a batch.  A call that fails part-way may leave work
+// forked onto the auxiliary streams; it is joined back to `st` before the
+// call returns, so that none of it runs unordered after the caller's stream
+// (where it could write into a workspace the caller has already released)
+// and a stream capture stays joined.  On success every fork is already
+// joined and nothing is added.
+pgm_status run_batch(const pgm_params* p, PairCtx* ctx, int n, cudaStream_t st) {
+    Forks fk;
+    const pgm_status r = run_batch_forked(p, ctx, n, st, fk);
+    bool box = fk.s_forked && r != PGM_OK;
+    for (int l = 0; l < MAXL; ++l) box = box || fk.box_open[l];
+    if (fk.aux && box) {
+        cudaEventRecord(fk.aux->fork, fk.aux->s);
+        cudaStreamWaitEvent(st, fk.aux->fork, 0);
+    }
+    if (fk.aux && fk.s2_open) {
+        cudaEventRecord(fk.aux->sjoin, fk.aux->s2);
+        cudaStreamWaitEvent(st, fk.aux->sjoin, 0);
+    }
+    if (r != PGM_OK) (void)cudaGetLastError();    // the status already reports the failure
+    return r;
 }
 
 pgm_status prepare_pair(const pgm_params* p, const void* pyr1, const void* pyr2, int w1, int h1,
@@ -787,6 +841,12 @@ pgm_status pgm_set_tuning(const pgm_tuning* t) {
     g_slack = t->window_slack;
     g_chunk = t->pairs_per_launch;
     g_tile_w = t->tile_w;
+    return PGM_OK;
+}
+
+pgm_status pgm_inject_launch_failure(int steps) {
+    if (steps < 0) return PGM_ERR_ARG;
+    g_fail_step.store(steps, std::memory_order_relaxed);
     return PGM_OK;
 }
 

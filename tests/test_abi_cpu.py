@@ -85,6 +85,14 @@ def test_size_queries_and_argument_checks(lib):
     assert lib.pgm_filter(C.byref(p), 64, 64, 64, 64, None, 1 << 20, None, 0, None, None, None) == 1
 
 
+def test_fault_injection_arguments(lib):
+    """pgm_inject_launch_failure arms and disarms without touching the device;
+    a negative step count is refused."""
+    assert lib.pgm_inject_launch_failure(-1) == 1
+    assert lib.pgm_inject_launch_failure(5) == 0
+    assert lib.pgm_inject_launch_failure(0) == 0
+
+
 def test_nominal_evals_match_hand_count(lib):
     """Hand count for 256x192, L = 3, stride 3, 6 iterations everywhere:
     lattices 85x64, 43x32, 21x16; visits 2,1,2,1,2,1,0; per seed and
