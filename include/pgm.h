@@ -175,7 +175,11 @@ size_t pgm_match_workspace_bytes(const pgm_params* p, int w1, int h1, int w2, in
  *                   different pairs draw independent numbers.
  *   d_ws:           >= pgm_match_workspace_bytes, 256-byte aligned; it
  *                   receives the fields of every level and both directions
- *                   and must be kept for pgm_filter / pgm_field_layout.
+ *                   and must be kept for pgm_filter / pgm_field_layout.  Its
+ *                   contents on entry do not matter: the call first clears
+ *                   the status word and the evaluation counters, so
+ *                   pgm_sync_status then reports this call's device-side
+ *                   failures.
  * Schedule (m = L-1): exhaustive nearest-neighbour init at m, then
  * [m-1, m] x N with field and outlier record, then m-1 with the field only,
  * then m-2 .. 0.  Each visit: cost of the current field, `iters` iterations
@@ -287,7 +291,7 @@ pgm_status pgm_sync_status(const pgm_params* p, int w1, int h1, int w2, int h2, 
  * backward; exhaustive initialisation forward, backward; and, of the
  * propagation/search and refresh ones, those scored outside the
  * shared-memory window (from global memory) forward, backward.  pgm_match
- * and pgm_match_batch zero them at their start. */
+ * and pgm_match_batch zero them, and the status word, at their start. */
 #define PGM_WS_EVALS_OFFSET 8
 #define PGM_WS_EVALS_COUNT 8
 

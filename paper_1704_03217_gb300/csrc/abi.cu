@@ -378,9 +378,9 @@ pgm_status run_batch_forked(const pgm_params* p, PairCtx* ctx, int n, cudaStream
     mc.descriptor = p->descriptor;
     static thread_local LvlBatch B;       // ~8 KB: kept off the stack
     static thread_local XferBatch X;
-    for (int k = 0; k < n; ++k)           // reset the evaluation counters
-        PGM_TRY(cudaMemsetAsync(ctx[k].ws + PGM_WS_EVALS_OFFSET, 0, 8 * PGM_WS_EVALS_COUNT, st),
-                "match: zero the counters");
+    for (int k = 0; k < n; ++k)           // reset the status word and the evaluation counters
+        PGM_TRY(cudaMemsetAsync(ctx[k].ws, 0, PGM_WS_EVALS_OFFSET + 8 * PGM_WS_EVALS_COUNT, st),
+                "match: zero the status word and counters");
     // per level and direction: box sums of |G|^2 over the target and the
     // reference patches.  The coarsest level's come first on the caller's
     // stream; the finer levels' are forked onto an auxiliary stream, where

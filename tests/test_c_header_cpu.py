@@ -6,29 +6,19 @@ pgm_tuning and pgm_interp_params; the workspace and no-allocation constants;
 the status codes).  The program makes host-side calls only (defaults, size
 queries, argument checks), so it runs without a GPU."""
 import ctypes as C
-import os
-import shutil
 import subprocess
 
 import pytest
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-
 
 @pytest.fixture(scope="module")
 def probe(tmp_path_factory):
-    cc = shutil.which("gcc") or shutil.which("cc")
-    if cc is None:
-        pytest.skip("no C compiler")
-    from paper_1704_03217_gb300 import build
-    lib = build.build()
-    libdir = os.path.dirname(lib)
+    from c_build import compile_c
     exe = str(tmp_path_factory.mktemp("cabi") / "probe")
-    cmd = [cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
-           "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "c_abi_probe.c"),
-           "-L", libdir, "-lpgm", "-Wl,-rpath," + libdir, "-o", exe]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    assert r.returncode == 0, r.stdout + r.stderr
+    ok, log = compile_c("c_abi_probe.c", exe)
+    if ok is None:
+        pytest.skip(log)
+    assert ok, log
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     out = {}
@@ -89,3 +79,16 @@ def test_calls_from_c_agree_with_the_binding(probe):
     assert int(probe["get_tuning"]) == 0 and int(probe["tuning_tile_w"]) == 8
     assert int(probe["set_tuning_bad"]) == 1          # tile_w 5 is rejected
     assert int(probe["checked_build"]) == 0
+
+
+def test_whole_path_program_builds(tmp_path):
+    """tests/c_match_pair.c, the whole path from C with cudaMalloc'ed buffers
+    (run on a GPU by tests/test_c_pipeline_gpu.py), compiles as strict C99
+    and links against libpgm.so and the CUDA runtime."""
+    from c_build import compile_c
+    ok, log = compile_c("c_match_pair.c", str(tmp_path / "c_match_pair"), cudart=True)
+    if ok is None:
+        pytest.skip(log)
+    assert ok, log
+    r = subprocess.run([str(tmp_path / "c_match_pair")], capture_output=True, text=True)
+    assert r.returncode == 2 and "usage" in r.stderr      # no arguments: usage, no CUDA call
