@@ -2,10 +2,12 @@
  * no Python and no PyTorch: device memory from cudaMalloc, the legacy default
  * stream.  Built and run by tests/test_c_pipeline_gpu.py.
  *
- *   c_match_pair W H LEVELS img1.rgb img2.rgb out.bin
+ *   c_match_pair W H LEVELS COLOR DESCRIPTOR img1.rgb img2.rgb out.bin
  *
- * img*.rgb: W x H interleaved RGB bytes.  The match workspace is filled with
- * 0xff before pgm_match (its contents on entry must not matter).  out.bin:
+ * img*.rgb: W x H interleaved RGB bytes; COLOR and DESCRIPTOR set
+ * pgm_params.color and .descriptor (the paper's defaults otherwise).  The
+ * pyramid buffers and the match workspace are filled with 0xff before use
+ * (their contents on entry must not matter).  out.bin:
  * int32 count, then count rows (x1, y1, x2, y2) int32.  Exit status 0 on
  * success; otherwise a message names the failing step. */
 #include <stdint.h>
@@ -50,23 +52,26 @@ int main(int argc, char** argv) {
     cudaError_t e;
     FILE* out;
 
-    if (argc != 7) {
-        fprintf(stderr, "usage: %s W H LEVELS img1.rgb img2.rgb out.bin\n", argv[0]);
+    if (argc != 9) {
+        fprintf(stderr, "usage: %s W H LEVELS COLOR DESCRIPTOR img1.rgb img2.rgb out.bin\n",
+                argv[0]);
         return 2;
     }
     w = atoi(argv[1]);
     h = atoi(argv[2]);
     levels = atoi(argv[3]);
     img_bytes = (size_t)w * h * 3;
-    h1 = read_file(argv[4], img_bytes);
-    h2 = read_file(argv[5], img_bytes);
+    h1 = read_file(argv[6], img_bytes);
+    h2 = read_file(argv[7], img_bytes);
     if (!h1 || !h2) {
         fprintf(stderr, "cannot read the images\n");
         goto done;
     }
 
-    pgm_default_params(&p);            /* PGM-C, the paper's settings */
+    pgm_default_params(&p);            /* the paper's settings */
     p.levels = levels;
+    p.color = atoi(argv[4]);
+    p.descriptor = atoi(argv[5]);
     pyr_bytes = pgm_pyramid_bytes(&p, w, h);
     ws_bytes = pgm_match_workspace_bytes(&p, w, h, w, h);
     if (!pyr_bytes || !ws_bytes) {
@@ -88,6 +93,8 @@ int main(int argc, char** argv) {
     }
     if ((e = cudaMemcpy(d_img1, h1, img_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(d_img2, h2, img_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(d_pyr1, 0xff, pyr_bytes)) != cudaSuccess ||
+        (e = cudaMemset(d_pyr2, 0xff, pyr_bytes)) != cudaSuccess ||
         (e = cudaMemset(d_ws, 0xff, ws_bytes)) != cudaSuccess) {
         rc = fail_cuda("copy in", e);
         goto done;
@@ -118,7 +125,7 @@ int main(int argc, char** argv) {
         rc = fail_cuda("copy the rows out", e);
         goto done;
     }
-    out = fopen(argv[6], "wb");
+    out = fopen(argv[8], "wb");
     if (!out) goto done;
     if (fwrite(&count, 4, 1, out) != 1 || fwrite(rows, 16, (size_t)count, out) != (size_t)count) {
         fclose(out);
