@@ -406,6 +406,18 @@ class Clocks:
 
 
 # --------------------------------------------------------------- GPU arm
+def optional_section(name, fn):
+    """Run one of the line's supplementary measurements; an exception there is
+    reported in its place (and on stderr) instead of ending the run, so that
+    the headline numbers, measured before, are still printed."""
+    try:
+        return fn()
+    except Exception as e:                        # reported, not hidden
+        import traceback
+        traceback.print_exc()
+        return {"error": "%s: %s: %s" % (name, type(e).__name__, e)}
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -617,8 +629,8 @@ def run_ours(a):
                              "int16 element MACs of Eq. 3's cross term per second; time of "
                              "the init class (clear, MMA and unpack launches)"}
 
-    variants = {}
-    if not a.no_variants:
+    def run_variants():
+        variants = {}
         for name, kw in VARIANTS.items():
             pv = prm.replace(**kw)
             mv = api.PairMatcher(pv, W_IMG, H_IMG, batch=B, device=dev)
@@ -644,22 +656,29 @@ def run_ours(a):
             del mv
         variants["note"] = ("pairs/s of the same 16 pairs, whole step graph-replayed; "
                             "gcand_evals_per_s nominal")
+        return variants
+
+    variants = {}
+    if not a.no_variants:
+        variants = optional_section("variants", run_variants)
 
     workloads = None
     if not a.no_variants and rank == 0:
-        workloads = run_workloads(api, prm, dev, flush, a.steps)
+        workloads = optional_section(
+            "workloads", lambda: run_workloads(api, prm, dev, flush, a.steps))
 
     batched = None
     if not a.no_variants and rank == 0:
-        batched = run_batched(api, prm, dev)
+        batched = optional_section("batched", lambda: run_batched(api, prm, dev))
 
     interp = None
     if not a.no_variants and rank == 0:
-        interp = run_interp(api, prm, m, dev, [p[2] for p in pairs])
+        interp = optional_section(
+            "interpolation", lambda: run_interp(api, prm, m, dev, [p[2] for p in pairs]))
 
     serving = None
     if a.serve > 0 and rank == 0:
-        serving = run_serving(api, prm, a.serve, dev)
+        serving = optional_section("serving", lambda: run_serving(api, prm, a.serve, dev))
 
     if rank == 0:
         cfg = config_dict(B, world)

@@ -78,3 +78,16 @@ def test_paper_timings_are_the_table_3_figures():
         assert all(t[fast][d] < t[full][d] for d in ("sintel", "kitti2012"))
     import json
     json.dumps(bench.PAPER_TIMINGS)
+
+
+def test_optional_section_reports_failures_in_place(capsys):
+    """A supplementary measurement that raises is reported in its place in the
+    line (and on stderr) instead of ending the run; one that works returns
+    its value."""
+    assert bench.optional_section("ok", lambda: {"x": 1}) == {"x": 1}
+
+    def broken():
+        raise RuntimeError("CUDA out of memory")
+    r = bench.optional_section("serving", broken)
+    assert r == {"error": "serving: RuntimeError: CUDA out of memory"}
+    assert "CUDA out of memory" in capsys.readouterr().err
