@@ -114,3 +114,20 @@ def test_workspace_layout(lib, w, h, prm):
                     spans.append((off, off + size))
         dims = [((x + 1) // 2, (y + 1) // 2) for x, y in dims]
     _disjoint(spans, "fields")
+
+
+def test_size_limits(lib):
+    """Images up to 32767 pixels a side are accepted (the largest PGM-C
+    pyramid is tens of GB, still addressed in 64 bits), one pixel more is
+    refused; the layout at the limit stays inside its buffer."""
+    from paper_1704_03217_gb300.api import Params
+    cp = Params(levels=5, color=1).cstruct()
+    big = lib.pgm_pyramid_bytes(C.byref(cp), 32767, 32767)
+    assert big > 2 * 2 * 32767 * 32767 * 16                # descriptor + split copy, 2 schemes
+    assert lib.pgm_pyramid_bytes(C.byref(cp), 32768, 64) == 0
+    assert lib.pgm_pyramid_bytes(C.byref(cp), 64, 32768) == 0
+    off, lw, lh, nch, row, px, bord = _desc(lib, cp, 32767, 32767, 1, 0)
+    assert off + 2 * row * (lh + bord) <= big
+    ws = lib.pgm_match_workspace_bytes(C.byref(cp), 32767, 32767, 32767, 32767)
+    assert ws > 2 * 13 * ((32767 - 2) // 3 + 1) ** 2      # u, cost, flags per seed, 2 directions
+    assert lib.pgm_match_workspace_bytes(C.byref(cp), 32768, 8, 8, 8) == 0
