@@ -216,6 +216,10 @@ def serve(requests, scheduler, executor, clock=time.perf_counter, idle_sleep=0.0
 def summary(done, wall=None):
     """Latency and throughput of the matched requests; failed ones counted
     (latencies are NaN when no request was matched)."""
+    if not done:
+        nan = float("nan")
+        return {"requests": 0, "failed": 0, "p50_ms": nan, "p99_ms": nan, "mean_ms": nan,
+                "pairs_per_s": 0.0}
     ok = [r for r in done if r.error is None]
     lat = np.array([r.latency for r in ok], dtype=np.float64) * 1e3
     first = min(r.arrival for r in done)

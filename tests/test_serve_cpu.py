@@ -179,3 +179,12 @@ def test_summary_when_every_request_failed():
     s = summary(reqs)
     assert s["failed"] == 3 and s["pairs_per_s"] == 0.0
     assert np.isnan(s["p50_ms"]) and np.isnan(s["p99_ms"]) and np.isnan(s["mean_ms"])
+
+
+def test_no_requests():
+    clock = FakeClock()
+    ex = FakeExecutor(clock)
+    sch = Scheduler(budget_bytes=10, max_batch=4, bytes_of=lambda r: 3, faults=Faults())
+    assert serve([], sch, ex, clock=clock, idle_sleep=0) == []
+    s = summary([])
+    assert s["requests"] == 0 and s["pairs_per_s"] == 0.0 and np.isnan(s["p50_ms"])
