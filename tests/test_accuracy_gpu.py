@@ -1,7 +1,6 @@
 """End-to-end sanity of the GPU path against synthetic ground truth, and the
 ablation switches of Table 1 (no refinement of the initial field, propagate
 inliers and outliers, no outlier-record propagation)."""
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu

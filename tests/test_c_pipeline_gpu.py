@@ -6,7 +6,6 @@ same stream id) and the Python binding's, and pgm_sync_status reports no
 failure although every buffer started as garbage.  Cases: PGM-C at full size,
 and at an odd size gray with the direction descriptor (its bit-planes) and
 PGM-C."""
-import os
 import subprocess
 
 import numpy as np

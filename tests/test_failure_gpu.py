@@ -4,7 +4,6 @@ search launch runs out; the kernel then records PGM_ERR_TIMEOUT in the
 workspace status word and ends early (copies already in flight still land),
 and the host reads the status.  The context stays usable: with the default
 limit restored the same pair matches exactly as before."""
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu

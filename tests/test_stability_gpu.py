@@ -5,7 +5,6 @@ The key reaches the kernels exactly as it reaches the oracle."""
 import os
 import sys
 
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
